@@ -1,0 +1,316 @@
+"""IRT-PS benchmark: Mrays/s of the whole loop on one seeded synthetic workload.
+
+Workload `bumps_512` (default): 512x512 RGB heightfield of 20 Gaussian bumps and
+dents plus a 90-degree V-groove, Voronoi albedo, 32x64 RGB cosine environment,
+K = 12 lights; trace 256 spp, 2 bounces; one step = one whole job: iteration 0
+(classic PS + integration) from device-resident images, then 5 IRT iterations
+(pyramid, trace, subtract + PS, integration, D_H).  Input images are rendered
+once on the GPU from the ground truth (256 spp, 2 bounces, sigma 0.002).
+
+value      = traced segments (primary, bounce and shadow rays) / second, all ranks
+e2e        = the same through the C ABI from pinned host images, results copied back
+roofline   = the trace kernel (dominant): algorithmic lane operations per second
+             against the lane-issue peak (bound "alu")
+cpu_baseline = the oracle (plain C++) on the host cores over a pixel sample
+
+`--impl reference` times the oracle itself on the same workload (pixel samples).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (scene factory, its arguments, spp, bounces, IRT iterations per job, render spp, render bounces)
+    "bumps_512": ("bumps_512", {}, 256, 2, 5, 256, 2),
+    "bowl_64": ("bowl_64", {}, 64, 1, 3, 256, 1),
+    # a small case of the same kernels for profiler captures (one IRT iteration per job)
+    "bumps_256_profile": ("bumps_512", {"H": 256, "W": 256}, 32, 2, 1, 32, 2),
+}
+
+# Algorithmic lane operations per unit of trace work (counted from the formulas:
+# Philox4x32-10 = 10 rounds x (2 mul.hi + 2 mul.lo + 4 xor) + 9 x 2 key adds;
+# cosine direction = uniforms, 2 sqrt, turn sine/cosine polynomial, Duff basis,
+# basis combination; node visit = node bounds, two exit parameters, height at the
+# entry, compare; triangle test = Moeller-Trumbore with its four rejections).
+OPS_PER_DRAW = 98 + 47
+OPS_PER_NODE = 16
+OPS_PER_TRI = 57
+SM_COUNT = 152
+LANES_PER_SM = 128
+
+
+def sm_max_mhz():
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.split()
+        return float(out[0])
+    except Exception:
+        return 2070.0
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=10)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(sc, spp, bounces, target_s=12.0, seed=1):
+    """The oracle as it stands, on all host cores, over a pixel sample of the workload."""
+    import oracle
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(123)
+    P = sc.H * sc.W
+
+    def run(n):
+        pix = np.sort(rng.choice(P, n, replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        _, _, (prim, segs) = oracle.trace(sc.depth, sc.normals, sc.albedo, sc.lights, sc.env, spp, bounces, seed,
+                                          0, pixels=pix, fp32=True, threads=threads)
+        return time.perf_counter() - t0, segs
+
+    n = max(threads, 16)
+    dt, segs = run(n)
+    n2 = int(min(P, max(n, n * target_s / max(dt, 1e-3))))
+    dt, segs = run(n2)
+    return {"value": segs / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n2} random pixels of the workload x {sc.K} lights x {spp} spp x {bounces} bounces "
+                      f"(ground-truth state, one trace pass, {segs} segments, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, same workload and metric."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import scenes
+    name, kw, spp, bounces, n_iter, _, _ = WORKLOADS[args.workload]
+    sc = getattr(scenes, name)(**kw)
+    per_step_s = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(sc, spp, bounces, target_s=min(per_step_s, 3.0))
+    vals = []
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(sc, spp, bounces, target_s=per_step_s)
+        vals.append(last["value"])
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": "IRT-PS Mrays/s", "value": v, "unit": "Mrays/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "spp": spp, "bounces": bounces},
+            "cpu_baseline": dict(last, value=v),
+            "e2e": {"value": v, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bumps_512", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import scenes
+    from paper_1811_02357_gb300 import build
+    build.build()
+    from paper_1811_02357_gb300 import irtps
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    name, kw, spp, bounces, n_iter, rspp, rb = WORKLOADS[args.workload]
+    sc = getattr(scenes, name)(**kw)
+    H, W, K, C = sc.H, sc.W, sc.K, sc.C
+    seed = 1 + rank
+    stream = torch.cuda.Stream(device=dev)
+    ctx = irtps.Context(H, W, sc.lights, sc.env)
+    ctx.set_stream(stream.cuda_stream)
+    A0 = torch.empty((K, C, H, W), dtype=torch.float32, device=dev)
+    ctx.set_state(sc.depth, sc.normals, sc.albedo)
+    ctx.render(rspp, rb, 1000 + rank, 0.002, out=A0)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
+
+    def job():
+        ctx.set_images(A0, on_device=True)
+        ctx.iterate(n_iter, spp, bounces, seed)
+        return ctx.stats()
+
+    for _ in range(args.warmup):
+        job()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = ctx.stats()["launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    tot = dict(segments=0, primary=0, draws=0, nodes=0, tris=0, trace_ms=0.0, ps_ms=0.0, depth_ms=0.0,
+               cg_iters=0)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[i][0].record(stream)
+            st = job()
+            ev[i][1].record(stream)
+            tot["segments"] += st["segments"]
+            tot["primary"] += st["primary_segments"]
+            tot["draws"] += st["draws"]
+            tot["nodes"] += st["node_visits"]
+            tot["tris"] += st["tri_tests"]
+            tot["trace_ms"] += st["trace_ms"]
+            tot["ps_ms"] += st["ps_ms"]
+            tot["depth_ms"] += st["depth_ms"]
+            tot["cg_iters"] += st["cg_iterations"]
+        torch.cuda.synchronize()
+    launches = ctx.stats()["launches"] - launches0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        s = torch.tensor([float(tot["segments"])], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(s)
+        ms_all, segs_all = float(t.item()), float(s.item())
+    else:
+        ms_all, segs_all = ms, float(tot["segments"])
+    value = segs_all / (ms_all / 1e3) / 1e6
+    P = H * W
+
+    # end to end through the C ABI: pinned host images in, results back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        A0_host = torch.empty((K, C, H, W), dtype=torch.float32, pin_memory=True)
+        A0_host.copy_(A0.cpu())
+        outs = {"depth": torch.empty((H, W), pin_memory=True), "normals": torch.empty((H, W, 4), pin_memory=True),
+                "albedo": torch.empty((C, H, W), pin_memory=True)}
+        lib = irtps._lib
+        steps_e2e = max(1, min(args.steps, 3))
+        segs_e2e = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps_e2e):
+            irtps._check(ctx.h, lib.irtps_set_images(ctx.h, irtps._addr(A0_host.data_ptr()), irtps.IRTPS_F32, 0))
+            irtps._check(ctx.h, lib.irtps_iterate(ctx.h, n_iter, spp, bounces, seed, None))
+            segs_e2e += ctx.stats()["segments"]
+            irtps._check(ctx.h, lib.irtps_get_depth(ctx.h, irtps._addr(outs["depth"].data_ptr()), 0))
+            irtps._check(ctx.h, lib.irtps_get_normals(ctx.h, irtps._addr(outs["normals"].data_ptr()), 0))
+            irtps._check(ctx.h, lib.irtps_get_albedo(ctx.h, irtps._addr(outs["albedo"].data_ptr()), 0))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": segs_e2e / dt / 1e6, "unit": "Mrays/s", "h2d_bytes_per_step": A0_host.numel() * 4,
+               "d2h_bytes_per_step": sum(t.numel() * 4 for t in outs.values()), "steps": steps_e2e}
+
+    # roofline of the dominant kernel (the trace): algorithmic lane-ops / its event-timed duration
+    clocks = clk.summary()
+    mhz = clocks["sm_max_mhz"] or sm_max_mhz()
+    ops = OPS_PER_DRAW * tot["draws"] + OPS_PER_NODE * tot["nodes"] + OPS_PER_TRI * tot["tris"]
+    trace_launches = args.steps * n_iter
+    achieved = ops / (tot["trace_ms"] / 1e3) / 1e12
+    peak = SM_COUNT * LANES_PER_SM * mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_trace",
+                "launch_ms": tot["trace_ms"] / trace_launches,
+                "note": "lane-operation issue peak = 152 SMs x 128 lanes x max SM clock; ops counted per "
+                        "sampled direction, pyramid node visit and triangle test"}
+
+    line = {"metric": "IRT-PS Mrays/s", "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "H": H, "W": W, "K": K, "C": C, "spp": spp,
+                       "bounces": bounces, "irt_iterations_per_step": n_iter, "parallelism": f"replicas{world}",
+                       "l2": "512 MB buffer written between timed steps"},
+            "pixel_iters_per_s": P * n_iter * world * args.steps / (ms_all / 1e3),
+            "primary_mrays_per_s": tot["primary"] * world / (ms_all / 1e3) / 1e6,
+            "stage_ms_per_step": {"trace": tot["trace_ms"] / args.steps, "ps": tot["ps_ms"] / args.steps,
+                                  "depth": tot["depth_ms"] / args.steps},
+            "cg_iterations_per_step": tot["cg_iters"] / args.steps,
+            "work_per_segment": {"node_visits": tot["nodes"] / max(1, tot["segments"]),
+                                 "tri_tests": tot["tris"] / max(1, tot["segments"]),
+                                 "draws": tot["draws"] / max(1, tot["segments"])},
+            "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc, spp, bounces)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,175 @@
+/*
+ * irtps.h — C ABI of the GB300 IRT-PS library (Iterative Ray Tracing
+ * Photometric Stereo; Khadka, Remagnino, Argyriou, arXiv:1811.02357).
+ *
+ * One context holds one object: an H x W pixel grid seen orthographically along
+ * -z, K distant white lights, C colour channels (1 or 3) and a known
+ * environment.  All device memory is allocated and owned by the context; every
+ * caller buffer is only read or written during the call that receives it.
+ *
+ * Geometry and units.  Pixel (i, j), row i in [0, H), column j in [0, W),
+ * linear index p = i*W + j, pixel pitch h = 1/W (object width 1); the depth
+ * H_ij is in the same unit; +z points to the viewer; a normal is
+ * n ~ (-dH/dx, -dH/dy, 1) with y increasing with i.  The surface is meshed
+ * with vertices at the pixel centres, two triangles per cell.  The environment
+ * is a C x EH x EW latitude-longitude map over the full sphere: rows cover
+ * theta = acos(w_z) in [0, pi], columns phi = atan2(w_y, w_x) in [0, 2 pi).
+ *
+ * Array layouts (all row-major, float32 unless noted):
+ *   lights   K x 3 unit vectors, z > 0                    (Eq. 3, matrix L)
+ *   env      C x EH x EW
+ *   images   K x C x H x W (float32 or float16)           (stage 0 input A)
+ *   depth    H x W
+ *   normals  H x W x 4: nx, ny, nz, mean albedo           (Eq. 4 output)
+ *   albedo   C x H x W
+ *   indirect K x C x H x W: Lbar, the mean incident radiance of the
+ *            reverted trace (irradiance = pi * Lbar); the subtracted image is
+ *            rho * Lbar                                   (Eq. 7, E^r_t)
+ *
+ * Status.  Every call returns IRTPS_OK (0) or a negative code; the message of
+ * the last failure is available from irtps_last_error.  A CUDA failure
+ * (IRTPS_ECUDA) leaves the context unusable except for irtps_destroy.
+ * Contexts are not thread-safe: use one context per host thread.
+ */
+#ifndef IRTPS_H
+#define IRTPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IRTPS_OK 0
+#define IRTPS_EINVAL (-1)    /* bad argument or size outside the supported range */
+#define IRTPS_ENOMEM (-2)    /* device or pinned host allocation failed */
+#define IRTPS_ECUDA (-3)     /* a CUDA runtime call or kernel launch failed */
+#define IRTPS_ENOTREADY (-4) /* irtps_iterate / irtps_solve_normals before irtps_set_images */
+#define IRTPS_ETIMEOUT (-5)  /* a bounded device loop gave up (step budget exhausted) */
+#define IRTPS_ENUMERIC (-6)  /* non-finite values, or the depth solve did not converge */
+
+#define IRTPS_F32 0
+#define IRTPS_F16 1
+
+#define IRTPS_MAX_LIGHTS 64
+
+typedef struct irtps_ctx irtps_ctx;
+
+/* Tunables.  Fill with irtps_default_options, then override. */
+typedef struct irtps_options {
+  int shadow_rays;    /* 1: light visibility at every hit by a shadow ray (default 1) */
+  float tau_lo;       /* a row k of pixel p takes part in the normal solve iff     */
+  float tau_hi;       /* tau_lo < mean_c I(p,k,c) < tau_hi (0.02, 0.98)             */
+  double cond_max;    /* masked 3x3 solves with 1-norm condition above this: invalid pixel (1e8) */
+  float nz_min;       /* n_z clamp of the slopes -n_x/n_z, -n_y/n_z (0.05) */
+  double cg_tol;      /* depth solve: stop at FP64 |b - A x| / |b| <= cg_tol (1e-9) */
+  int cg_max_iter;    /* depth solve iteration cap (50000) */
+  int cg_check_every; /* FP64 true-residual refresh and convergence test period (50) */
+  double stop_tol;    /* irtps_iterate stops early when D_H < stop_tol; 0 = never (0) */
+} irtps_options;
+
+/* Counters of the last irtps_iterate / irtps_trace / irtps_integrate call. */
+typedef struct irtps_stats {
+  unsigned long long primary_segments; /* primary rays: pixels * K * spp per trace */
+  unsigned long long segments;         /* all traced segments incl. bounces and shadow rays */
+  unsigned long long walk_overflows;   /* marches that hit their step budget (expected 0) */
+  int cg_iterations;                   /* CG iterations of the last depth solve */
+  double cg_rel_residual;              /* FP64 |b - A x| / |b| at its end */
+  double dH_max;                       /* D_H of the last iteration: max |dH| / range(H) */
+  double dH_rms;                       /* RMS of H_{t+1} - H_t */
+  int iterations_done;                 /* IRT iterations completed by the last irtps_iterate */
+  unsigned long long node_visits;      /* pyramid nodes and cells examined by the marches */
+  unsigned long long tri_tests;        /* ray / triangle tests */
+  double trace_ms;                     /* device time of the trace kernel(s), CUDA events */
+  double ps_ms;                        /* device time of the subtract + PS kernel(s) */
+  double depth_ms;                     /* device time of the depth solve(s) incl. host checks */
+  unsigned long long launches;         /* kernels launched since irtps_create (cumulative) */
+  unsigned long long draws;            /* sampled directions (primary and bounce segments) */
+} irtps_stats;
+
+/* Defaults listed beside each field of irtps_options. */
+void irtps_default_options(irtps_options *opt);
+
+/* Create a context for an H x W object (H, W >= 2; H*W*K*C < 2^31), K lights
+ * (3 <= K <= 64, at least three non-coplanar: Eq. 4 needs (L^T L)^-1), C in {1, 3},
+ * environment EH x EW (>= 1).  lights, env: host pointers, copied.  opt may be
+ * NULL (defaults).  (L^T L)^-1 L^T is formed on the host in FP64 (Eq. 4). */
+int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *lights, const float *env, int EH,
+                 int EW, const irtps_options *opt);
+
+/* Run all later work on `stream` (a cudaStream_t, e.g. torch's current stream);
+ * NULL restores the context's own stream.  The caller keeps the stream alive. */
+int irtps_set_stream(irtps_ctx *ctx, void *stream);
+
+/* Stage 0 / stage 1 (Sec. IV): take the K input images (dtype IRTPS_F32 or
+ * IRTPS_F16; host pointer if on_device == 0, else a device pointer readable on
+ * the context stream) and run iteration 0: classic PS (Eq. 4, masked rows
+ * re-solved in FP64) and integration of the normals into the surface H_0.
+ * Resets the IRT iteration index to 0. */
+int irtps_set_images(irtps_ctx *ctx, const void *images, int dtype, int on_device);
+
+/* IRT iterations (Sec. IV, stages 4-5 and the loop): n_iter times
+ *   build the min/max pyramid of H_t; trace Lbar_t over (H_t, n_t, rho_t) with
+ *   spp samples per (pixel, light) and bounces in 1..3 (the paper's r1..r3);
+ *   I = A0 - rho_t * Lbar_t (subtracted from the ORIGINAL images); PS -> n, rho;
+ *   integrate -> H_{t+1}; D_H = max|H_{t+1} - H_t| / range(H_{t+1}).
+ * Random draws: Philox4x32-10, key {seed_lo ^ object, seed_hi}, counter
+ * {pixel, sample, light<<8 | bounce<<4 | 0, t}; t advances by one per iteration.
+ * out_dH (nullable host pointer) receives D_H of the last iteration. */
+int irtps_iterate(irtps_ctx *ctx, int n_iter, int spp, int bounces, uint64_t seed, double *out_dH);
+
+/* Single stages over the current state, for staged use and testing. */
+/* Trace only: Lbar over the current (depth, normals, albedo) with iteration
+ * field `iteration` and stream tag `stream_tag` (0 for the IRT loop, 1 for the
+ * forward render) in the Philox counter; result in the context's indirect buffer. */
+int irtps_trace(irtps_ctx *ctx, int spp, int bounces, uint64_t seed, uint32_t iteration, uint32_t stream_tag);
+/* Subtract + PS: images minus albedo * indirect, then Eq. 4 per pixel. */
+int irtps_solve_normals(irtps_ctx *ctx);
+/* Integrate the current normals into the depth (warm start from the current depth). */
+int irtps_integrate(irtps_ctx *ctx);
+
+/* Trace a list of pixels only (host arrays): out_lbar K x C x n_pix;
+ * out_rec (nullable) n_pix x K x spp x bounces x 2 int32 per segment:
+ * {hit pixel | -1 escape | -2 not reached, shadow visibility 1 | 0 | -1 not cast}. */
+int irtps_trace_pixels(irtps_ctx *ctx, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
+                       uint32_t iteration, uint32_t stream_tag, float *out_lbar, int32_t *out_rec);
+
+/* Replace the current estimate (host arrays): depth H x W, normals H x W x 3
+ * (unit), albedo C x H x W.  Any of them may be NULL to keep the current one. */
+int irtps_set_state(irtps_ctx *ctx, const float *depth, const float *normals, const float *albedo);
+/* Replace the indirect buffer (host, K x C x H x W). */
+int irtps_set_indirect(irtps_ctx *ctx, const float *indirect);
+
+/* Synthetic stage-0 images of the current state taken as ground truth
+ * (test-input generation): A0 = rho max(0, n.l) V + rho Lbar_gt + sigma z with
+ * Lbar_gt traced with stream tag 1 and iteration 0xFFFFFFFF (left in the
+ * indirect buffer), z ~ N(0,1) from Philox.  out: K x C x H x W float32, host
+ * or device (on_device). */
+int irtps_render(irtps_ctx *ctx, int spp, int bounces, uint64_t seed, float sigma, float *out, int on_device);
+
+/* Copies of the state (host pointer if on_device == 0, else device). */
+int irtps_get_normals(irtps_ctx *ctx, float *out, int on_device);   /* H x W x 4 */
+int irtps_get_albedo(irtps_ctx *ctx, float *out, int on_device);    /* C x H x W */
+int irtps_get_depth(irtps_ctx *ctx, float *out, int on_device);     /* H x W, mean 0 */
+int irtps_get_indirect(irtps_ctx *ctx, float *out, int on_device);  /* K x C x H x W */
+int irtps_get_valid(irtps_ctx *ctx, uint8_t *out, int on_device);   /* H x W, 1 = normal solved */
+int irtps_get_stats(irtps_ctx *ctx, irtps_stats *out);
+
+/* Geometry probes for the parity tests.  Host arrays.
+ * irtps_probe_dirs: cosine-weighted directions (Eq. 7 sampling) for n unit
+ * normals (n x 3) and raw Philox words x0, x1 -> out n x 3.
+ * irtps_probe_rays: closest hit of n grid-space rays (n x 6: origin, direction;
+ * vertex (i, j) at (j, i, depth)) with the current depth's mesh -> t (NaN on a
+ * miss) and triangle index 2*(cell_row*(W-1) + cell_col) + {0, 1} (-1). */
+int irtps_probe_dirs(int n, const float *normals, const uint32_t *x0, const uint32_t *x1, float *out);
+int irtps_probe_rays(irtps_ctx *ctx, int n, const float *rays, float *out_t, int32_t *out_tri);
+
+const char *irtps_last_error(const irtps_ctx *ctx);
+void irtps_destroy(irtps_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IRTPS_H */

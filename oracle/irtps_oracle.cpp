@@ -283,7 +283,7 @@ void walk(const Field &f, const V3<T> &o, const V3<T> &d, int cx, int cy, Hit<T>
     const T tx = sx > 0 ? ((T)(cx + 1) - o.x) * ix : (sx < 0 ? ((T)cx - o.x) * ix : inf);
     const T ty = sy > 0 ? ((T)(cy + 1) - o.y) * iy : (sy < 0 ? ((T)cy - o.y) * iy : inf);
     if (tx == inf && ty == inf) break;
-    if (std::fabs(tx - ty) <= corner * std::max(tx, ty)) {
+    if (tx != inf && ty != inf && std::fabs(tx - ty) <= corner * std::max(tx, ty)) {
       if (cx + sx >= 0 && cx + sx < Wc) test_cell<T>(f, cy, cx + sx, o, d, best);
       if (cy + sy >= 0 && cy + sy < Hc) test_cell<T>(f, cy + sy, cx, o, d, best);
     }

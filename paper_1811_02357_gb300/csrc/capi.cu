@@ -1,0 +1,552 @@
+// C ABI of the IRT-PS library: context life cycle, buffers, and the stage
+// sequence of one IRT iteration (Sec. IV): pyramid -> trace -> subtract + PS ->
+// integration -> D_H.  Declarations and argument contracts: include/irtps.h.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "irtps_internal.h"
+
+using irtps::Ctx;
+
+struct irtps_ctx {
+  Ctx c;
+};
+
+namespace {
+
+int fail(Ctx &c, int code, const std::string &msg) {
+  c.err = msg;
+  return code;
+}
+
+int cuda_fail(Ctx &c, cudaError_t e, const char *what) {
+  c.err = std::string(what) + ": " + cudaGetErrorString(e);
+  return IRTPS_ECUDA;
+}
+
+#define CK(call, what)                                     \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what);  \
+  } while (0)
+
+template <typename T>
+int dalloc(Ctx &c, T **p, size_t n, const char *what) {
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, e == cudaErrorMemoryAllocation ? IRTPS_ENOMEM : IRTPS_ECUDA,
+                std::string("allocation of ") + what + ": " + cudaGetErrorString(e));
+  }
+  return IRTPS_OK;
+}
+
+void release(Ctx &c) {
+  void *bufs[] = {c.env, c.images, c.lbar, c.depth, c.depth_prev, c.nrm, c.albedo, c.valid, c.pmin, c.pmax,
+                  c.cg_x, c.cg_b, c.cg_r, c.cg_z, c.cg_p, c.cg_ap, c.part, c.counts, c.cg_ctl};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  if (c.h_part) cudaFreeHost(c.h_part);
+  for (cudaEvent_t ev : c.ev)
+    if (ev) cudaEventDestroy(ev);
+  if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
+}
+
+// Copy to or from a caller buffer on the context stream; host copies complete before return.
+int copy_out(Ctx &c, void *dst, const void *src, size_t bytes, int on_device) {
+  CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c.stream),
+     "copy out");
+  if (!on_device) CK(cudaStreamSynchronize(c.stream), "copy out");
+  return IRTPS_OK;
+}
+
+int copy_in(Ctx &c, void *dst, const void *src, size_t bytes, int on_device) {
+  CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.stream),
+     "copy in");
+  if (!on_device) CK(cudaStreamSynchronize(c.stream), "copy in");
+  return IRTPS_OK;
+}
+
+int read_counts(Ctx &c) {
+  unsigned long long h[irtps::kCounters];
+  CK(cudaMemcpyAsync(h, c.counts, sizeof(h), cudaMemcpyDeviceToHost, c.stream), "counts");
+  CK(cudaStreamSynchronize(c.stream), "counts");
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, c.ev[0], c.ev[1]), "trace timing");
+  c.stats.trace_ms += ms;
+  c.stats.segments = h[1];
+  c.stats.walk_overflows = h[2];
+  c.stats.node_visits += h[3];
+  c.stats.tri_tests += h[4];
+  c.stats.draws += h[5];
+  if (h[2]) return fail(c, IRTPS_ETIMEOUT, "trace: a heightfield march exhausted its step budget");
+  return IRTPS_OK;
+}
+
+int trace_into(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed, uint32_t iter,
+               uint32_t stream_tag, float *out, int32_t *rec) {
+  CK(irtps::build_pyramid(c), "pyramid build");
+  CK(cudaMemcpyAsync(&c.zmax, c.pmax + c.off[c.levels - 1], sizeof(float), cudaMemcpyDeviceToHost, c.stream),
+     "pyramid top");
+  CK(cudaStreamSynchronize(c.stream), "pyramid top");
+  CK(cudaMemsetAsync(c.counts, 0, irtps::kCounters * sizeof(unsigned long long), c.stream), "counts");
+  CK(cudaEventRecord(c.ev[0], c.stream), "trace timing");
+  CK(irtps::launch_trace(c, pixels, n_pix, spp, bounces, seed, iter, stream_tag, out, rec), "trace launch");
+  CK(cudaEventRecord(c.ev[1], c.stream), "trace timing");
+  c.stats.primary_segments = (unsigned long long)n_pix * c.K * spp;
+  return read_counts(c);
+}
+
+bool trace_args_ok(Ctx &c, int spp, int bounces) {
+  if (spp < 1 || bounces < 1 || bounces > 3) {
+    c.err = "spp must be >= 1 and bounces in 1..3";
+    return false;
+  }
+  return true;
+}
+
+// Subtract + PS, timed with events on the context stream.
+int run_ps(Ctx &c, bool zero_indirect) {
+  CK(cudaEventRecord(c.ev[0], c.stream), "ps timing");
+  CK(irtps::launch_ps(c, zero_indirect), "ps launch");
+  CK(cudaEventRecord(c.ev[1], c.stream), "ps timing");
+  CK(cudaEventSynchronize(c.ev[1]), "ps");
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, c.ev[0], c.ev[1]), "ps timing");
+  c.stats.ps_ms += ms;
+  return IRTPS_OK;
+}
+
+// Depth solve, timed with events (the solve itself synchronises for its convergence tests).
+int run_depth(Ctx &c) {
+  CK(cudaEventRecord(c.ev[0], c.stream), "depth timing");
+  int rc = irtps::solve_depth(c);
+  if (rc) return rc;
+  CK(cudaEventRecord(c.ev[1], c.stream), "depth timing");
+  CK(cudaEventSynchronize(c.ev[1]), "depth");
+  float ms = 0.0f;
+  CK(cudaEventElapsedTime(&ms, c.ev[0], c.ev[1]), "depth timing");
+  c.stats.depth_ms += ms;
+  return IRTPS_OK;
+}
+
+void reset_timers(Ctx &c) {
+  c.stats.trace_ms = c.stats.ps_ms = c.stats.depth_ms = 0.0;
+  c.stats.node_visits = c.stats.tri_tests = c.stats.draws = 0;
+}
+
+int iteration_zero(Ctx &c) {
+  int rc = run_ps(c, true);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(c.depth, 0, sizeof(float) * c.H * c.W, c.stream), "depth reset");
+  return run_depth(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+void irtps_default_options(irtps_options *opt) {
+  if (!opt) return;
+  opt->shadow_rays = 1;
+  opt->tau_lo = 0.02f;
+  opt->tau_hi = 0.98f;
+  opt->cond_max = 1e8;
+  opt->nz_min = 0.05f;
+  opt->cg_tol = 1e-9;
+  opt->cg_max_iter = 50000;
+  opt->cg_check_every = 50;
+  opt->stop_tol = 0.0;
+}
+
+int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *lights, const float *env, int EH,
+                 int EW, const irtps_options *opt) {
+  if (!out) return IRTPS_EINVAL;
+  *out = nullptr;
+  irtps_ctx *x = new (std::nothrow) irtps_ctx;
+  if (!x) return IRTPS_ENOMEM;
+  Ctx &c = x->c;
+  auto bail = [&](int rc) {
+    // keep the context so that the caller can read the message; it is still destroyable
+    *out = x;
+    return rc;
+  };
+  if (H < 2 || W < 2 || K < 3 || K > irtps::kMaxLights || (C != 1 && C != 3) || EH < 1 || EW < 1 || !lights ||
+      !env)
+    return bail(fail(c, IRTPS_EINVAL, "create: need H, W >= 2, 3 <= K <= 64, C in {1,3}, EH, EW >= 1, lights, env"));
+  if ((long long)H * W * K * C >= (1LL << 31) || (long long)(W - 1) * (H - 1) * 2 >= (1LL << 31))
+    return bail(fail(c, IRTPS_EINVAL, "create: H*W*K*C must stay below 2^31"));
+  c.H = H;
+  c.W = W;
+  c.K = K;
+  c.C = C;
+  c.EH = EH;
+  c.EW = EW;
+  if (opt)
+    c.opt = *opt;
+  else
+    irtps_default_options(&c.opt);
+  c.eps = (float)1e-3 / (float)W;  // same expression as the oracle's lift
+  // lights and pinv(L) = (L^T L)^-1 L^T in FP64 (Eq. 4)
+  c.h_lights.assign(lights, lights + 3 * K);
+  double M[3][3] = {{0}};
+  for (int k = 0; k < K; ++k) {
+    const double l[3] = {lights[3 * k], lights[3 * k + 1], lights[3 * k + 2]};
+    if (!std::isfinite(l[0]) || !std::isfinite(l[1]) || !std::isfinite(l[2]))
+      return bail(fail(c, IRTPS_EINVAL, "create: non-finite light direction"));
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) M[a][b] += l[a] * l[b];
+  }
+  const double A[3][3] = {{M[1][1] * M[2][2] - M[1][2] * M[2][1], M[0][2] * M[2][1] - M[0][1] * M[2][2],
+                           M[0][1] * M[1][2] - M[0][2] * M[1][1]},
+                          {M[1][2] * M[2][0] - M[1][0] * M[2][2], M[0][0] * M[2][2] - M[0][2] * M[2][0],
+                           M[0][2] * M[1][0] - M[0][0] * M[1][2]},
+                          {M[1][0] * M[2][1] - M[1][1] * M[2][0], M[0][1] * M[2][0] - M[0][0] * M[2][1],
+                           M[0][0] * M[1][1] - M[0][1] * M[1][0]}};
+  const double det = M[0][0] * A[0][0] + M[0][1] * A[1][0] + M[0][2] * A[2][0];
+  double trace = M[0][0] + M[1][1] + M[2][2];
+  if (!(std::fabs(det) > 1e-12 * trace * trace * trace))
+    return bail(fail(c, IRTPS_EINVAL, "create: the lights are coplanar (L^T L is singular)"));
+  c.h_pinv.resize(3 * K);
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < K; ++k) {
+      double v = 0.0;
+      for (int b = 0; b < 3; ++b) v += A[a][b] / det * lights[3 * k + b];
+      c.h_pinv[a * K + k] = (float)v;
+    }
+  // pyramid geometry
+  int w = W - 1, h = H - 1, total = 0, l = 0;
+  while (true) {
+    if (l >= irtps::kMaxLevels) return bail(fail(c, IRTPS_EINVAL, "create: grid too large for the pyramid"));
+    c.off[l] = total;
+    c.lw[l] = w;
+    c.lh[l] = h;
+    total += w * h;
+    ++l;
+    if (w == 1 && h == 1) break;
+    w = (w + 1) / 2;
+    h = (h + 1) / 2;
+  }
+  c.levels = l;
+  // buffers
+  const size_t P = (size_t)H * W;
+  int rc;
+  cudaError_t e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "create: stream"));
+  c.own_stream = true;
+  for (int i = 0; i < 2; ++i) {
+    e = cudaEventCreate(&c.ev[i]);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "create: events"));
+  }
+  c.cg_blocks = (int)std::min<size_t>((P + 255) / 256, (size_t)irtps::cg_grid_limit());
+  c.part_stride = c.cg_blocks;
+  if ((rc = dalloc(c, &c.env, (size_t)C * EH * EW, "environment")) ||
+      (rc = dalloc(c, (float **)&c.images, (size_t)K * C * P, "images")) ||
+      (rc = dalloc(c, &c.lbar, (size_t)K * C * P, "indirect")) || (rc = dalloc(c, &c.depth, P, "depth")) ||
+      (rc = dalloc(c, &c.depth_prev, P, "depth")) || (rc = dalloc(c, &c.nrm, P, "normals")) ||
+      (rc = dalloc(c, &c.albedo, (size_t)C * P, "albedo")) || (rc = dalloc(c, &c.valid, P, "valid")) ||
+      (rc = dalloc(c, &c.pmin, (size_t)total, "pyramid")) || (rc = dalloc(c, &c.pmax, (size_t)total, "pyramid")) ||
+      (rc = dalloc(c, &c.cg_x, P, "cg")) || (rc = dalloc(c, &c.cg_b, P, "cg")) ||
+      (rc = dalloc(c, &c.cg_r, P, "cg")) || (rc = dalloc(c, &c.cg_z, P, "cg")) ||
+      (rc = dalloc(c, &c.cg_p, 2 * P, "cg")) || (rc = dalloc(c, &c.cg_ap, 2 * P, "cg")) ||
+      (rc = dalloc(c, &c.part, (size_t)irtps::kPartSlots * c.part_stride, "partials")) ||
+      (rc = dalloc(c, &c.counts, irtps::kCounters, "counters")) ||
+      (rc = dalloc(c, (irtps::CGCtl **)&c.cg_ctl, 1, "solver control")))
+    return bail(rc);
+  e = cudaMallocHost((void **)&c.h_part, sizeof(double) * c.part_stride);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "create: pinned partials"));
+  e = cudaMemcpyAsync(c.env, env, sizeof(float) * C * EH * EW, cudaMemcpyHostToDevice, c.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.lbar, 0, sizeof(float) * K * C * P, c.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.depth, 0, sizeof(float) * P, c.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.albedo, 0, sizeof(float) * C * P, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "create: upload"));
+  *out = x;
+  return IRTPS_OK;
+}
+
+int irtps_set_stream(irtps_ctx *ctx, void *stream) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (c.own_stream && c.stream) {
+    CK(cudaStreamSynchronize(c.stream), "set stream");
+    CK(cudaStreamDestroy(c.stream), "set stream");
+    c.own_stream = false;
+  }
+  if (stream) {
+    c.stream = (cudaStream_t)stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking), "set stream");
+    c.own_stream = true;
+  }
+  return IRTPS_OK;
+}
+
+int irtps_set_images(irtps_ctx *ctx, const void *images, int dtype, int on_device) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (!images || (dtype != IRTPS_F32 && dtype != IRTPS_F16))
+    return fail(c, IRTPS_EINVAL, "set_images: need images and dtype IRTPS_F32 or IRTPS_F16");
+  const size_t n = (size_t)c.K * c.C * c.H * c.W;
+  c.images_dtype = dtype;
+  int rc = copy_in(c, c.images, images, n * (dtype == IRTPS_F16 ? 2 : 4), on_device);
+  if (rc) return rc;
+  c.have_images = true;
+  c.t = 0;
+  reset_timers(c);
+  return iteration_zero(c);
+}
+
+int irtps_iterate(irtps_ctx *ctx, int n_iter, int spp, int bounces, uint64_t seed, double *out_dH) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (!c.have_images) return fail(c, IRTPS_ENOTREADY, "iterate: call irtps_set_images first");
+  if (n_iter < 0 || !trace_args_ok(c, spp, bounces)) return fail(c, IRTPS_EINVAL, c.err.empty() ? "iterate" : c.err);
+  c.stats.iterations_done = 0;
+  reset_timers(c);
+  unsigned long long prim = 0, segs = 0;
+  for (int it = 0; it < n_iter; ++it) {
+    CK(cudaMemcpyAsync(c.depth_prev, c.depth, sizeof(float) * c.H * c.W, cudaMemcpyDeviceToDevice, c.stream),
+       "iterate");
+    int rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, c.t, 0u, c.lbar, nullptr);
+    if (rc) return rc;
+    prim += c.stats.primary_segments;
+    segs += c.stats.segments;
+    rc = run_ps(c, false);
+    if (rc) return rc;
+    rc = run_depth(c);
+    if (rc) return rc;
+    rc = irtps::depth_change(c, &c.stats.dH_max, &c.stats.dH_rms);
+    if (rc) return rc;
+    ++c.t;
+    c.stats.iterations_done = it + 1;
+    if (c.opt.stop_tol > 0.0 && c.stats.dH_max < c.opt.stop_tol) break;
+  }
+  c.stats.primary_segments = prim;
+  c.stats.segments = segs;
+  if (out_dH) *out_dH = c.stats.dH_max;
+  return IRTPS_OK;
+}
+
+int irtps_trace(irtps_ctx *ctx, int spp, int bounces, uint64_t seed, uint32_t iteration, uint32_t stream_tag) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (!trace_args_ok(c, spp, bounces) || stream_tag > 15) return fail(c, IRTPS_EINVAL, "trace: bad arguments");
+  reset_timers(c);
+  return trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, iteration, stream_tag, c.lbar, nullptr);
+}
+
+int irtps_solve_normals(irtps_ctx *ctx) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (!c.have_images) return fail(c, IRTPS_ENOTREADY, "solve_normals: call irtps_set_images first");
+  reset_timers(c);
+  return run_ps(c, false);
+}
+
+int irtps_integrate(irtps_ctx *ctx) {
+  if (!ctx) return IRTPS_EINVAL;
+  reset_timers(ctx->c);
+  return run_depth(ctx->c);
+}
+
+int irtps_trace_pixels(irtps_ctx *ctx, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
+                       uint32_t iteration, uint32_t stream_tag, float *out_lbar, int32_t *out_rec) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (!pixels || n_pix < 1 || !out_lbar || !trace_args_ok(c, spp, bounces) || stream_tag > 15)
+    return fail(c, IRTPS_EINVAL, "trace_pixels: bad arguments");
+  const int P = c.H * c.W;
+  for (int i = 0; i < n_pix; ++i)
+    if (pixels[i] < 0 || pixels[i] >= P) return fail(c, IRTPS_EINVAL, "trace_pixels: pixel index out of range");
+  const size_t nrec = out_rec ? (size_t)n_pix * c.K * spp * bounces * 2 : 0;
+  int32_t *d_pix = nullptr, *d_rec = nullptr;
+  float *d_out = nullptr;
+  int rc;
+  if ((rc = dalloc(c, &d_pix, n_pix, "pixel list")) || (rc = dalloc(c, &d_out, (size_t)c.K * c.C * n_pix, "out")) ||
+      (out_rec && (rc = dalloc(c, &d_rec, nrec, "records")))) {
+    cudaFree(d_pix);
+    cudaFree(d_out);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(d_pix, pixels, sizeof(int32_t) * n_pix, cudaMemcpyHostToDevice, c.stream);
+  if (e == cudaSuccess) {
+    rc = trace_into(c, d_pix, n_pix, spp, bounces, seed, iteration, stream_tag, d_out, d_rec);
+    if (rc == IRTPS_OK) {
+      e = cudaMemcpyAsync(out_lbar, d_out, sizeof(float) * c.K * c.C * n_pix, cudaMemcpyDeviceToHost, c.stream);
+      if (e == cudaSuccess && out_rec)
+        e = cudaMemcpyAsync(out_rec, d_rec, sizeof(int32_t) * nrec, cudaMemcpyDeviceToHost, c.stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    }
+  }
+  cudaFree(d_pix);
+  cudaFree(d_out);
+  if (d_rec) cudaFree(d_rec);
+  if (e != cudaSuccess) return cuda_fail(c, e, "trace_pixels");
+  return rc;
+}
+
+int irtps_set_state(irtps_ctx *ctx, const float *depth, const float *normals, const float *albedo) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  const size_t P = (size_t)c.H * c.W;
+  if (depth) {
+    int rc = copy_in(c, c.depth, depth, sizeof(float) * P, 0);
+    if (rc) return rc;
+  }
+  if (albedo) {
+    int rc = copy_in(c, c.albedo, albedo, sizeof(float) * c.C * P, 0);
+    if (rc) return rc;
+  }
+  if (normals || albedo) {
+    // pack (n, mean albedo) on the host from the given or current arrays
+    std::vector<float> n4(4 * P), rho((size_t)c.C * P), cur(4 * P);
+    if (!normals) CK(cudaMemcpy(cur.data(), c.nrm, sizeof(float) * 4 * P, cudaMemcpyDeviceToHost), "set_state");
+    if (albedo)
+      std::memcpy(rho.data(), albedo, sizeof(float) * c.C * P);
+    else
+      CK(cudaMemcpy(rho.data(), c.albedo, sizeof(float) * c.C * P, cudaMemcpyDeviceToHost), "set_state");
+    for (size_t p = 0; p < P; ++p) {
+      for (int a = 0; a < 3; ++a) n4[4 * p + a] = normals ? normals[3 * p + a] : cur[4 * p + a];
+      float s = 0.0f;
+      for (int ch = 0; ch < c.C; ++ch) s += rho[ch * P + p];
+      n4[4 * p + 3] = s / (float)c.C;
+    }
+    int rc = copy_in(c, c.nrm, n4.data(), sizeof(float) * 4 * P, 0);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(c.valid, 1, P, c.stream), "set_state");
+  }
+  return IRTPS_OK;
+}
+
+int irtps_set_indirect(irtps_ctx *ctx, const float *indirect) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (!indirect) return fail(c, IRTPS_EINVAL, "set_indirect: NULL");
+  return copy_in(c, c.lbar, indirect, sizeof(float) * c.K * c.C * c.H * c.W, 0);
+}
+
+int irtps_render(irtps_ctx *ctx, int spp, int bounces, uint64_t seed, float sigma, float *out, int on_device) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (!out || !trace_args_ok(c, spp, bounces) || !(sigma >= 0.0f)) return fail(c, IRTPS_EINVAL, "render: bad arguments");
+  int rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, 0xFFFFFFFFu, 1u, c.lbar, nullptr);
+  if (rc) return rc;
+  const size_t n = (size_t)c.K * c.C * c.H * c.W;
+  float *dst = out;
+  float *tmp = nullptr;
+  if (!on_device) {
+    if ((rc = dalloc(c, &tmp, n, "render output"))) return rc;
+    dst = tmp;
+  }
+  cudaError_t e = irtps::launch_render(c, seed, sigma, c.lbar, dst);
+  if (e == cudaSuccess && !on_device) {
+    e = cudaMemcpyAsync(out, tmp, sizeof(float) * n, cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  }
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(c, e, "render");
+  return IRTPS_OK;
+}
+
+int irtps_get_normals(irtps_ctx *ctx, float *out, int on_device) {
+  if (!ctx || !out) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  return copy_out(c, out, c.nrm, sizeof(float) * 4 * c.H * c.W, on_device);
+}
+int irtps_get_albedo(irtps_ctx *ctx, float *out, int on_device) {
+  if (!ctx || !out) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  return copy_out(c, out, c.albedo, sizeof(float) * c.C * c.H * c.W, on_device);
+}
+int irtps_get_depth(irtps_ctx *ctx, float *out, int on_device) {
+  if (!ctx || !out) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  return copy_out(c, out, c.depth, sizeof(float) * c.H * c.W, on_device);
+}
+int irtps_get_indirect(irtps_ctx *ctx, float *out, int on_device) {
+  if (!ctx || !out) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  return copy_out(c, out, c.lbar, sizeof(float) * c.K * c.C * c.H * c.W, on_device);
+}
+int irtps_get_valid(irtps_ctx *ctx, uint8_t *out, int on_device) {
+  if (!ctx || !out) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  return copy_out(c, out, c.valid, (size_t)c.H * c.W, on_device);
+}
+int irtps_get_stats(irtps_ctx *ctx, irtps_stats *out) {
+  if (!ctx || !out) return IRTPS_EINVAL;
+  *out = ctx->c.stats;
+  return IRTPS_OK;
+}
+
+int irtps_probe_dirs(int n, const float *normals, const uint32_t *x0, const uint32_t *x1, float *out) {
+  if (n < 1 || !normals || !x0 || !x1 || !out) return IRTPS_EINVAL;
+  float *dn = nullptr, *dout = nullptr;
+  uint32_t *d0 = nullptr, *d1 = nullptr;
+  cudaError_t e = cudaMalloc(&dn, sizeof(float) * 3 * n);
+  if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(float) * 3 * n);
+  if (e == cudaSuccess) e = cudaMalloc(&d0, sizeof(uint32_t) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&d1, sizeof(uint32_t) * n);
+  if (e == cudaSuccess) e = cudaMemcpy(dn, normals, sizeof(float) * 3 * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d0, x0, sizeof(uint32_t) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d1, x1, sizeof(uint32_t) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = irtps::launch_probe_dirs(nullptr, n, dn, d0, d1, dout);
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost);
+  cudaFree(dn);
+  cudaFree(dout);
+  cudaFree(d0);
+  cudaFree(d1);
+  return e == cudaSuccess ? IRTPS_OK : IRTPS_ECUDA;
+}
+
+int irtps_probe_rays(irtps_ctx *ctx, int n, const float *rays, float *out_t, int32_t *out_tri) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (n < 1 || !rays || !out_t || !out_tri) return fail(c, IRTPS_EINVAL, "probe_rays: bad arguments");
+  CK(irtps::build_pyramid(c), "pyramid build");
+  CK(cudaMemcpyAsync(&c.zmax, c.pmax + c.off[c.levels - 1], sizeof(float), cudaMemcpyDeviceToHost, c.stream),
+     "pyramid top");
+  CK(cudaStreamSynchronize(c.stream), "pyramid top");
+  float *dr = nullptr, *dt = nullptr;
+  int32_t *dtri = nullptr;
+  int *dov = nullptr;
+  int rc;
+  if ((rc = dalloc(c, &dr, (size_t)6 * n, "rays")) || (rc = dalloc(c, &dt, (size_t)n, "t")) ||
+      (rc = dalloc(c, &dtri, (size_t)n, "tri")) || (rc = dalloc(c, &dov, 1, "flag"))) {
+    cudaFree(dr);
+    cudaFree(dt);
+    cudaFree(dtri);
+    return rc;
+  }
+  int ov = 0;
+  cudaError_t e = cudaMemcpyAsync(dr, rays, sizeof(float) * 6 * n, cudaMemcpyHostToDevice, c.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dov, 0, sizeof(int), c.stream);
+  if (e == cudaSuccess) e = irtps::launch_probe_rays(c, n, dr, dt, dtri, dov);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_t, dt, sizeof(float) * n, cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_tri, dtri, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ov, dov, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  cudaFree(dr);
+  cudaFree(dt);
+  cudaFree(dtri);
+  cudaFree(dov);
+  if (e != cudaSuccess) return cuda_fail(c, e, "probe_rays");
+  if (ov) return fail(c, IRTPS_ETIMEOUT, "probe_rays: a march exhausted its step budget");
+  return IRTPS_OK;
+}
+
+const char *irtps_last_error(const irtps_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+void irtps_destroy(irtps_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->c.stream) cudaStreamSynchronize(ctx->c.stream);
+  release(ctx->c);
+  delete ctx;
+}
+
+}  // extern "C"

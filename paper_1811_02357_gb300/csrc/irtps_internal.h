@@ -1,0 +1,103 @@
+// Internal state of one IRT-PS context and the launchers behind the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/irtps.h"
+#include "geom.cuh"
+
+namespace irtps {
+
+constexpr int kMaxLights = 64;
+
+struct Ctx {
+  int H = 0, W = 0, K = 0, C = 0, EH = 0, EW = 0;
+  uint32_t obj = 0;
+  irtps_options opt{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool have_images = false;
+  uint32_t t = 0;                 // IRT iteration index of the next irtps_iterate step
+  float eps = 0.0f;               // ray-origin lift, 1e-3 of a pixel pitch
+  std::string err;
+
+  // host copies
+  std::vector<float> h_lights;    // K*3
+  std::vector<float> h_pinv;      // 3*K, (L^T L)^-1 L^T rounded to float
+
+  // device buffers (owned)
+  float *env = nullptr;           // C*EH*EW
+  void *images = nullptr;         // K*C*H*W, float or half
+  int images_dtype = IRTPS_F32;
+  float *lbar = nullptr;          // K*C*H*W
+  float *depth = nullptr;         // H*W
+  float *depth_prev = nullptr;    // H*W
+  float4 *nrm = nullptr;          // H*W
+  float *albedo = nullptr;        // C*H*W
+  uint8_t *valid = nullptr;       // H*W, 1 = normal solved
+  float *pmin = nullptr, *pmax = nullptr;  // pyramid, all levels
+  int levels = 0;
+  int off[kMaxLevels] = {0}, lw[kMaxLevels] = {0}, lh[kMaxLevels] = {0};
+  float zmax = 0.0f;              // host copy of the top pyramid node
+  // depth solve
+  double *cg_x = nullptr, *cg_b = nullptr;
+  float *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_ap = nullptr;
+  double *part = nullptr;         // reduction partials: kPartSlots slots of part_stride doubles
+  int part_stride = 0, cg_blocks = 0;
+  double *h_part = nullptr;       // pinned host mirror of one partial slot
+  void *cg_ctl = nullptr;         // device control block of the cooperative CG loop
+  unsigned long long *counts = nullptr;  // {unused, segments, walk overflows, node visits, triangle tests, sampled directions}
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  irtps_stats stats{};
+
+  Field field() const {
+    Field f;
+    f.depth = depth;
+    f.pmax = pmax;
+    f.H = H;
+    f.W = W;
+    f.Wc = W - 1;
+    f.Hc = H - 1;
+    f.levels = levels;
+    for (int l = 0; l < kMaxLevels; ++l) {
+      f.off[l] = off[l];
+      f.lw[l] = lw[l];
+    }
+    f.zmax_margin = zmax + 1e-4f;
+    float a = zmax < 0 ? -zmax : zmax;
+    f.dz = 1e-5f * (1.0f + a);
+    return f;
+  }
+};
+
+constexpr int kPartSlots = 12;
+
+// Control block of the cooperative depth-solve loop (see poisson.cu).
+struct CGCtl {
+  unsigned count, gen;
+  int err;
+  int iters;
+  double rel;
+};
+constexpr int kCounters = 6;
+
+// trace.cu
+cudaError_t build_pyramid(Ctx &c);
+cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
+                         uint32_t iter, uint32_t stream, float *out, int32_t *rec);
+cudaError_t launch_render(Ctx &c, uint64_t seed, float sigma, const float *lbar, float *out);
+cudaError_t launch_probe_dirs(cudaStream_t s, int n, const float *normals, const uint32_t *x0, const uint32_t *x1,
+                              float *out);
+cudaError_t launch_probe_rays(Ctx &c, int n, const float *rays, float *t_out, int32_t *tri_out, int *overflow);
+// ps.cu
+cudaError_t launch_ps(Ctx &c, bool zero_indirect);
+// poisson.cu
+int solve_depth(Ctx &c);          // IRTPS_OK or an error code (message in c.err)
+int depth_change(Ctx &c, double *dH_max, double *dH_rms);
+int cg_grid_limit();  // co-resident blocks available to the cooperative solve
+
+}  // namespace irtps

@@ -1,0 +1,533 @@
+// Integration of the normals into the surface (Sec. IV, stage 1: "integrating
+// over the obtained normals a 3D surface H_t is obtained") and the convergence
+// measure D_H = H_{t+1} - H_t of the loop.
+//
+// The surface minimises sum over grid edges (H_b - H_a - g_e)^2 with trapezoidal
+// edge targets g = h (p_a + p_b) / 2 (rows) and h (q_a + q_b) / 2 (columns), slopes
+// p = -n_x / max(n_z, nz_min), q = -n_y / max(n_z, nz_min); mean(H) = 0.  Its normal
+// equations L H = D^T g use the Neumann 5-point graph Laplacian L.
+//
+// Solver: Jacobi-preconditioned CG (M = diag(degree)) in FP32 for the search
+// direction, residual and preconditioned residual, with the iterate x and the
+// right-hand side b in FP64; every cg_check_every iterations the residual is
+// replaced by the FP64 true residual b - A x (iterative refinement) and tested
+// against cg_tol.  Reductions are two-stage and deterministic: each block writes
+// one partial, and every consumer block sums all partials in the same order.
+#include <cmath>
+#include <vector>
+
+#include "irtps_internal.h"
+
+namespace irtps {
+
+enum Slot { S_BB = 0, S_PAP = 1, S_RZ0 = 2, S_RZ1 = 3, S_RR = 4, S_SUMX = 5, S_DMAX = 6, S_DSQ = 7, S_HMAX = 8,
+            S_HMIN = 9, S_RZREF = 10 };
+static_assert(S_RZREF < kPartSlots, "partial slots");
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum (or max); the result is valid in thread 0.
+template <bool MAX>
+__device__ __forceinline__ double block_reduce(double v, double *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = MAX ? warp_max(v) : warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const double ident = MAX ? -INFINITY : 0.0;
+    v = lane < (int)(blockDim.x >> 5) ? sh[lane] : ident;
+    v = MAX ? warp_max(v) : warp_sum(v);
+  }
+  return v;
+}
+
+// Sum of n partials, identical in every block (fixed order); all threads get it.
+__device__ __forceinline__ double total(const double *part, int n, double *sh) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += 32) v += part[i];
+    v = warp_sum(v);
+    if (threadIdx.x == 0) sh[32] = v;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+template <typename T>
+__device__ __forceinline__ T lap_at(const T *v, int i, int j, int H, int W) {
+  const size_t p = (size_t)i * W + j;
+  const T c = v[p];
+  T s = 0;
+  int deg = 0;
+  if (j > 0) { s += v[p - 1]; ++deg; }
+  if (j < W - 1) { s += v[p + 1]; ++deg; }
+  if (i > 0) { s += v[p - W]; ++deg; }
+  if (i < H - 1) { s += v[p + W]; ++deg; }
+  return (T)deg * c - s;
+}
+
+__device__ __forceinline__ int degree(int i, int j, int H, int W) {
+  return (j > 0) + (j < W - 1) + (i > 0) + (i < H - 1);
+}
+
+struct CG {
+  int H, W, P;
+  double h;
+  float nz_min;
+  const float4 *nrm;
+  float *depth;
+  double *x, *b;
+  float *r, *z, *p, *ap;  // p: two buffers of P; ap: A p, then the FP32 correction
+  double *part;
+  int stride, nblk;
+};
+
+__device__ __forceinline__ void slopes(const float4 *nrm, size_t p, float nz_min, double &sp, double &sq) {
+  const float4 n = nrm[p];
+  const double nz = fmax((double)n.z, (double)nz_min);
+  sp = -(double)n.x / nz;
+  sq = -(double)n.y / nz;
+}
+
+// b = D^T g (FP64) and |b|^2 partials.
+__global__ void __launch_bounds__(kThreads) k_rhs(const CG g) {
+  __shared__ double sh[33];
+  double bb = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
+    const int i = p / g.W, j = p - i * g.W;
+    double pc, qc, pn, qn;
+    slopes(g.nrm, p, g.nz_min, pc, qc);
+    double v = 0.0;
+    if (j > 0) { slopes(g.nrm, p - 1, g.nz_min, pn, qn); v += g.h * (pn + pc) * 0.5; }
+    if (j < g.W - 1) { slopes(g.nrm, p + 1, g.nz_min, pn, qn); v -= g.h * (pc + pn) * 0.5; }
+    if (i > 0) { slopes(g.nrm, p - g.W, g.nz_min, pn, qn); v += g.h * (qn + qc) * 0.5; }
+    if (i < g.H - 1) { slopes(g.nrm, p + g.W, g.nz_min, pn, qn); v -= g.h * (qc + qn) * 0.5; }
+    g.b[p] = v;
+    bb += v * v;
+  }
+  bb = block_reduce<false>(bb, sh);
+  if (threadIdx.x == 0) g.part[S_BB * g.stride + blockIdx.x] = bb;
+}
+
+__global__ void __launch_bounds__(kThreads) k_load_x(const CG g) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) g.x[p] = (double)g.depth[p];
+}
+
+// True residual r = b - A x in FP64 (stored FP32), z = r / deg, partials of r.z and |r|^2 (FP64).
+__global__ void __launch_bounds__(kThreads) k_residual(const CG g, int rz_slot) {
+  __shared__ double sh[33];
+  double rz = 0.0, rr = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
+    const int i = p / g.W, j = p - i * g.W;
+    const double res = g.b[p] - lap_at<double>(g.x, i, j, g.H, g.W);
+    const float rf = (float)res;
+    const float zf = rf / (float)degree(i, j, g.H, g.W);
+    g.r[p] = rf;
+    g.z[p] = zf;
+    rz += (double)rf * (double)zf;
+    rr += res * res;
+  }
+  rz = block_reduce<false>(rz, sh);
+  if (threadIdx.x == 0) {
+    g.part[rz_slot * g.stride + blockIdx.x] = rz;
+    g.part[S_RZREF * g.stride + blockIdx.x] = rz;
+  }
+  rr = block_reduce<false>(rr, sh);
+  if (threadIdx.x == 0) g.part[S_RR * g.stride + blockIdx.x] = rr;
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks co-resident).  Thread 0
+// of each block arrives on a counter; the last one resets it and advances the
+// generation word the others poll.  Every poll loop is bounded: on running out it
+// raises the error flag, and all blocks leave the solve at the next check.
+__device__ __forceinline__ void grid_barrier(unsigned *count, volatile unsigned *gen, int *err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g0 = *gen;
+    __threadfence();
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      *count = 0u;
+      __threadfence();
+      atomicAdd((unsigned *)gen, 1u);
+    } else {
+      unsigned long long polls = 0;
+      while (*gen == g0) {
+        if (++polls > (1ull << 24)) {
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Block-wide FP32 sum; the result is valid in thread 0.
+__device__ __forceinline__ float block_sum_f(float v, float *shf) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) shf[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? shf[lane] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// Pixel coordinates of a grid-stride loop, advanced without divisions.
+struct Stride {
+  int p, i, j, dp, di, dj;
+  __device__ __forceinline__ Stride(int W) {
+    p = blockIdx.x * blockDim.x + threadIdx.x;
+    i = p / W;
+    j = p - i * W;
+    dp = gridDim.x * blockDim.x;
+    di = dp / W;
+    dj = dp - di * W;
+  }
+  __device__ __forceinline__ void next(int W) {
+    p += dp;
+    i += di;
+    j += dj;
+    if (j >= W) {
+      j -= W;
+      ++i;
+    }
+  }
+};
+
+__device__ __forceinline__ float inv_degree(int i, int j, int H, int W) {
+  const int d = (j > 0) + (j < W - 1) + (i > 0) + (i < H - 1);
+  return d == 4 ? 0.25f : (d == 3 ? (1.0f / 3.0f) : (d == 2 ? 0.5f : 1.0f));
+}
+
+// The whole Jacobi-PCG loop in one cooperative launch.  The iterate is
+// x = x64 + e: the FP64 part changes only at a refresh, the FP32 correction e
+// collects alpha * p in between.  Per iteration:
+//  A: beta = rz_{it-1}/rz_{it-2}; p_it = z + beta p_{it-1} (also at the 4
+//     neighbours, recomputed locally); Ap; partial p.Ap       -- barrier --
+//  B: alpha = rz_{it-1}/p.Ap; e += alpha p; r -= alpha Ap; z = r/deg;
+//     partial r.z                                             -- barrier --
+// Every `check` iterations, or as soon as r.z has fallen below 1e-10 of its
+// value at the last refresh (the FP32 recursion has converged and further steps
+// would follow rounding noise: the direction is then frozen to 0), x64 += e,
+// e = 0, and the residual is recomputed in FP64 (r = b - A x64) and tested
+// against tol (iterative refinement).  Dot products are FP32 within a block and
+// FP64 across blocks; every block sums the same partials in the same order and
+// so takes the same decisions.
+__global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, double bnorm, double tol,
+                                                      int max_iter, int check) {
+  __shared__ double sh[33];
+  __shared__ float shf[33];
+  __shared__ float s_ab[2];
+  __shared__ int s_frozen;
+  double best = INFINITY;
+  int stall = 0, it = 0;
+  double rel = ctl->rel;
+  float *e = g.ap + g.P;  // correction accumulator (second half of the Ap buffer)
+  for (Stride q(g.W); q.p < g.P; q.next(g.W)) e[q.p] = 0.0f;
+  while (rel > tol && it < max_iter) {
+    ++it;
+    // ---- A ----
+    const double num = total(g.part + (S_RZ0 + ((it - 1) & 1)) * g.stride, g.nblk, sh);
+    const double ref = total(g.part + S_RZREF * g.stride, g.nblk, sh);
+    const double den = it > 1 ? total(g.part + (S_RZ0 + (it & 1)) * g.stride, g.nblk, sh) : 0.0;
+    if (threadIdx.x == 0) {
+      const bool frozen = !(num > 1e-10 * ref);
+      s_frozen = frozen;
+      s_ab[1] = (it > 1 && !frozen && den > 0.0) ? (float)(num / den) : 0.0f;
+    }
+    __syncthreads();
+    const bool frozen = s_frozen;
+    const float beta = s_ab[1];
+    const bool first = it == 1;
+    const float *pold = g.p + (size_t)((it - 1) & 1) * g.P;
+    float *pnew = g.p + (size_t)(it & 1) * g.P;
+    auto dir = [&](int r) { return frozen ? 0.0f : (first ? g.z[r] : fmaf(beta, pold[r], g.z[r])); };
+    float pap = 0.0f;
+    for (Stride q(g.W); q.p < g.P; q.next(g.W)) {
+      const int p = q.p;
+      const float pc = dir(p);
+      float s = 0.0f, deg = 0.0f;
+      if (q.j > 0) { s += dir(p - 1); deg += 1.0f; }
+      if (q.j < g.W - 1) { s += dir(p + 1); deg += 1.0f; }
+      if (q.i > 0) { s += dir(p - g.W); deg += 1.0f; }
+      if (q.i < g.H - 1) { s += dir(p + g.W); deg += 1.0f; }
+      const float apv = fmaf(deg, pc, -s);
+      pnew[p] = pc;
+      g.ap[p] = apv;
+      pap = fmaf(pc, apv, pap);
+    }
+    pap = block_sum_f(pap, shf);
+    if (threadIdx.x == 0) g.part[S_PAP * g.stride + blockIdx.x] = (double)pap;
+    grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+    if (*(volatile int *)&ctl->err) break;
+    // ---- B ----
+    const double dpap = total(g.part + S_PAP * g.stride, g.nblk, sh);
+    if (threadIdx.x == 0) s_ab[0] = (dpap > 0.0 && isfinite(dpap)) ? (float)(num / dpap) : 0.0f;
+    __syncthreads();
+    const float af = s_ab[0];
+    float rz = 0.0f;
+    for (Stride q(g.W); q.p < g.P; q.next(g.W)) {
+      const int p = q.p;
+      e[p] = fmaf(af, pnew[p], e[p]);
+      const float rf = fmaf(-af, g.ap[p], g.r[p]);
+      const float zf = rf * inv_degree(q.i, q.j, g.H, g.W);
+      g.r[p] = rf;
+      g.z[p] = zf;
+      rz = fmaf(rf, zf, rz);
+    }
+    rz = block_sum_f(rz, shf);
+    if (threadIdx.x == 0) g.part[(S_RZ0 + (it & 1)) * g.stride + blockIdx.x] = (double)rz;
+    grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+    if (*(volatile int *)&ctl->err) break;
+    // ---- refresh from FP64 ----
+    if (it % check == 0 || frozen) {
+      for (Stride q(g.W); q.p < g.P; q.next(g.W)) {
+        g.x[q.p] += (double)e[q.p];
+        e[q.p] = 0.0f;
+      }
+      grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+      if (*(volatile int *)&ctl->err) break;
+      double rzr = 0.0, rr = 0.0;
+      for (Stride q(g.W); q.p < g.P; q.next(g.W)) {
+        const double res = g.b[q.p] - lap_at<double>(g.x, q.i, q.j, g.H, g.W);
+        const float rf = (float)res;
+        const float zf = rf * inv_degree(q.i, q.j, g.H, g.W);
+        g.r[q.p] = rf;
+        g.z[q.p] = zf;
+        rzr += (double)rf * (double)zf;
+        rr += res * res;
+      }
+      rzr = block_reduce<false>(rzr, sh);
+      if (threadIdx.x == 0) {
+        g.part[(S_RZ0 + (it & 1)) * g.stride + blockIdx.x] = rzr;
+        g.part[S_RZREF * g.stride + blockIdx.x] = rzr;
+      }
+      rr = block_reduce<false>(rr, sh);
+      if (threadIdx.x == 0) g.part[S_RR * g.stride + blockIdx.x] = rr;
+      grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+      if (*(volatile int *)&ctl->err) break;
+      rel = sqrt(total(g.part + S_RR * g.stride, g.nblk, sh)) / bnorm;
+      if (!isfinite(rel)) break;
+      if (rel < 0.95 * best) {
+        best = rel;
+        stall = 0;
+      } else if (++stall >= 10) {
+        break;  // the FP64 residual has stopped improving (rounding floor)
+      }
+    }
+  }
+  // fold in a correction collected since the last refresh (none when the loop ended on a refresh)
+  for (Stride q(g.W); q.p < g.P; q.next(g.W)) g.x[q.p] += (double)e[q.p];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->iters = it;
+    ctl->rel = rel;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_sum_x(const CG g) {
+  __shared__ double sh[33];
+  double s = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) s += g.x[p];
+  s = block_reduce<false>(s, sh);
+  if (threadIdx.x == 0) g.part[S_SUMX * g.stride + blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_store_depth(const CG g) {
+  __shared__ double sh[33];
+  const double mean = total(g.part + S_SUMX * g.stride, g.nblk, sh) / (double)g.P;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x)
+    g.depth[p] = (float)(g.x[p] - mean);
+}
+
+__global__ void __launch_bounds__(kThreads) k_zero_depth(const CG g) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) g.depth[p] = 0.0f;
+}
+
+// D_H partials: max |H_new - H_old|, sum (H_new - H_old)^2, max H_new, -min H_new.
+__global__ void __launch_bounds__(kThreads) k_depth_change(const CG g, const float *old) {
+  __shared__ double sh[33];
+  double dmax = 0.0, dsq = 0.0, hmax = -INFINITY, hmin = -INFINITY;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
+    const double a = g.depth[p], d = a - (double)old[p];
+    dmax = fmax(dmax, fabs(d));
+    dsq += d * d;
+    hmax = fmax(hmax, a);
+    hmin = fmax(hmin, -a);
+  }
+  dmax = block_reduce<true>(dmax, sh);
+  if (threadIdx.x == 0) g.part[S_DMAX * g.stride + blockIdx.x] = dmax;
+  dsq = block_reduce<false>(dsq, sh);
+  if (threadIdx.x == 0) g.part[S_DSQ * g.stride + blockIdx.x] = dsq;
+  hmax = block_reduce<true>(hmax, sh);
+  if (threadIdx.x == 0) g.part[S_HMAX * g.stride + blockIdx.x] = hmax;
+  hmin = block_reduce<true>(hmin, sh);
+  if (threadIdx.x == 0) g.part[S_HMIN * g.stride + blockIdx.x] = hmin;
+}
+
+// Blocks of the cooperative solve: all must be co-resident; two per SM keep the
+// barrier's arrival counter short.
+int cg_grid_limit() {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_loop, kThreads, 0) != cudaSuccess) return 1;
+  per = per < 2 ? per : 2;
+  return per * sms > 0 ? per * sms : 1;
+}
+
+static CG make_cg(Ctx &c) {
+  CG g;
+  g.H = c.H;
+  g.W = c.W;
+  g.P = c.H * c.W;
+  g.h = 1.0 / (double)c.W;
+  g.nz_min = c.opt.nz_min;
+  g.nrm = c.nrm;
+  g.depth = c.depth;
+  g.x = c.cg_x;
+  g.b = c.cg_b;
+  g.r = c.cg_r;
+  g.z = c.cg_z;
+  g.p = c.cg_p;
+  g.ap = c.cg_ap;
+  g.part = c.part;
+  g.stride = c.part_stride;
+  g.nblk = c.cg_blocks;
+  return g;
+}
+
+// Copy one partial slot to the host and combine it there (fixed order).
+static int read_slot(Ctx &c, int slot, bool is_max, double *out) {
+  cudaError_t e = cudaMemcpyAsync(c.h_part, c.part + (size_t)slot * c.part_stride, sizeof(double) * c.cg_blocks,
+                                  cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) {
+    c.err = std::string("depth solve: ") + cudaGetErrorString(e);
+    return IRTPS_ECUDA;
+  }
+  double v = is_max ? -INFINITY : 0.0;
+  for (int i = 0; i < c.cg_blocks; ++i) v = is_max ? std::fmax(v, c.h_part[i]) : v + c.h_part[i];
+  *out = v;
+  return IRTPS_OK;
+}
+
+#define LAUNCH_CHECK()                                              \
+  do {                                                              \
+    cudaError_t e_ = cudaGetLastError();                            \
+    if (e_ != cudaSuccess) {                                        \
+      c.err = std::string("depth solve: ") + cudaGetErrorString(e_); \
+      return IRTPS_ECUDA;                                           \
+    }                                                               \
+  } while (0)
+
+int solve_depth(Ctx &c) {
+  const CG g = make_cg(c);
+  const int nb = c.cg_blocks;
+  k_rhs<<<nb, kThreads, 0, c.stream>>>(g);
+  ++c.stats.launches;
+  LAUNCH_CHECK();
+  double bb;
+  int rc = read_slot(c, S_BB, false, &bb);
+  if (rc) return rc;
+  if (!std::isfinite(bb)) {
+    c.err = "depth solve: non-finite right-hand side";
+    return IRTPS_ENUMERIC;
+  }
+  c.stats.cg_iterations = 0;
+  c.stats.cg_rel_residual = 0.0;
+  if (bb == 0.0) {
+    k_zero_depth<<<nb, kThreads, 0, c.stream>>>(g);
+    ++c.stats.launches;
+    LAUNCH_CHECK();
+    return IRTPS_OK;
+  }
+  const double bnorm = std::sqrt(bb);
+  k_load_x<<<nb, kThreads, 0, c.stream>>>(g);
+  k_residual<<<nb, kThreads, 0, c.stream>>>(g, S_RZ0);
+  c.stats.launches += 2;
+  LAUNCH_CHECK();
+  double rr;
+  rc = read_slot(c, S_RR, false, &rr);
+  if (rc) return rc;
+  double rel = std::sqrt(rr) / bnorm;
+  int it = 0;
+  if (rel > c.opt.cg_tol) {
+    irtps::CGCtl h{0u, 0u, 0, 0, rel};
+    cudaError_t e = cudaMemcpyAsync(c.cg_ctl, &h, sizeof(h), cudaMemcpyHostToDevice, c.stream);
+    if (e != cudaSuccess) {
+      c.err = std::string("depth solve: ") + cudaGetErrorString(e);
+      return IRTPS_ECUDA;
+    }
+    const int m = c.opt.cg_check_every > 0 ? c.opt.cg_check_every : 50;
+    double tol = c.opt.cg_tol;
+    int max_iter = c.opt.cg_max_iter;
+    irtps::CGCtl *ctl = (irtps::CGCtl *)c.cg_ctl;
+    void *args[] = {(void *)&g, (void *)&ctl, (void *)&bnorm, (void *)&tol, (void *)&max_iter, (void *)&m};
+    e = cudaLaunchCooperativeKernel((const void *)k_cg_loop, dim3(nb), dim3(kThreads), args, 0, c.stream);
+    ++c.stats.launches;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c.cg_ctl, sizeof(h), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) {
+      c.err = std::string("depth solve: ") + cudaGetErrorString(e);
+      return IRTPS_ECUDA;
+    }
+    if (h.err) {
+      c.err = "depth solve: a grid barrier timed out";
+      return IRTPS_ETIMEOUT;
+    }
+    it = h.iters;
+    rel = h.rel;
+  }
+  c.stats.cg_iterations = it;
+  c.stats.cg_rel_residual = rel;
+  k_sum_x<<<nb, kThreads, 0, c.stream>>>(g);
+  k_store_depth<<<nb, kThreads, 0, c.stream>>>(g);
+  c.stats.launches += 2;
+  LAUNCH_CHECK();
+  if (!std::isfinite(rel)) {
+    c.err = "depth solve: non-finite residual";
+    return IRTPS_ENUMERIC;
+  }
+  if (rel > c.opt.cg_tol) {
+    c.err = "depth solve: relative residual " + std::to_string(rel) + " above cg_tol after " + std::to_string(it) +
+            " iterations";
+    return IRTPS_ENUMERIC;
+  }
+  return IRTPS_OK;
+}
+
+int depth_change(Ctx &c, double *dH_max, double *dH_rms) {
+  const CG g = make_cg(c);
+  k_depth_change<<<c.cg_blocks, kThreads, 0, c.stream>>>(g, c.depth_prev);
+  ++c.stats.launches;
+  LAUNCH_CHECK();
+  double dmax, dsq, hmax, hmin;
+  int rc = read_slot(c, S_DMAX, true, &dmax);
+  if (!rc) rc = read_slot(c, S_DSQ, false, &dsq);
+  if (!rc) rc = read_slot(c, S_HMAX, true, &hmax);
+  if (!rc) rc = read_slot(c, S_HMIN, true, &hmin);
+  if (rc) return rc;
+  const double range = hmax + hmin;  // max H - min H
+  *dH_max = range > 0.0 ? dmax / range : 0.0;
+  *dH_rms = std::sqrt(dsq / (double)g.P);
+  return IRTPS_OK;
+}
+
+}  // namespace irtps

@@ -1,0 +1,484 @@
+// Reverted Monte-Carlo trace (Sec. IV, Eq. 5-7): min/max pyramid build, the
+// per-(pixel, light) trace kernel, the stage-0 forward render, and geometry
+// probes used by the parity tests.
+#include <cstdint>
+#include <cuda_fp16.h>
+
+#include "geom.cuh"
+#include "irtps_internal.h"
+
+namespace irtps {
+
+// ---------------------------------------------------------------------------
+// Min / max pyramid.  Level 0: one node per cell, over its 4 vertex heights.
+// Level l: one node per 2x2 block of level l-1 nodes (clipped at the border).
+// ---------------------------------------------------------------------------
+__global__ void k_pyramid_leaf(const float *__restrict__ depth, int H, int W, float *__restrict__ pmin,
+                               float *__restrict__ pmax) {
+  const int Wc = W - 1, Hc = H - 1;
+  const int n = Wc * Hc;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int cy = i / Wc, cx = i - cy * Wc;
+    const float *r = depth + (size_t)cy * W + cx;
+    const float a = r[0], b = r[1], c = r[W], d = r[W + 1];
+    pmin[i] = fminf(fminf(a, b), fminf(c, d));
+    pmax[i] = fmaxf(fmaxf(a, b), fmaxf(c, d));
+  }
+}
+
+__global__ void k_pyramid_up(const float *__restrict__ cmin, const float *__restrict__ cmax, int cw, int ch,
+                             float *__restrict__ pmin, float *__restrict__ pmax, int w, int h) {
+  const int n = w * h;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int y = i / w, x = i - y * w;
+    float lo = __int_as_float(0x7f800000), hi = -lo;
+    for (int dy = 0; dy < 2; ++dy) {
+      const int yy = 2 * y + dy;
+      if (yy >= ch) break;
+      for (int dx = 0; dx < 2; ++dx) {
+        const int xx = 2 * x + dx;
+        if (xx >= cw) break;
+        lo = fminf(lo, cmin[yy * cw + xx]);
+        hi = fmaxf(hi, cmax[yy * cw + xx]);
+      }
+    }
+    pmin[i] = lo;
+    pmax[i] = hi;
+  }
+}
+
+cudaError_t build_pyramid(Ctx &c) {
+  const int Wc = c.W - 1, Hc = c.H - 1;
+  const int threads = 256;
+  int blocks = (Wc * Hc + threads - 1) / threads;
+  blocks = blocks < 1 ? 1 : (blocks > 4096 ? 4096 : blocks);
+  k_pyramid_leaf<<<blocks, threads, 0, c.stream>>>(c.depth, c.H, c.W, c.pmin, c.pmax);
+  c.stats.launches += c.levels;
+  for (int l = 1; l < c.levels; ++l) {
+    const int n = c.lw[l] * c.lh[l];
+    int b = (n + threads - 1) / threads;
+    b = b > 4096 ? 4096 : b;
+    k_pyramid_up<<<b, threads, 0, c.stream>>>(c.pmin + c.off[l - 1], c.pmax + c.off[l - 1], c.lw[l - 1],
+                                               c.lh[l - 1], c.pmin + c.off[l], c.pmax + c.off[l], c.lw[l],
+                                               c.lh[l]);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Environment: bilinear lookup in a C x EH x EW latitude-longitude map over the
+// full sphere (theta = acos(w_z) down the rows, phi = atan2(w_y, w_x) across,
+// texel centres at half-integers, wrap in phi, clamp in theta).
+// ---------------------------------------------------------------------------
+template <int C>
+__device__ __forceinline__ void env_lookup(const float *__restrict__ env, int EH, int EW, F3 w, float *out) {
+  const float inv = rsqrtf(w.x * w.x + w.y * w.y + w.z * w.z);
+  const float z = fminf(1.0f, fmaxf(-1.0f, w.z * inv));
+  const float theta = acosf(z);
+  float phi = atan2f(w.y, w.x);
+  if (phi < 0.0f) phi += 6.28318530717958647692f;
+  const float row = theta * ((float)EH * 0.318309886183790671538f) - 0.5f;
+  const float col = phi * ((float)EW * 0.159154943091895335769f) - 0.5f;
+  const float r0 = floorf(row), c0 = floorf(col);
+  const float fr = row - r0, fc = col - c0;
+  const int ra = min(EH - 1, max(0, (int)r0));
+  const int rb = min(EH - 1, max(0, (int)r0 + 1));
+  int ca = (int)c0 % EW;
+  if (ca < 0) ca += EW;
+  const int cb = ca + 1 == EW ? 0 : ca + 1;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const float *m = env + (size_t)c * EH * EW;
+    const float top = (1.0f - fc) * __ldg(m + ra * EW + ca) + fc * __ldg(m + ra * EW + cb);
+    const float bot = (1.0f - fc) * __ldg(m + rb * EW + ca) + fc * __ldg(m + rb * EW + cb);
+    out[c] = (1.0f - fr) * top + fr * bot;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The trace.  Each thread owns one (light k, pixel p) and runs its spp sample
+// paths in order, Kahan-summing their radiance in FP32.  Sample path: bounce
+// b = 1..B draws Philox4x32-10 at counter {p, s, (k<<8)|(b<<4)|stream, iteration}
+// with key {seed_lo ^ obj, seed_hi}, samples a cosine direction about the
+// current normal estimate at the origin, and marches the heightfield.  Escape:
+// add T * Env(w), stop.  Hit at q (nearest vertex): add
+// T * rho_q * max(0, n_q . l_k) * V_k(q) (V from a shadow ray, cast when
+// n_q . l_k > 0), then T <- T * rho_q and continue from q lifted by eps.
+// Lbar(k, c, p) = sum / spp: mean incident radiance (irradiance / pi).
+//
+// Execution: every lane is a small state machine (set up a segment -> march ->
+// resolve).  March steps of all lanes run in a loop that the warp leaves only
+// when at most half of its live lanes are still marching; the finished lanes
+// then resolve and set up their next segments together.  Lanes therefore stay
+// busy although path lengths differ widely, while each lane's own sequence of
+// operations - and so every result bit - is that of a plain sequential trace.
+// ---------------------------------------------------------------------------
+struct TraceArgs {
+  Field f;
+  const float4 *nrm;      // H*W (nx, ny, nz, mean albedo)
+  const float *albedo;    // C*H*W
+  const float *env;       // C*EH*EW
+  int EH, EW;
+  const int32_t *pixels;  // optional pixel list
+  int n_pix, K, spp, bounces, shadow;
+  uint32_t iter, stream;
+  uint2 key;
+  float eps, Wf;
+  float *out;             // K*C*n_pix
+  int32_t *rec;           // optional n_pix*K*spp*B*2
+  unsigned long long *counts;  // {unused, segments, walk overflows, node visits, triangle tests, draws}
+  float3 light[kMaxLights];
+};
+
+#ifndef IRTPS_TRACE_MINB
+#define IRTPS_TRACE_MINB 12
+#endif
+#ifndef IRTPS_MARCH_KEEP
+#define IRTPS_MARCH_KEEP 3
+#endif
+#ifndef IRTPS_LEAF_BATCH
+#define IRTPS_LEAF_BATCH 4
+#endif
+constexpr int kTraceThreads = 128;
+// leave the march loop when marching lanes <= live lanes / kMarchKeep
+constexpr int kMarchKeep = IRTPS_MARCH_KEEP;
+// run leaf steps once kLeafBatch * (lanes waiting for one) >= lanes doing node steps
+constexpr int kLeafBatch = IRTPS_LEAF_BATCH;
+enum : int { PH_SETUP = 0, PH_MARCH = 1, PH_RESOLVE = 2, PH_DONE = 3 };
+
+template <int C>
+__global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const TraceArgs a) {
+  __shared__ LevelTable lt;
+  load_levels(a.f, &lt);
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool alive = idx < a.n_pix * a.K;
+  const int k = alive ? idx / a.n_pix : 0;
+  const int ip = alive ? idx - k * a.n_pix : 0;
+  const int p = alive ? (a.pixels ? a.pixels[ip] : ip) : 0;
+  const int W = a.f.W, H = a.f.H;
+  const size_t P = (size_t)H * W;
+  const int pi = p / W, pj = p - pi * W;
+  const F3 org0 = {(float)pj, (float)pi, radd(__ldg(a.f.depth + p), a.eps)};
+  const float3 l3 = a.light[k];
+  const F3 l = {l3.x, l3.y, l3.z};
+  const F3 lg = {rmul(l.x, a.Wf), rmul(l.y, a.Wf), l.z};
+  const int budget0 = 8 * (a.f.Wc + a.f.Hc + 8) * (a.f.levels + 1);
+
+  int phase = alive ? PH_SETUP : PH_DONE;
+  int s = 0, b = 1, npix = p, qp = 0, budget = budget0;
+  bool shadow = false;
+  F3 org = org0;
+  float cosv = 0.0f;
+  float thr[C], acc[C], sum[C], comp[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    thr[c] = 1.0f;
+    acc[c] = sum[c] = comp[c] = 0.0f;
+  }
+  int32_t *rec = nullptr;
+  Walker m;
+  bool at_leaf = false;
+  Work w;
+  uint32_t segs = 0;
+  int overflow = 0;
+
+  auto rec_slot = [&](int bb) -> int32_t * {
+    return a.rec + ((((size_t)ip * a.K + k) * a.spp + s) * a.bounces + (bb - 1)) * 2;
+  };
+  auto end_sample = [&]() {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {  // Kahan summation over samples
+      const float y = acc[c] - comp[c];
+      const float t = sum[c] + y;
+      comp[c] = (t - sum[c]) - y;
+      sum[c] = t;
+      acc[c] = 0.0f;
+      thr[c] = 1.0f;
+    }
+    ++s;
+    b = 1;
+    org = org0;
+    npix = p;
+    budget = budget0;
+    phase = PH_SETUP;
+  };
+  auto continue_path = [&](int q, F3 from) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) thr[c] *= __ldg(a.albedo + c * P + q);
+    if (b < a.bounces) {
+      ++b;
+      org = from;
+      npix = q;
+      phase = PH_SETUP;
+    } else {
+      end_sample();
+    }
+  };
+
+  while (true) {
+    // ---- set up the next primary or bounce segment ----
+    if (phase == PH_SETUP) {
+      if (s >= a.spp) {
+        phase = PH_DONE;
+      } else {
+        if (a.rec && b == 1) {
+          int32_t *r = rec_slot(1);
+          for (int j = 0; j < 2 * a.bounces; ++j) r[j] = -2;
+        }
+        const uint4 x = philox4x32_10(
+            make_uint4((uint32_t)p, (uint32_t)s, ((uint32_t)k << 8) | ((uint32_t)b << 4) | a.stream, a.iter), a.key);
+        const float4 n4 = __ldg(a.nrm + npix);
+        const F3 dw = cosine_dir(F3{n4.x, n4.y, n4.z}, x.x, x.y);
+        walker_init(m, org, F3{rmul(dw.x, a.Wf), rmul(dw.y, a.Wf), dw.z}, false);
+        shadow = false;
+        ++segs;
+        ++w.draws;
+        phase = PH_MARCH;
+      }
+    }
+    if (__all_sync(0xffffffffu, phase == PH_DONE)) break;
+    // ---- march while enough of the live lanes are marching; node steps every
+    // iteration, leaf steps once enough marching lanes wait for one ----
+    while (true) {
+      if (phase == PH_MARCH && !at_leaf) {
+        if (walker_node_step(m, a.f, lt, w, at_leaf)) phase = PH_RESOLVE;
+      }
+      const unsigned leaf = __ballot_sync(0xffffffffu, phase == PH_MARCH && at_leaf);
+      const unsigned node = __ballot_sync(0xffffffffu, phase == PH_MARCH && !at_leaf);
+      if (leaf != 0u && kLeafBatch * __popc(leaf) >= __popc(node)) {
+        if (phase == PH_MARCH && at_leaf) {
+          at_leaf = false;
+          if (walker_leaf_step(m, a.f, w)) phase = PH_RESOLVE;
+        }
+      }
+      if (phase == PH_MARCH && --budget < 0) {
+        overflow = 1;
+        at_leaf = false;
+        phase = PH_RESOLVE;
+      }
+      const unsigned marching = __ballot_sync(0xffffffffu, phase == PH_MARCH);
+      const unsigned live = __ballot_sync(0xffffffffu, phase != PH_DONE);
+      if (marching == 0u || kMarchKeep * __popc(marching) <= __popc(live)) break;
+    }
+    // ---- resolve finished segments ----
+    if (phase == PH_RESOLVE) {
+      if (shadow) {
+        const int vis = m.btri >= 0 ? 0 : 1;
+        if (a.rec) rec_slot(b)[1] = vis;
+        if (vis) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * __ldg(a.albedo + c * P + qp), cosv, acc[c]);
+        }
+        continue_path(qp, org);
+      } else if (m.btri < 0) {
+        // escaped: environment radiance along the (world) direction
+        const F3 dw = {m.d.x / a.Wf, m.d.y / a.Wf, m.d.z};
+        float e[C];
+        env_lookup<C>(a.env, a.EH, a.EW, dw, e);
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c], e[c], acc[c]);
+        if (a.rec) {
+          int32_t *r = rec_slot(b);
+          r[0] = -1;
+          r[1] = -1;
+        }
+        end_sample();
+      } else {
+        const float t = m.bt;
+        const F3 q = {radd(m.o.x, rmul(t, m.d.x)), radd(m.o.y, rmul(t, m.d.y)), radd(m.o.z, rmul(t, m.d.z))};
+        qp = nearest_index(q.y, H) * W + nearest_index(q.x, W);
+        const float4 m4 = __ldg(a.nrm + qp);
+        const F3 nq = {m4.x, m4.y, m4.z};
+        const F3 o2 = {q.x, q.y, radd(q.z, a.eps)};
+        if (a.rec) {
+          int32_t *r = rec_slot(b);
+          r[0] = qp;
+          r[1] = -1;
+        }
+        if (f3dot(nq, l) > 0.0f) {
+          cosv = fmaxf(0.0f, nq.x * l.x + nq.y * l.y + nq.z * l.z);
+          if (a.shadow) {
+            walker_init(m, o2, lg, true);
+            shadow = true;
+            org = o2;
+            ++segs;
+            phase = PH_MARCH;
+          } else {
+            if (a.rec) rec_slot(b)[1] = 1;
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * __ldg(a.albedo + c * P + qp), cosv, acc[c]);
+            continue_path(qp, o2);
+          }
+        } else {
+          continue_path(qp, o2);
+        }
+      }
+    }
+  }
+  if (alive) {
+    const float inv = 1.0f / (float)a.spp;
+#pragma unroll
+    for (int c = 0; c < C; ++c) a.out[((size_t)k * C + c) * a.n_pix + ip] = sum[c] * inv;
+  }
+  // counters: warp sums, one atomic per warp and counter
+  unsigned long long sg = segs, ov = (unsigned)overflow, nv = w.nodes, tt = w.tris, dr = w.draws;
+  for (int o = 16; o > 0; o >>= 1) {
+    sg += __shfl_down_sync(0xffffffffu, sg, o);
+    ov += __shfl_down_sync(0xffffffffu, ov, o);
+    nv += __shfl_down_sync(0xffffffffu, nv, o);
+    tt += __shfl_down_sync(0xffffffffu, tt, o);
+    dr += __shfl_down_sync(0xffffffffu, dr, o);
+  }
+  if ((threadIdx.x & 31) == 0 && a.counts) {
+    if (sg) atomicAdd(a.counts + 1, sg);
+    if (ov) atomicAdd(a.counts + 2, ov);
+    if (nv) atomicAdd(a.counts + 3, nv);
+    if (tt) atomicAdd(a.counts + 4, tt);
+    if (dr) atomicAdd(a.counts + 5, dr);
+  }
+}
+
+static void fill_trace_args(const Ctx &c, TraceArgs &a) {
+  a.f = c.field();
+  a.nrm = c.nrm;
+  a.albedo = c.albedo;
+  a.env = c.env;
+  a.EH = c.EH;
+  a.EW = c.EW;
+  a.K = c.K;
+  a.shadow = c.opt.shadow_rays;
+  a.eps = c.eps;
+  a.Wf = (float)c.W;
+  a.counts = c.counts;
+  for (int k = 0; k < c.K; ++k) a.light[k] = make_float3(c.h_lights[3 * k], c.h_lights[3 * k + 1], c.h_lights[3 * k + 2]);
+}
+
+cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
+                         uint32_t iter, uint32_t stream, float *out, int32_t *rec) {
+  TraceArgs a;
+  fill_trace_args(c, a);
+  a.pixels = pixels;
+  a.n_pix = n_pix;
+  a.spp = spp;
+  a.bounces = bounces;
+  a.iter = iter;
+  a.stream = stream;
+  a.key = make_uint2((uint32_t)seed ^ c.obj, (uint32_t)(seed >> 32));
+  a.out = out;
+  a.rec = rec;
+  const long long n = (long long)n_pix * c.K;
+  const int threads = kTraceThreads;
+  const long long blocks = (n + threads - 1) / threads;
+  ++c.stats.launches;
+  if (c.C == 1)
+    k_trace<1><<<(unsigned)blocks, threads, 0, c.stream>>>(a);
+  else
+    k_trace<3><<<(unsigned)blocks, threads, 0, c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Stage-0 forward render of a ground-truth state (synthetic input images):
+// A0(k, c, p) = rho * max(0, n . l_k) * V_k(p) + rho * Lbar_gt(k, c, p) + sigma * z,
+// V_k(p) from a shadow ray at the pixel's own vertex (cast when n . l_k > 0),
+// z standard normal by Box-Muller on Philox counter {p, 0, (k<<8)|(c<<4)|2, ~0}.
+// ---------------------------------------------------------------------------
+template <int C>
+__global__ void k_render(const TraceArgs a, const float *__restrict__ lbar, float sigma, float *__restrict__ out) {
+  __shared__ LevelTable lt;
+  load_levels(a.f, &lt);
+  const int P = a.f.H * a.f.W;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P * a.K) return;
+  const int k = idx / P, p = idx - k * P;
+  const int pi = p / a.f.W, pj = p - pi * a.f.W;
+  const float4 n4 = a.nrm[p];
+  const F3 n = {n4.x, n4.y, n4.z};
+  const float3 l3 = a.light[k];
+  const F3 l = {l3.x, l3.y, l3.z};
+  float cosv = 0.0f;
+  if (f3dot(n, l) > 0.0f) {
+    int vis = 1;
+    if (a.shadow) {
+      const F3 o = {(float)pj, (float)pi, radd(a.f.depth[p], a.eps)};
+      const F3 lg = {rmul(l.x, a.Wf), rmul(l.y, a.Wf), l.z};
+      float t;
+      int tri;
+      int budget = 8 * (a.f.Wc + a.f.Hc + 8) * (a.f.levels + 1);
+      Work w;
+      vis = march(a.f, lt, o, lg, true, t, tri, budget, w) ? 0 : 1;
+    }
+    if (vis) cosv = fmaxf(0.0f, n.x * l.x + n.y * l.y + n.z * l.z);
+  }
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)p, 0u, ((uint32_t)k << 8) | ((uint32_t)c << 4) | 2u,
+                                             0xFFFFFFFFu), a.key);
+    const float u1 = (float)((x.x >> 8) + 1u) * 5.9604644775390625e-08f;
+    const float u2 = (float)(x.y >> 8) * 5.9604644775390625e-08f;
+    const float z = sqrtf(-2.0f * logf(u1)) * cosf(6.28318530717958647692f * u2);
+    const float rho = a.albedo[(size_t)c * P + p];
+    const size_t o = ((size_t)k * C + c) * P + p;
+    out[o] = rho * cosv + rho * lbar[o] + sigma * z;
+  }
+}
+
+cudaError_t launch_render(Ctx &c, uint64_t seed, float sigma, const float *lbar, float *out) {
+  TraceArgs a;
+  fill_trace_args(c, a);
+  a.key = make_uint2((uint32_t)seed ^ c.obj, (uint32_t)(seed >> 32));
+  const long long n = (long long)c.H * c.W * c.K;
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  ++c.stats.launches;
+  if (c.C == 1)
+    k_render<1><<<blocks, threads, 0, c.stream>>>(a, lbar, sigma, out);
+  else
+    k_render<3><<<blocks, threads, 0, c.stream>>>(a, lbar, sigma, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Geometry probes (parity tests): sampled directions and ray / mesh hits.
+// ---------------------------------------------------------------------------
+__global__ void k_probe_dirs(int n, const float *__restrict__ normals, const uint32_t *__restrict__ x0,
+                             const uint32_t *__restrict__ x1, float *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const F3 nn = {normals[3 * i], normals[3 * i + 1], normals[3 * i + 2]};
+  const F3 d = cosine_dir(nn, x0[i], x1[i]);
+  out[3 * i] = d.x;
+  out[3 * i + 1] = d.y;
+  out[3 * i + 2] = d.z;
+}
+
+__global__ void k_probe_rays(const Field f, int n, const float *__restrict__ rays, float *__restrict__ t_out,
+                             int32_t *__restrict__ tri_out, int *__restrict__ overflow) {
+  __shared__ LevelTable lt;
+  load_levels(f, &lt);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const F3 o = {rays[6 * i], rays[6 * i + 1], rays[6 * i + 2]};
+  const F3 d = {rays[6 * i + 3], rays[6 * i + 4], rays[6 * i + 5]};
+  float t;
+  int tri;
+  int budget = 8 * (f.Wc + f.Hc + 8) * (f.levels + 1);
+  Work w;
+  const bool hit = march(f, lt, o, d, false, t, tri, budget, w);
+  t_out[i] = hit ? t : __int_as_float(0x7fc00000);
+  tri_out[i] = hit ? tri : -1;
+  if (budget < 0) atomicAdd(overflow, 1);
+}
+
+cudaError_t launch_probe_dirs(cudaStream_t s, int n, const float *normals, const uint32_t *x0, const uint32_t *x1,
+                              float *out) {
+  k_probe_dirs<<<(n + 127) / 128, 128, 0, s>>>(n, normals, x0, x1, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_rays(Ctx &c, int n, const float *rays, float *t_out, int32_t *tri_out, int *overflow) {
+  k_probe_rays<<<(n + 127) / 128, 128, 0, c.stream>>>(c.field(), n, rays, t_out, tri_out, overflow);
+  return cudaGetLastError();
+}
+
+}  // namespace irtps

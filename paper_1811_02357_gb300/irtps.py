@@ -1,0 +1,350 @@
+"""Thin Python binding of the IRT-PS C ABI (include/irtps.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+`_lib/libirtps.so`.  Host arrays are numpy arrays; device arrays are anything
+exposing `data_ptr()` (torch tensors) or a raw integer address.  There is no
+CPU fallback: if the library is missing or fails to load, importing this
+module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libirtps.so")
+
+IRTPS_OK = 0
+IRTPS_EINVAL = -1
+IRTPS_ENOMEM = -2
+IRTPS_ECUDA = -3
+IRTPS_ENOTREADY = -4
+IRTPS_ETIMEOUT = -5
+IRTPS_ENUMERIC = -6
+IRTPS_F32 = 0
+IRTPS_F16 = 1
+FORWARD_ITER = 0xFFFFFFFF
+
+EXPORTED = [
+    "irtps_default_options", "irtps_create", "irtps_set_stream", "irtps_set_images", "irtps_iterate",
+    "irtps_trace", "irtps_solve_normals", "irtps_integrate", "irtps_trace_pixels", "irtps_set_state",
+    "irtps_set_indirect", "irtps_render", "irtps_get_normals", "irtps_get_albedo", "irtps_get_depth",
+    "irtps_get_indirect", "irtps_get_valid", "irtps_get_stats", "irtps_probe_dirs", "irtps_probe_rays",
+    "irtps_last_error", "irtps_destroy",
+]
+
+
+class irtps_options(ctypes.Structure):
+    _fields_ = [("shadow_rays", ctypes.c_int), ("tau_lo", ctypes.c_float), ("tau_hi", ctypes.c_float),
+                ("cond_max", ctypes.c_double), ("nz_min", ctypes.c_float), ("cg_tol", ctypes.c_double),
+                ("cg_max_iter", ctypes.c_int), ("cg_check_every", ctypes.c_int), ("stop_tol", ctypes.c_double)]
+
+
+class irtps_stats(ctypes.Structure):
+    _fields_ = [("primary_segments", ctypes.c_ulonglong), ("segments", ctypes.c_ulonglong),
+                ("walk_overflows", ctypes.c_ulonglong), ("cg_iterations", ctypes.c_int),
+                ("cg_rel_residual", ctypes.c_double), ("dH_max", ctypes.c_double), ("dH_rms", ctypes.c_double),
+                ("iterations_done", ctypes.c_int), ("node_visits", ctypes.c_ulonglong),
+                ("tri_tests", ctypes.c_ulonglong), ("trace_ms", ctypes.c_double), ("ps_ms", ctypes.c_double),
+                ("depth_ms", ctypes.c_double), ("launches", ctypes.c_ulonglong), ("draws", ctypes.c_ulonglong)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class IrtpsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"irtps error {code}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                          f"g.build()'` (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i32, u32, u64, f32, dbl = (ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64,
+                                  ctypes.c_float, ctypes.c_double)
+    sig = {
+        "irtps_default_options": (None, [P]),
+        "irtps_create": (i32, [P, i32, i32, i32, i32, P, P, i32, i32, P]),
+        "irtps_set_stream": (i32, [P, P]),
+        "irtps_set_images": (i32, [P, P, i32, i32]),
+        "irtps_iterate": (i32, [P, i32, i32, i32, u64, P]),
+        "irtps_trace": (i32, [P, i32, i32, u64, u32, u32]),
+        "irtps_solve_normals": (i32, [P]),
+        "irtps_integrate": (i32, [P]),
+        "irtps_trace_pixels": (i32, [P, P, i32, i32, i32, u64, u32, u32, P, P]),
+        "irtps_set_state": (i32, [P, P, P, P]),
+        "irtps_set_indirect": (i32, [P, P]),
+        "irtps_render": (i32, [P, i32, i32, u64, f32, P, i32]),
+        "irtps_get_normals": (i32, [P, P, i32]),
+        "irtps_get_albedo": (i32, [P, P, i32]),
+        "irtps_get_depth": (i32, [P, P, i32]),
+        "irtps_get_indirect": (i32, [P, P, i32]),
+        "irtps_get_valid": (i32, [P, P, i32]),
+        "irtps_get_stats": (i32, [P, P]),
+        "irtps_probe_dirs": (i32, [i32, P, P, P, P]),
+        "irtps_probe_rays": (i32, [P, i32, P, P, P]),
+        "irtps_last_error": (ctypes.c_char_p, [P]),
+        "irtps_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _addr(a):
+    """Address of a numpy array (host), a torch tensor (data_ptr) or an int."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _check(handle, rc):
+    if rc != IRTPS_OK:
+        msg = _lib.irtps_last_error(handle).decode() if handle else ""
+        raise IrtpsError(rc, msg)
+
+
+# ---------------------------------------------------------------------------
+# C-ABI names, one to one
+# ---------------------------------------------------------------------------
+def irtps_default_options():
+    opt = irtps_options()
+    _lib.irtps_default_options(ctypes.byref(opt))
+    return opt
+
+
+def irtps_create(H, W, K, C, lights, env, opt=None):
+    """Returns an opaque handle (ctypes.c_void_p)."""
+    l = _host(lights, np.float32).reshape(-1, 3)
+    e = _host(env, np.float32)
+    EH, EW = e.shape[-2], e.shape[-1]
+    h = ctypes.c_void_p()
+    rc = _lib.irtps_create(ctypes.byref(h), H, W, K, C, _addr(l), _addr(e), EH, EW,
+                           ctypes.byref(opt) if opt is not None else None)
+    if rc != IRTPS_OK:
+        msg = _lib.irtps_last_error(h).decode() if h.value else ""
+        if h.value:
+            _lib.irtps_destroy(h)
+        raise IrtpsError(rc, msg)
+    return h
+
+
+def irtps_set_stream(h, stream):
+    _check(h, _lib.irtps_set_stream(h, ctypes.c_void_p(stream)))
+
+
+def irtps_set_images(h, images, dtype=IRTPS_F32, on_device=False):
+    if not on_device:
+        images = _host(images, np.float16 if dtype == IRTPS_F16 else np.float32)
+    _check(h, _lib.irtps_set_images(h, _addr(images), dtype, int(on_device)))
+
+
+def irtps_iterate(h, n_iter, spp, bounces, seed):
+    dh = ctypes.c_double(0.0)
+    _check(h, _lib.irtps_iterate(h, n_iter, spp, bounces, seed, ctypes.byref(dh)))
+    return dh.value
+
+
+def irtps_trace(h, spp, bounces, seed, iteration, stream_tag=0):
+    _check(h, _lib.irtps_trace(h, spp, bounces, seed, iteration & 0xFFFFFFFF, stream_tag))
+
+
+def irtps_solve_normals(h):
+    _check(h, _lib.irtps_solve_normals(h))
+
+
+def irtps_integrate(h):
+    _check(h, _lib.irtps_integrate(h))
+
+
+def irtps_trace_pixels(h, pixels, K, C, spp, bounces, seed, iteration, stream_tag=0, records=False):
+    pix = _host(pixels, np.int32)
+    out = np.zeros((K, C, pix.size), np.float32)
+    rec = np.zeros((pix.size, K, spp, bounces, 2), np.int32) if records else None
+    _check(h, _lib.irtps_trace_pixels(h, _addr(pix), pix.size, spp, bounces, seed, iteration & 0xFFFFFFFF,
+                                      stream_tag, _addr(out), _addr(rec)))
+    return out, rec
+
+
+def irtps_set_state(h, depth=None, normals=None, albedo=None):
+    d = None if depth is None else _host(depth, np.float32)
+    n = None if normals is None else _host(normals, np.float32)
+    a = None if albedo is None else _host(albedo, np.float32)
+    _check(h, _lib.irtps_set_state(h, _addr(d), _addr(n), _addr(a)))
+
+
+def irtps_set_indirect(h, indirect):
+    _check(h, _lib.irtps_set_indirect(h, _addr(_host(indirect, np.float32))))
+
+
+def irtps_render(h, shape, spp, bounces, seed, sigma, out=None):
+    """Host render unless `out` (a device tensor) is given."""
+    if out is None:
+        buf = np.zeros(shape, np.float32)
+        _check(h, _lib.irtps_render(h, spp, bounces, seed, sigma, _addr(buf), 0))
+        return buf
+    _check(h, _lib.irtps_render(h, spp, bounces, seed, sigma, _addr(out), 1))
+    return out
+
+
+def _get(fn, h, shape, dtype, out):
+    if out is None:
+        buf = np.zeros(shape, dtype)
+        _check(h, fn(h, _addr(buf), 0))
+        return buf
+    _check(h, fn(h, _addr(out), 1))
+    return out
+
+
+def irtps_get_normals(h, shape, out=None):
+    return _get(_lib.irtps_get_normals, h, shape, np.float32, out)
+
+
+def irtps_get_albedo(h, shape, out=None):
+    return _get(_lib.irtps_get_albedo, h, shape, np.float32, out)
+
+
+def irtps_get_depth(h, shape, out=None):
+    return _get(_lib.irtps_get_depth, h, shape, np.float32, out)
+
+
+def irtps_get_indirect(h, shape, out=None):
+    return _get(_lib.irtps_get_indirect, h, shape, np.float32, out)
+
+
+def irtps_get_valid(h, shape, out=None):
+    return _get(_lib.irtps_get_valid, h, shape, np.uint8, out)
+
+
+def irtps_get_stats(h):
+    s = irtps_stats()
+    _check(h, _lib.irtps_get_stats(h, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def irtps_probe_dirs(normals, x0, x1):
+    n = _host(normals, np.float32).reshape(-1, 3)
+    a = _host(x0, np.uint32)
+    b = _host(x1, np.uint32)
+    out = np.zeros_like(n)
+    rc = _lib.irtps_probe_dirs(n.shape[0], _addr(n), _addr(a), _addr(b), _addr(out))
+    if rc != IRTPS_OK:
+        raise IrtpsError(rc, "probe_dirs")
+    return out
+
+
+def irtps_probe_rays(h, rays):
+    r = _host(rays, np.float32).reshape(-1, 6)
+    t = np.zeros(r.shape[0], np.float32)
+    tri = np.zeros(r.shape[0], np.int32)
+    _check(h, _lib.irtps_probe_rays(h, r.shape[0], _addr(r), _addr(t), _addr(tri)))
+    return t, tri
+
+
+def irtps_last_error(h):
+    return _lib.irtps_last_error(h).decode()
+
+
+def irtps_destroy(h):
+    if h is not None and h.value:
+        _lib.irtps_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper (same calls, shapes remembered)
+# ---------------------------------------------------------------------------
+class Context:
+    """One IRT-PS object: H x W pixels, K lights, C channels (1 or 3)."""
+
+    def __init__(self, H, W, lights, env, opt=None):
+        lights = np.asarray(lights, np.float32).reshape(-1, 3)
+        env = np.asarray(env, np.float32)
+        self.H, self.W, self.K, self.C = H, W, lights.shape[0], env.shape[0]
+        self.h = irtps_create(H, W, self.K, self.C, lights, env, opt)
+
+    def close(self):
+        irtps_destroy(self.h)
+        self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) is not None:
+                self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        irtps_set_stream(self.h, stream)
+
+    def set_images(self, images, dtype=IRTPS_F32, on_device=False):
+        irtps_set_images(self.h, images, dtype, on_device)
+
+    def iterate(self, n_iter, spp, bounces, seed):
+        return irtps_iterate(self.h, n_iter, spp, bounces, seed)
+
+    def trace(self, spp, bounces, seed, iteration, stream_tag=0):
+        irtps_trace(self.h, spp, bounces, seed, iteration, stream_tag)
+
+    def solve_normals(self):
+        irtps_solve_normals(self.h)
+
+    def integrate(self):
+        irtps_integrate(self.h)
+
+    def trace_pixels(self, pixels, spp, bounces, seed, iteration, stream_tag=0, records=False):
+        return irtps_trace_pixels(self.h, pixels, self.K, self.C, spp, bounces, seed, iteration, stream_tag,
+                                  records)
+
+    def set_state(self, depth=None, normals=None, albedo=None):
+        irtps_set_state(self.h, depth, normals, albedo)
+
+    def set_indirect(self, indirect):
+        irtps_set_indirect(self.h, indirect)
+
+    def render(self, spp, bounces, seed, sigma, out=None):
+        return irtps_render(self.h, (self.K, self.C, self.H, self.W), spp, bounces, seed, sigma, out)
+
+    def normals(self, out=None):
+        return irtps_get_normals(self.h, (self.H, self.W, 4), out)
+
+    def albedo(self, out=None):
+        return irtps_get_albedo(self.h, (self.C, self.H, self.W), out)
+
+    def depth(self, out=None):
+        return irtps_get_depth(self.h, (self.H, self.W), out)
+
+    def indirect(self, out=None):
+        return irtps_get_indirect(self.h, (self.K, self.C, self.H, self.W), out)
+
+    def valid(self, out=None):
+        return irtps_get_valid(self.h, (self.H, self.W), out)
+
+    def stats(self):
+        return irtps_get_stats(self.h)
+
+    def probe_rays(self, rays):
+        return irtps_probe_rays(self.h, rays)

@@ -1,0 +1,77 @@
+"""GPU subtract + photometric stereo (Eq. 3-4) and depth integration against the oracle."""
+import numpy as np
+import pytest
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _images(oracle_mod, sc, spp=16, bounces=1, seed=3, sigma=0.002):
+    return oracle_mod.render(sc.depth, sc.normals, sc.albedo, sc.lights, sc.env, spp, bounces, seed, sigma)
+
+
+@pytest.mark.parametrize("case", ["bowl64", "mixed_45x38_c3", "mixed_20x9_c3_k9"])
+@pytest.mark.parametrize("f16", [False, True])
+def test_ps_stage(lib, oracle_mod, case, f16):
+    sc = {"bowl64": lambda: scenes.bowl_64(),
+          "mixed_45x38_c3": lambda: scenes.mixed(8, 45, 38, K=6, C=3),
+          "mixed_20x9_c3_k9": lambda: scenes.mixed(2, 20, 9, K=9, C=3)}[case]()
+    A0 = _images(oracle_mod, sc)
+    if f16:
+        A0 = A0.astype(np.float16).astype(np.float32)
+    K, C, H, W = A0.shape
+    P = H * W
+    rng = np.random.default_rng(1)
+    lbar = (rng.uniform(0.0, 0.3, (K, C, P))).astype(np.float32)
+    rho = (sc.albedo * rng.uniform(0.9, 1.1, sc.albedo.shape)).astype(np.float32)
+    with lib.Context(H, W, sc.lights, sc.env) as ctx:
+        ctx.set_images(A0.astype(np.float16) if f16 else A0, lib.IRTPS_F16 if f16 else lib.IRTPS_F32)
+        n0, v0 = ctx.normals(), ctx.valid()
+        ctx.set_state(albedo=rho)
+        ctx.set_indirect(lbar.reshape(K, C, H, W))
+        ctx.solve_normals()
+        n1, a1, v1 = ctx.normals(), ctx.albedo(), ctx.valid()
+    for (n, v, lb, r) in [(n0, v0, np.zeros_like(lbar), np.zeros((C, P))), (n1, v1, lbar, rho.reshape(C, P))]:
+        want_n, want_r, ok = oracle_mod.ps_step(A0, r, lb, sc.lights)
+        assert np.array_equal(v.ravel().astype(bool), ok)
+        err = oracle_mod.angular_error_deg(n[..., :3].reshape(-1, 3)[ok], want_n[ok])
+        assert err.max() < 1e-3, err.max()
+        assert np.all(n[..., :3].reshape(-1, 3)[~ok] == [0, 0, 1])
+    want_n, want_r, ok = oracle_mod.ps_step(A0, rho.reshape(C, P), lbar, sc.lights)
+    assert np.abs(a1.reshape(C, P) - want_r).max() < 1e-5 * max(1.0, want_r.max())
+    assert (~ok).sum() < P  # masked and valid pixels both present or all valid
+    assert n1[..., 3].reshape(-1)[ok].min() > 0
+
+
+@pytest.mark.parametrize("H,W", [(64, 64), (37, 53), (256, 256), (2, 5)])
+def test_integrate(lib, oracle_mod, H, W):
+    sc = scenes.mixed(H * 7 + W, H, W, K=3, C=1) if H > 2 else None
+    normals = sc.normals if sc is not None else scenes.normals_from_gradient(
+        np.array([[0.1, 0.2, 0.0, -0.1, 0.3], [0.0, -0.2, 0.1, 0.2, 0.0]]),
+        np.array([[0.3, 0.0, -0.1, 0.0, 0.1], [0.1, 0.1, 0.0, -0.3, 0.2]])).astype(np.float32)
+    lights = scenes.ring_lights(3, 45.0)
+    with lib.Context(H, W, lights, np.zeros((1, 2, 2), np.float32)) as ctx:
+        ctx.set_state(depth=np.zeros((H, W), np.float32), normals=normals)
+        ctx.integrate()
+        d = ctx.depth()
+        st = ctx.stats()
+    want = oracle_mod.poisson_solve(normals.astype(np.float64), 1.0 / W)
+    rng = max(np.ptp(want), 1e-12)
+    assert np.abs(d - want).max() <= 1e-4 * rng, (np.abs(d - want).max() / rng, st)
+    assert abs(float(d.astype(np.float64).mean())) < 1e-6 * rng + 1e-9
+    assert st["cg_rel_residual"] <= 1e-9
+
+
+def test_integrate_quadric_exact(lib, oracle_mod):
+    H, W = 96, 80
+    X, Y = scenes.grid(H, W)
+    f = 0.9 * (X ** 2 + Y ** 2) - 0.4 * X * Y + 0.2 * X
+    n = scenes.normals_from_gradient(1.8 * X - 0.4 * Y + 0.2, 1.8 * Y - 0.4 * X).astype(np.float32)
+    with lib.Context(H, W, scenes.ring_lights(3, 45.0), np.zeros((1, 2, 2), np.float32)) as ctx:
+        ctx.set_state(depth=np.zeros((H, W), np.float32), normals=n)
+        ctx.integrate()
+        d = ctx.depth()
+    want = f - f.mean()
+    # exact up to the float32 rounding of the normals and of the stored depth
+    assert np.abs(d - want).max() < 2e-5 * np.ptp(want)
