@@ -165,6 +165,28 @@ int irtps_get_stats(irtps_ctx *ctx, irtps_stats *out);
 int irtps_probe_dirs(int n, const float *normals, const uint32_t *x0, const uint32_t *x1, float *out);
 int irtps_probe_rays(irtps_ctx *ctx, int n, const float *rays, float *out_t, int32_t *out_tri);
 
+/* Depth integration without any device allocation.  The paper has no
+ * counterpart: this entry exists for callers that cannot allocate device memory
+ * when they need the surface (a host framework that owns the whole device pool
+ * through its own allocator, or a latency-critical loop that cannot accept the
+ * device-wide synchronisation of cudaMalloc / cudaFree).  It runs the same solve
+ * as irtps_integrate, with its working vectors in one file-scope device array
+ * that holds at most 512 x 512 = 262144 pixels (about 11 MB, kept by every GPU
+ * that loads the library until the process exits).
+ *   normals : device, H x W x 4 float (nx, ny, nz, unused), read only
+ *   depth   : device, H x W float; in: warm start, out: the surface, mean 0
+ *   nz_min, tol, max_iter: as irtps_options.nz_min, cg_tol, cg_max_iter
+ *   stream  : cudaStream_t to run on (NULL: the legacy default stream); the call
+ *             returns after the work on it has finished
+ * Returns IRTPS_EINVAL for H or W < 2, H*W > 262144 or bad tolerances,
+ * IRTPS_ENUMERIC if the residual stays above tol, IRTPS_ETIMEOUT if a grid
+ * barrier gave up, IRTPS_ECUDA on a CUDA failure.  The first call on a device
+ * looks up the array's device address (make it before any stream capture).  All
+ * calls share the array: calls that overlap on the GPU race and must not be
+ * issued. */
+int irtps_integrate_noalloc(const float *normals, int H, int W, float nz_min, double tol, int max_iter, float *depth,
+                            void *stream);
+
 const char *irtps_last_error(const irtps_ctx *ctx);
 void irtps_destroy(irtps_ctx *ctx);
 

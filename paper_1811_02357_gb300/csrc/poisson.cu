@@ -14,6 +14,7 @@
 // against cg_tol.  Reductions are two-stage and deterministic: each block writes
 // one partial, and every consumer block sums all partials in the same order.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "irtps_internal.h"
@@ -530,4 +531,130 @@ int depth_change(Ctx &c, double *dH_max, double *dH_rms) {
   return IRTPS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free depth solve.  Some callers cannot allocate device memory at
+// the moment they need a result: a host framework may own the whole device
+// pool through its own allocator, or a latency-critical loop may not accept the
+// device-wide synchronisation of cudaMalloc / cudaFree.  For them the solver's
+// working vectors live in one file-scope device array, sized for at most
+// kNoAllocMaxPixels pixels, that every GPU loading this library holds until the
+// process exits.  Every call shares it, so calls that overlap on the GPU race.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxPixels = 512 * 512;
+constexpr int kNoAllocMaxBlocks = 2048;
+constexpr size_t kNaX = 0;                                              // x: doubles
+constexpr size_t kNaB = kNaX + 8ull * kNoAllocMaxPixels;               // b: doubles
+constexpr size_t kNaR = kNaB + 8ull * kNoAllocMaxPixels;               // r: floats
+constexpr size_t kNaZ = kNaR + 4ull * kNoAllocMaxPixels;               // z: floats
+constexpr size_t kNaP = kNaZ + 4ull * kNoAllocMaxPixels;               // p: 2 x floats
+constexpr size_t kNaAp = kNaP + 8ull * kNoAllocMaxPixels;              // Ap and correction: 2 x floats
+constexpr size_t kNaPart = kNaAp + 8ull * kNoAllocMaxPixels;           // partials: doubles
+constexpr size_t kNaCtl = kNaPart + 8ull * kPartSlots * kNoAllocMaxBlocks;
+constexpr size_t kNaScal = kNaCtl + 256;                                // two scalar totals
+constexpr size_t kNaBytes = kNaScal + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// Sum of n partials into *out (one warp, fixed order).
+__global__ void k_total_to(const double *part, int n, double *out) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) v += part[i];
+  v = warp_sum(v);
+  if (threadIdx.x == 0) *out = v;
+}
+
+// Device address of the scratch array on the current device: looked up once per
+// device (the first call on a device does it) and cached.
+static unsigned char *noalloc_base() {
+  static std::mutex mu;
+  static unsigned char *base[64] = {nullptr};
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!base[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+    base[dev] = (unsigned char *)p;
+  }
+  return base[dev];
+}
+
+static int noalloc_read(cudaStream_t s, const double *part, int n, double *scal, double *out) {
+  k_total_to<<<1, 32, 0, s>>>(part, n, scal);
+  if (cudaGetLastError() != cudaSuccess) return IRTPS_ECUDA;
+  if (cudaMemcpyAsync(out, scal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return IRTPS_ECUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? IRTPS_OK : IRTPS_ECUDA;
+}
+
 }  // namespace irtps
+
+extern "C" int irtps_integrate_noalloc(const float *normals, int H, int W, float nz_min, double tol, int max_iter,
+                                       float *depth, void *stream) {
+  using namespace irtps;
+  if (!normals || !depth || H < 2 || W < 2 || (long long)H * W > kNoAllocMaxPixels || !(nz_min > 0.0f) ||
+      !(tol > 0.0) || max_iter < 0)
+    return IRTPS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char *base = noalloc_base();
+  if (!base) return IRTPS_ECUDA;
+  const int P = H * W;
+  int nb = std::min((P + kThreads - 1) / kThreads, cg_grid_limit());
+  nb = std::max(1, std::min(nb, kNoAllocMaxBlocks));
+  CG g;
+  g.H = H;
+  g.W = W;
+  g.P = P;
+  g.h = 1.0 / (double)W;
+  g.nz_min = nz_min;
+  g.nrm = reinterpret_cast<const float4 *>(normals);
+  g.depth = depth;
+  g.x = reinterpret_cast<double *>(base + kNaX);
+  g.b = reinterpret_cast<double *>(base + kNaB);
+  g.r = reinterpret_cast<float *>(base + kNaR);
+  g.z = reinterpret_cast<float *>(base + kNaZ);
+  g.p = reinterpret_cast<float *>(base + kNaP);
+  g.ap = reinterpret_cast<float *>(base + kNaAp);
+  g.part = reinterpret_cast<double *>(base + kNaPart);
+  g.stride = kNoAllocMaxBlocks;
+  g.nblk = nb;
+  CGCtl *ctl = reinterpret_cast<CGCtl *>(base + kNaCtl);
+  double *scal = reinterpret_cast<double *>(base + kNaScal);
+
+  k_rhs<<<nb, kThreads, 0, s>>>(g);
+  if (cudaGetLastError() != cudaSuccess) return IRTPS_ECUDA;
+  double bb = 0.0;
+  int rc = noalloc_read(s, g.part + S_BB * g.stride, nb, scal, &bb);
+  if (rc) return rc;
+  if (!std::isfinite(bb)) return IRTPS_ENUMERIC;
+  if (bb == 0.0) {
+    k_zero_depth<<<nb, kThreads, 0, s>>>(g);
+    if (cudaGetLastError() != cudaSuccess) return IRTPS_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? IRTPS_OK : IRTPS_ECUDA;
+  }
+  double bnorm = std::sqrt(bb);
+  k_load_x<<<nb, kThreads, 0, s>>>(g);
+  k_residual<<<nb, kThreads, 0, s>>>(g, S_RZ0);
+  if (cudaGetLastError() != cudaSuccess) return IRTPS_ECUDA;
+  double rr = 0.0;
+  rc = noalloc_read(s, g.part + S_RR * g.stride, nb, scal + 1, &rr);
+  if (rc) return rc;
+  double rel = std::sqrt(rr) / bnorm;
+  if (rel > tol) {
+    CGCtl h{0u, 0u, 0, 0, rel};  // barrier counters start at zero on every call
+    if (cudaMemcpyAsync(ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s) != cudaSuccess) return IRTPS_ECUDA;
+    int m = 50;
+    void *args[] = {(void *)&g, (void *)&ctl, (void *)&bnorm, (void *)&tol, (void *)&max_iter, (void *)&m};
+    if (cudaLaunchCooperativeKernel((const void *)k_cg_loop, dim3(nb), dim3(kThreads), args, 0, s) != cudaSuccess)
+      return IRTPS_ECUDA;
+    if (cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return IRTPS_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return IRTPS_ECUDA;
+    if (h.err) return IRTPS_ETIMEOUT;
+    rel = h.rel;
+  }
+  k_sum_x<<<nb, kThreads, 0, s>>>(g);
+  k_store_depth<<<nb, kThreads, 0, s>>>(g);
+  if (cudaGetLastError() != cudaSuccess) return IRTPS_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return IRTPS_ECUDA;
+  return (std::isfinite(rel) && rel <= tol) ? IRTPS_OK : IRTPS_ENUMERIC;
+}
+

@@ -32,7 +32,7 @@ EXPORTED = [
     "irtps_trace", "irtps_solve_normals", "irtps_integrate", "irtps_trace_pixels", "irtps_set_state",
     "irtps_set_indirect", "irtps_render", "irtps_get_normals", "irtps_get_albedo", "irtps_get_depth",
     "irtps_get_indirect", "irtps_get_valid", "irtps_get_stats", "irtps_probe_dirs", "irtps_probe_rays",
-    "irtps_last_error", "irtps_destroy",
+    "irtps_last_error", "irtps_destroy", "irtps_integrate_noalloc",
 ]
 
 
@@ -89,6 +89,7 @@ def _load():
         "irtps_probe_dirs": (i32, [i32, P, P, P, P]),
         "irtps_probe_rays": (i32, [P, i32, P, P, P]),
         "irtps_last_error": (ctypes.c_char_p, [P]),
+        "irtps_integrate_noalloc": (i32, [P, i32, i32, f32, dbl, i32, P, P]),
         "irtps_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -257,6 +258,15 @@ def irtps_probe_rays(h, rays):
     tri = np.zeros(r.shape[0], np.int32)
     _check(h, _lib.irtps_probe_rays(h, r.shape[0], _addr(r), _addr(t), _addr(tri)))
     return t, tri
+
+
+def irtps_integrate_noalloc(normals, depth, H, W, nz_min=0.05, tol=1e-9, max_iter=50000, stream=0):
+    """Allocation-free depth solve on device buffers: normals (H, W, 4) float32, depth (H, W) float32
+    (warm start in, surface out).  `stream` is a raw cudaStream_t value (0: legacy default stream)."""
+    rc = _lib.irtps_integrate_noalloc(_addr(normals), H, W, nz_min, tol, max_iter, _addr(depth),
+                                      ctypes.c_void_p(stream))
+    if rc != IRTPS_OK:
+        raise IrtpsError(rc, "integrate_noalloc")
 
 
 def irtps_last_error(h):
