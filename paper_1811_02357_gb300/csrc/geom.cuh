@@ -170,13 +170,18 @@ struct Work {
   uint32_t nodes = 0, tris = 0, draws = 0;
 };
 
+#ifndef IRTPS_CLIMB
+#define IRTPS_CLIMB 1
+#endif
+constexpr int kClimb = IRTPS_CLIMB;     // levels climbed after passing over a node
 constexpr float kHitMargin = 1e-4f;   // entry beyond best hit by this: stop
 constexpr float kCorner = 1e-5f;      // near-vertex crossing: test both side cells
 
 // Both triangles of cell (cy, cx).  This is the Moeller-Trumbore test above
 // written out for the cell's vertices, whose x and y are consecutive integers:
 // every product with an edge component of 0 or 1 is exact, so dropping it leaves
-// each remaining rounding, and hence every result bit, unchanged.
+// each remaining rounding, and hence every result bit, unchanged.  The
+// rejections are evaluated as one predicate per triangle (straight-line code).
 __device__ __forceinline__ void test_cell(const Field &f, int cy, int cx, F3 o, F3 d, float &bt, int &btri, Work &w) {
   w.tris += 2;
   const float *r0 = f.depth + (size_t)cy * f.W + cx;
@@ -186,68 +191,65 @@ __device__ __forceinline__ void test_cell(const Field &f, int cy, int cx, F3 o, 
   const F3 tv = {rsub(o.x, (float)cx), rsub(o.y, (float)cy), rsub(o.z, h00)};
   const float e11 = rsub(h11, h00);  // z of v11 - v0 (edge to the far corner)
   // T0 = (v00, v01, v11): e1 = (1, 0, h01 - h00), e2 = (1, 1, h11 - h00)
+  float t0;
+  bool hit0;
   {
     const float e1z = rsub(h01, h00);
     const F3 pv = {rsub(rmul(d.y, e11), d.z), rsub(d.z, rmul(d.x, e11)), rsub(d.x, d.y)};
     const float det = radd(pv.x, rmul(e1z, pv.z));
-    if (det != 0.0f) {
-      const float inv = __frcp_rn(det);
-      const float u = rmul(f3dot(tv, pv), inv);
-      if (!(u < 0.0f || u > 1.0f)) {
-        const F3 qv = {rmul(tv.y, e1z), rsub(tv.z, rmul(tv.x, e1z)), -tv.y};
-        const float v = rmul(f3dot(d, qv), inv);
-        if (!(v < 0.0f || radd(u, v) > 1.0f)) {
-          const float t = rmul(radd(radd(qv.x, qv.y), rmul(e11, qv.z)), inv);
-          if (t > 0.0f && (btri < 0 || t < bt || (t == bt && base < btri))) {
-            bt = t;
-            btri = base;
-          }
-        }
-      }
-    }
+    const float inv = __frcp_rn(det);
+    const float u = rmul(f3dot(tv, pv), inv);
+    const F3 qv = {rmul(tv.y, e1z), rsub(tv.z, rmul(tv.x, e1z)), -tv.y};
+    const float v = rmul(f3dot(d, qv), inv);
+    t0 = rmul(radd(radd(qv.x, qv.y), rmul(e11, qv.z)), inv);
+    hit0 = det != 0.0f && u >= 0.0f && u <= 1.0f && v >= 0.0f && radd(u, v) <= 1.0f && t0 > 0.0f;
   }
   // T1 = (v00, v11, v10): e1 = (1, 1, h11 - h00), e2 = (0, 1, h10 - h00)
+  float t1;
+  bool hit1;
   {
     const float e2z = rsub(h10, h00);
     const F3 pv = {rsub(rmul(d.y, e2z), d.z), -rmul(d.x, e2z), d.x};
     const float det = radd(radd(pv.x, pv.y), rmul(e11, pv.z));
-    if (det != 0.0f) {
-      const float inv = __frcp_rn(det);
-      const float u = rmul(f3dot(tv, pv), inv);
-      if (!(u < 0.0f || u > 1.0f)) {
-        const F3 qv = {rsub(rmul(tv.y, e11), tv.z), rsub(tv.z, rmul(tv.x, e11)), rsub(tv.x, tv.y)};
-        const float v = rmul(f3dot(d, qv), inv);
-        if (!(v < 0.0f || radd(u, v) > 1.0f)) {
-          const float t = rmul(radd(qv.y, rmul(e2z, qv.z)), inv);
-          if (t > 0.0f && (btri < 0 || t < bt || (t == bt && base + 1 < btri))) {
-            bt = t;
-            btri = base + 1;
-          }
-        }
-      }
-    }
+    const float inv = __frcp_rn(det);
+    const float u = rmul(f3dot(tv, pv), inv);
+    const F3 qv = {rsub(rmul(tv.y, e11), tv.z), rsub(tv.z, rmul(tv.x, e11)), rsub(tv.x, tv.y)};
+    const float v = rmul(f3dot(d, qv), inv);
+    t1 = rmul(radd(qv.y, rmul(e2z, qv.z)), inv);
+    hit1 = det != 0.0f && u >= 0.0f && u <= 1.0f && v >= 0.0f && radd(u, v) <= 1.0f && t1 > 0.0f;
+  }
+  if (hit0 && (btri < 0 || t0 < bt || (t0 == bt && base < btri))) {
+    bt = t0;
+    btri = base;
+  }
+  if (hit1 && (btri < 0 || t1 < bt || (t1 == bt && base + 1 < btri))) {
+    bt = t1;
+    btri = base + 1;
   }
 }
 
 // Cell index along one axis at which a cell walk stands when the other axis is
 // crossed at parameter t: the first index c (from `cur`, moving by `s`, inside
 // [lo, hi)) whose own exit parameter e(c) = (edge(c) - o) * inv is >= t, plus one
-// step when e(c) == t (the walk then steps diagonally).  e(c) is monotone in c,
-// so a floor estimate corrected by at most a few probes gives the walk's answer.
+// step when e(c) == t (the walk then steps diagonally).  e(c) is monotone in c
+// and differs from the exact crossing only by rounding (far below one cell), so
+// the floor of the crossing coordinate is the answer or its neighbour: one probe
+// on each side settles it.
 __device__ __forceinline__ int cell_at(float o, float d, float inv, int s, int cur, int lo, int hi, float t) {
   const int cmin = s > 0 ? cur : lo;
   const int cmax = s > 0 ? hi - 1 : cur;
   int c = (int)floorf(radd(o, rmul(t, d)));
   c = min(max(c, cmin), cmax);
-  if (s > 0) {
-    while (c > cmin && rmul(rsub((float)c, o), inv) >= t) --c;          // e(c-1) >= t
-    while (c < cmax && rmul(rsub((float)(c + 1), o), inv) < t) ++c;     // e(c) < t
-    if (rmul(rsub((float)(c + 1), o), inv) == t) ++c;
-  } else {
-    while (c < cmax && rmul(rsub((float)(c + 1), o), inv) >= t) ++c;    // e(c+1) >= t
-    while (c > cmin && rmul(rsub((float)c, o), inv) < t) --c;           // e(c) < t
-    if (rmul(rsub((float)c, o), inv) == t) --c;
+  // exit parameter of cell c along the direction of travel: edge c+1 (s > 0) or c (s < 0)
+  const int up = s > 0 ? 1 : 0;
+  const float e_c = rmul(rsub((float)(c + up), o), inv);
+  const float e_back = rmul(rsub((float)(c + up - s), o), inv);  // e of the cell behind c
+  if (c != (s > 0 ? cmin : cmax) && e_back >= t) {
+    c -= s;
+  } else if (c != (s > 0 ? cmax : cmin) && e_c < t) {
+    c += s;
   }
+  if (rmul(rsub((float)(c + up), o), inv) == t) c += s;
   return c;
 }
 
@@ -261,20 +263,26 @@ __device__ __forceinline__ int cell_at(float o, float d, float inv, int s, int c
 struct Walker {
   F3 o, d;
   float ix, iy;
-  int cx0, cy0;       // start cell of walk 0
   int cx, cy, lv;
   float t_entry;
   float bt;
   int btri;
-  int8_t nx, ny, wi;  // walk multiplicity in x and y, current walk index
-  bool any;
+  int flags;  // bit 0: any-hit; bits 1, 2: a second walk in x, in y; bits 3-4: current walk index
 };
 
-__device__ __forceinline__ void walker_begin_walk(Walker &m) {
-  m.cx = m.cx0 - (m.wi % m.nx);
-  m.cy = m.cy0 - (m.wi / m.nx);
+// Start cell of walk `wi`: the cell holding the origin, on the side the ray moves
+// toward when the origin is on a grid line, shifted back by one column / row for
+// the second walk of a ray that runs exactly along that grid line.
+__device__ __forceinline__ void walker_begin_walk(Walker &m, int wi) {
+  int cx = (int)floorf(m.o.x), cy = (int)floorf(m.o.y);
+  if ((float)cx == m.o.x && m.d.x < 0.0f) --cx;
+  if ((float)cy == m.o.y && m.d.y < 0.0f) --cy;
+  const int nx = (m.flags & 2) ? 2 : 1;
+  m.cx = cx - (wi % nx);
+  m.cy = cy - (wi / nx);
   m.lv = 0;
   m.t_entry = 0.0f;
+  m.flags = (m.flags & 7) | (wi << 3);
 }
 
 __device__ __forceinline__ void walker_init(Walker &m, F3 o, F3 d, bool any) {
@@ -282,19 +290,11 @@ __device__ __forceinline__ void walker_init(Walker &m, F3 o, F3 d, bool any) {
   m.d = d;
   m.ix = __frcp_rn(d.x);
   m.iy = __frcp_rn(d.y);
-  int cx = (int)floorf(o.x), cy = (int)floorf(o.y);
-  const bool on_x = (float)cx == o.x, on_y = (float)cy == o.y;
-  if (on_x && d.x < 0.0f) --cx;
-  if (on_y && d.y < 0.0f) --cy;
-  m.cx0 = cx;
-  m.cy0 = cy;
-  m.nx = (on_x && d.x == 0.0f) ? 2 : 1;
-  m.ny = (on_y && d.y == 0.0f) ? 2 : 1;
-  m.wi = 0;
+  const bool on_x = floorf(o.x) == o.x, on_y = floorf(o.y) == o.y;
+  m.flags = (any ? 1 : 0) | ((on_x && d.x == 0.0f) ? 2 : 0) | ((on_y && d.y == 0.0f) ? 4 : 0);
   m.bt = __int_as_float(0x7f800000);
   m.btri = -1;
-  m.any = any;
-  walker_begin_walk(m);
+  walker_begin_walk(m, 0);
 }
 
 // The march advances in two kinds of steps.  A node step examines the pyramid
@@ -307,9 +307,11 @@ __device__ __forceinline__ void walker_init(Walker &m, F3 o, F3 d, bool any) {
 // Bookkeeping at the start of every step: ends the current walk (and the march,
 // or moves to the next walk of a grid-line ray).  Returns true when the march is over.
 __device__ __forceinline__ bool walker_finish_walk(Walker &m) {
-  if (m.any && m.btri >= 0) return true;
-  if (++m.wi < m.nx * m.ny) {
-    walker_begin_walk(m);
+  if ((m.flags & 1) && m.btri >= 0) return true;
+  const int wi = (m.flags >> 3) + 1;
+  const int walks = ((m.flags & 2) ? 2 : 1) * ((m.flags & 4) ? 2 : 1);
+  if (wi < walks) {
+    walker_begin_walk(m, wi);
     return false;
   }
   return true;
@@ -330,14 +332,16 @@ __device__ __forceinline__ bool walker_node_step(Walker &m, const Field &f, cons
   const int sx = m.d.x > 0.0f ? 1 : (m.d.x < 0.0f ? -1 : 0);
   const int sy = m.d.y > 0.0f ? 1 : (m.d.y < 0.0f ? -1 : 0);
   const int lv = m.lv;
-  const int X0 = (m.cx >> lv) << lv, Y0 = (m.cy >> lv) << lv;
+  const int nx = m.cx >> lv, ny = m.cy >> lv;
+  const int X0 = nx << lv, Y0 = ny << lv;
   const int X1 = min(X0 + (1 << lv), f.Wc), Y1 = min(Y0 + (1 << lv), f.Hc);
-  const float tX = sx > 0 ? rmul(rsub((float)X1, m.o.x), m.ix) : (sx < 0 ? rmul(rsub((float)X0, m.o.x), m.ix) : inf);
-  const float tY = sy > 0 ? rmul(rsub((float)Y1, m.o.y), m.iy) : (sy < 0 ? rmul(rsub((float)Y0, m.o.y), m.iy) : inf);
-  const float t_exit = fminf(tX, tY);
-  const float zlow = fmaf(m.d.z >= 0.0f ? m.t_entry : t_exit, m.d.z, m.o.z);
-  const float nmax = __ldg(f.pmax + lt.off[lv] + (m.cy >> lv) * lt.lw[lv] + (m.cx >> lv));
+  const float nmax = __ldg(f.pmax + lt.off[lv] + ny * lt.lw[lv] + nx);
   ++w.nodes;
+  const float tX = sx != 0 ? rmul(rsub((float)(sx > 0 ? X1 : X0), m.o.x), m.ix) : inf;
+  const float tY = sy != 0 ? rmul(rsub((float)(sy > 0 ? Y1 : Y0), m.o.y), m.iy) : inf;
+  const float t_exit = fminf(tX, tY);
+  // lowest height of the ray over the node: at entry when rising, else at exit
+  const float zlow = fmaf(m.d.z >= 0.0f ? m.t_entry : t_exit, m.d.z, m.o.z);
   if (zlow > nmax + f.dz) {
     if (t_exit == inf) return walker_finish_walk(m);  // vertical ray above everything below it
     if (tX < tY) {
@@ -353,7 +357,7 @@ __device__ __forceinline__ bool walker_node_step(Walker &m, const Field &f, cons
       m.cy = sy > 0 ? Y1 : Y0 - 1;
       m.t_entry = tX;
     }
-    if (lv + 1 < f.levels) m.lv = lv + 1;
+    m.lv = min(lv + kClimb, f.levels - 1);
   } else if (lv > 0) {
     m.lv = lv - 1;
   } else {
@@ -378,7 +382,7 @@ __device__ __forceinline__ bool walker_leaf_step(Walker &m, const Field &f, Work
     if (m.cx + sx >= 0 && m.cx + sx < f.Wc) test_cell(f, m.cy, m.cx + sx, m.o, m.d, m.bt, m.btri, w);
     if (m.cy + sy >= 0 && m.cy + sy < f.Hc) test_cell(f, m.cy + sy, m.cx, m.o, m.d, m.bt, m.btri, w);
   }
-  if (m.any && m.btri >= 0) return true;
+  if ((m.flags & 1) && m.btri >= 0) return true;
   if (tx == inf && ty == inf) return walker_finish_walk(m);
   if (tx < ty) {
     m.cx += sx;

@@ -25,7 +25,13 @@ enum Slot { S_BB = 0, S_PAP = 1, S_RZ0 = 2, S_RZ1 = 3, S_RR = 4, S_SUMX = 5, S_D
             S_HMIN = 9, S_RZREF = 10 };
 static_assert(S_RZREF < kPartSlots, "partial slots");
 
-constexpr int kThreads = 256;
+#ifndef IRTPS_CG_THREADS
+#define IRTPS_CG_THREADS 256
+#endif
+#ifndef IRTPS_CG_BLOCKS_PER_SM
+#define IRTPS_CG_BLOCKS_PER_SM 2
+#endif
+constexpr int kThreads = IRTPS_CG_THREADS;
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -103,7 +109,7 @@ __device__ __forceinline__ void slopes(const float4 *nrm, size_t p, float nz_min
 
 // b = D^T g (FP64) and |b|^2 partials.
 __global__ void __launch_bounds__(kThreads) k_rhs(const CG g) {
-  __shared__ double sh[33];
+  __shared__ double sh[kThreads / 32 + 1 > 33 ? kThreads / 32 + 1 : 33];
   double bb = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
     const int i = p / g.W, j = p - i * g.W;
@@ -127,7 +133,7 @@ __global__ void __launch_bounds__(kThreads) k_load_x(const CG g) {
 
 // True residual r = b - A x in FP64 (stored FP32), z = r / deg, partials of r.z and |r|^2 (FP64).
 __global__ void __launch_bounds__(kThreads) k_residual(const CG g, int rz_slot) {
-  __shared__ double sh[33];
+  __shared__ double sh[kThreads / 32 + 1 > 33 ? kThreads / 32 + 1 : 33];
   double rz = 0.0, rr = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
     const int i = p / g.W, j = p - i * g.W;
@@ -233,7 +239,7 @@ __device__ __forceinline__ float inv_degree(int i, int j, int H, int W) {
 // so takes the same decisions.
 __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, double bnorm, double tol,
                                                       int max_iter, int check) {
-  __shared__ double sh[33];
+  __shared__ double sh[kThreads / 32 + 1 > 33 ? kThreads / 32 + 1 : 33];
   __shared__ float shf[33];
   __shared__ float s_ab[2];
   __shared__ int s_frozen;
@@ -343,7 +349,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, do
 }
 
 __global__ void __launch_bounds__(kThreads) k_sum_x(const CG g) {
-  __shared__ double sh[33];
+  __shared__ double sh[kThreads / 32 + 1 > 33 ? kThreads / 32 + 1 : 33];
   double s = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) s += g.x[p];
   s = block_reduce<false>(s, sh);
@@ -351,7 +357,7 @@ __global__ void __launch_bounds__(kThreads) k_sum_x(const CG g) {
 }
 
 __global__ void __launch_bounds__(kThreads) k_store_depth(const CG g) {
-  __shared__ double sh[33];
+  __shared__ double sh[kThreads / 32 + 1 > 33 ? kThreads / 32 + 1 : 33];
   const double mean = total(g.part + S_SUMX * g.stride, g.nblk, sh) / (double)g.P;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x)
     g.depth[p] = (float)(g.x[p] - mean);
@@ -363,7 +369,7 @@ __global__ void __launch_bounds__(kThreads) k_zero_depth(const CG g) {
 
 // D_H partials: max |H_new - H_old|, sum (H_new - H_old)^2, max H_new, -min H_new.
 __global__ void __launch_bounds__(kThreads) k_depth_change(const CG g, const float *old) {
-  __shared__ double sh[33];
+  __shared__ double sh[kThreads / 32 + 1 > 33 ? kThreads / 32 + 1 : 33];
   double dmax = 0.0, dsq = 0.0, hmax = -INFINITY, hmin = -INFINITY;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
     const double a = g.depth[p], d = a - (double)old[p];
@@ -389,7 +395,7 @@ int cg_grid_limit() {
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_loop, kThreads, 0) != cudaSuccess) return 1;
-  per = per < 2 ? per : 2;
+  per = per < IRTPS_CG_BLOCKS_PER_SM ? per : IRTPS_CG_BLOCKS_PER_SM;
   return per * sms > 0 ? per * sms : 1;
 }
 

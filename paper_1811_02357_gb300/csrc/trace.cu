@@ -131,7 +131,7 @@ struct TraceArgs {
 };
 
 #ifndef IRTPS_TRACE_MINB
-#define IRTPS_TRACE_MINB 12
+#define IRTPS_TRACE_MINB 10
 #endif
 #ifndef IRTPS_MARCH_KEEP
 #define IRTPS_MARCH_KEEP 3
@@ -157,17 +157,20 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
   const int p = alive ? (a.pixels ? a.pixels[ip] : ip) : 0;
   const int W = a.f.W, H = a.f.H;
   const size_t P = (size_t)H * W;
-  const int pi = p / W, pj = p - pi * W;
-  const F3 org0 = {(float)pj, (float)pi, radd(__ldg(a.f.depth + p), a.eps)};
-  const float3 l3 = a.light[k];
-  const F3 l = {l3.x, l3.y, l3.z};
-  const F3 lg = {rmul(l.x, a.Wf), rmul(l.y, a.Wf), l.z};
+  // the pixel's own vertex, lifted: origin of every primary ray of this lane
+  auto pixel_origin = [&]() -> F3 {
+    const int pi = p / W, pj = p - pi * W;
+    return F3{(float)pj, (float)pi, radd(__ldg(a.f.depth + p), a.eps)};
+  };
+  auto light = [&]() -> F3 {
+    const float3 l3 = a.light[k];
+    return F3{l3.x, l3.y, l3.z};
+  };
   const int budget0 = 8 * (a.f.Wc + a.f.Hc + 8) * (a.f.levels + 1);
 
   int phase = alive ? PH_SETUP : PH_DONE;
-  int s = 0, b = 1, npix = p, qp = 0, budget = budget0;
+  int s = 0, b = 1, qp = 0, budget = budget0;
   bool shadow = false;
-  F3 org = org0;
   float cosv = 0.0f;
   float thr[C], acc[C], sum[C], comp[C];
 #pragma unroll
@@ -197,18 +200,16 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
     }
     ++s;
     b = 1;
-    org = org0;
-    npix = p;
     budget = budget0;
     phase = PH_SETUP;
   };
-  auto continue_path = [&](int q, F3 from) {
+  // after a hit at pixel q (qp) the next bounce starts from the lifted hit point,
+  // which the walker keeps as its origin m.o until the next set-up
+  auto continue_path = [&](int q) {
 #pragma unroll
     for (int c = 0; c < C; ++c) thr[c] *= __ldg(a.albedo + c * P + q);
     if (b < a.bounces) {
       ++b;
-      org = from;
-      npix = q;
       phase = PH_SETUP;
     } else {
       end_sample();
@@ -227,7 +228,10 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
         }
         const uint4 x = philox4x32_10(
             make_uint4((uint32_t)p, (uint32_t)s, ((uint32_t)k << 8) | ((uint32_t)b << 4) | a.stream, a.iter), a.key);
-        const float4 n4 = __ldg(a.nrm + npix);
+        // bounce 1 leaves the pixel's own vertex about its normal; later bounces the
+        // previous hit point (m.o) about the hit pixel's normal
+        const F3 org = b == 1 ? pixel_origin() : m.o;
+        const float4 n4 = __ldg(a.nrm + (b == 1 ? p : qp));
         const F3 dw = cosine_dir(F3{n4.x, n4.y, n4.z}, x.x, x.y);
         walker_init(m, org, F3{rmul(dw.x, a.Wf), rmul(dw.y, a.Wf), dw.z}, false);
         shadow = false;
@@ -236,7 +240,8 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
         phase = PH_MARCH;
       }
     }
-    if (__all_sync(0xffffffffu, phase == PH_DONE)) break;
+    const unsigned live = __ballot_sync(0xffffffffu, phase != PH_DONE);  // no lane finishes inside the march loop
+    if (live == 0u) break;
     // ---- march while enough of the live lanes are marching; node steps every
     // iteration, leaf steps once enough marching lanes wait for one ----
     while (true) {
@@ -257,7 +262,6 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
         phase = PH_RESOLVE;
       }
       const unsigned marching = __ballot_sync(0xffffffffu, phase == PH_MARCH);
-      const unsigned live = __ballot_sync(0xffffffffu, phase != PH_DONE);
       if (marching == 0u || kMarchKeep * __popc(marching) <= __popc(live)) break;
     }
     // ---- resolve finished segments ----
@@ -269,7 +273,7 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
 #pragma unroll
           for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * __ldg(a.albedo + c * P + qp), cosv, acc[c]);
         }
-        continue_path(qp, org);
+        continue_path(qp);
       } else if (m.btri < 0) {
         // escaped: environment radiance along the (world) direction
         const F3 dw = {m.d.x / a.Wf, m.d.y / a.Wf, m.d.z};
@@ -295,22 +299,24 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
           r[0] = qp;
           r[1] = -1;
         }
+        const F3 l = light();
         if (f3dot(nq, l) > 0.0f) {
           cosv = fmaxf(0.0f, nq.x * l.x + nq.y * l.y + nq.z * l.z);
           if (a.shadow) {
-            walker_init(m, o2, lg, true);
+            walker_init(m, o2, F3{rmul(l.x, a.Wf), rmul(l.y, a.Wf), l.z}, true);
             shadow = true;
-            org = o2;
             ++segs;
             phase = PH_MARCH;
           } else {
             if (a.rec) rec_slot(b)[1] = 1;
 #pragma unroll
             for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * __ldg(a.albedo + c * P + qp), cosv, acc[c]);
-            continue_path(qp, o2);
+            m.o = o2;
+            continue_path(qp);
           }
         } else {
-          continue_path(qp, o2);
+          m.o = o2;
+          continue_path(qp);
         }
       }
     }
