@@ -243,6 +243,7 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "create: events"));
   }
   c.cg_blocks = (int)std::min<size_t>((P + 255) / 256, (size_t)irtps::cg_grid_limit());
+  c.trace_blocks = irtps::trace_grid_limit(C);
   c.part_stride = c.cg_blocks;
   if ((rc = dalloc(c, &c.env, (size_t)C * EH * EW, "environment")) ||
       (rc = dalloc(c, (float **)&c.images, (size_t)K * C * P, "images")) ||

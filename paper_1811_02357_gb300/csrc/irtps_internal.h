@@ -41,6 +41,7 @@ struct Ctx {
   uint8_t *valid = nullptr;       // H*W, 1 = normal solved
   float *pmin = nullptr, *pmax = nullptr;  // pyramid, all levels
   int levels = 0;
+  int trace_blocks = 0;           // resident blocks of the persistent trace grid (0: one lane per item)
   int off[kMaxLevels] = {0}, lw[kMaxLevels] = {0}, lh[kMaxLevels] = {0};
   float zmax = 0.0f;              // host copy of the top pyramid node
   // depth solve
@@ -90,6 +91,7 @@ cudaError_t build_pyramid(Ctx &c);
 cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
                          uint32_t iter, uint32_t stream, float *out, int32_t *rec);
 cudaError_t launch_render(Ctx &c, uint64_t seed, float sigma, const float *lbar, float *out);
+int trace_grid_limit(int C);  // resident blocks of the trace kernel, 0 if unknown
 cudaError_t launch_probe_dirs(cudaStream_t s, int n, const float *normals, const uint32_t *x0, const uint32_t *x1,
                               float *out);
 cudaError_t launch_probe_rays(Ctx &c, int n, const float *rays, float *t_out, int32_t *tri_out, int *overflow);

@@ -127,11 +127,12 @@ struct TraceArgs {
   float *out;             // K*C*n_pix
   int32_t *rec;           // optional n_pix*K*spp*B*2
   unsigned long long *counts;  // {unused, segments, walk overflows, node visits, triangle tests, draws}
+  unsigned *next_item;         // work-item counter, zero before the launch
   float3 light[kMaxLights];
 };
 
 #ifndef IRTPS_TRACE_MINB
-#define IRTPS_TRACE_MINB 10
+#define IRTPS_TRACE_MINB 8
 #endif
 #ifndef IRTPS_MARCH_KEEP
 #define IRTPS_MARCH_KEEP 3
@@ -150,11 +151,21 @@ template <int C>
 __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const TraceArgs a) {
   __shared__ LevelTable lt;
   load_levels(a.f, &lt);
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool alive = idx < a.n_pix * a.K;
-  const int k = alive ? idx / a.n_pix : 0;
-  const int ip = alive ? idx - k * a.n_pix : 0;
-  const int p = alive ? (a.pixels ? a.pixels[ip] : ip) : 0;
+  // Work items are (light, pixel) pairs, item = k * n_pix + ip.  Each lane starts
+  // with the item of its global index and, when done, takes the next unclaimed
+  // item from a counter (claimed a warp at a time), so that no lane idles while
+  // items remain.  An item is always traced by one lane, samples in order.
+  const int n_items = a.n_pix * a.K;
+  int item = blockIdx.x * blockDim.x + threadIdx.x;
+  int k = 0, ip = 0, p = 0;
+  auto take = [&](int it) {
+    item = it;
+    k = it / a.n_pix;
+    ip = it - k * a.n_pix;
+    p = a.pixels ? a.pixels[ip] : ip;
+  };
+  const bool alive = item < n_items;
+  if (alive) take(item);
   const int W = a.f.W, H = a.f.H;
   const size_t P = (size_t)H * W;
   // the pixel's own vertex, lifted: origin of every primary ray of this lane
@@ -217,11 +228,38 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
   };
 
   while (true) {
+    // ---- finished items: store the mean and claim the next item ----
+    const bool item_done = phase == PH_SETUP && s >= a.spp;
+    const unsigned need = __ballot_sync(0xffffffffu, item_done);
+    if (need) {
+      if (item_done) {
+        const float inv = 1.0f / (float)a.spp;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          a.out[((size_t)k * C + c) * a.n_pix + ip] = sum[c] * inv;
+          sum[c] = comp[c] = 0.0f;
+        }
+      }
+      const int lane = threadIdx.x & 31;
+      const int leader = __ffs(need) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(a.next_item, (unsigned)__popc(need));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (item_done) {
+        const unsigned mine = base + (unsigned)__popc(need & ((1u << lane) - 1u));
+        if (mine < (unsigned)n_items) {
+          take((int)mine);
+          s = 0;
+          b = 1;
+          budget = budget0;
+        } else {
+          phase = PH_DONE;
+        }
+      }
+    }
     // ---- set up the next primary or bounce segment ----
     if (phase == PH_SETUP) {
-      if (s >= a.spp) {
-        phase = PH_DONE;
-      } else {
+      {
         if (a.rec && b == 1) {
           int32_t *r = rec_slot(1);
           for (int j = 0; j < 2 * a.bounces; ++j) r[j] = -2;
@@ -321,11 +359,6 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
       }
     }
   }
-  if (alive) {
-    const float inv = 1.0f / (float)a.spp;
-#pragma unroll
-    for (int c = 0; c < C; ++c) a.out[((size_t)k * C + c) * a.n_pix + ip] = sum[c] * inv;
-  }
   // counters: warp sums, one atomic per warp and counter
   unsigned long long sg = segs, ov = (unsigned)overflow, nv = w.nodes, tt = w.tris, dr = w.draws;
   for (int o = 16; o > 0; o >>= 1) {
@@ -374,7 +407,14 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
   a.rec = rec;
   const long long n = (long long)n_pix * c.K;
   const int threads = kTraceThreads;
-  const long long blocks = (n + threads - 1) / threads;
+  // a persistent grid: as many blocks as stay resident, each lane claiming items until none remain
+  long long blocks = (n + threads - 1) / threads;
+  if (c.trace_blocks > 0 && blocks > c.trace_blocks) blocks = c.trace_blocks;
+  a.next_item = reinterpret_cast<unsigned *>(c.counts);  // slot 0, zeroed with the counters
+  const unsigned first_free = (unsigned)(blocks * threads);   // items taken by the lanes' start indices
+  if (cudaMemcpyAsync(a.next_item, &first_free, sizeof(unsigned), cudaMemcpyHostToDevice, c.stream) != cudaSuccess)
+    return cudaGetLastError();
+  if (cudaStreamSynchronize(c.stream) != cudaSuccess) return cudaGetLastError();
   ++c.stats.launches;
   if (c.C == 1)
     k_trace<1><<<(unsigned)blocks, threads, 0, c.stream>>>(a);
@@ -427,6 +467,17 @@ __global__ void k_render(const TraceArgs a, const float *__restrict__ lbar, floa
     const size_t o = ((size_t)k * C + c) * P + p;
     out[o] = rho * cosv + rho * lbar[o] + sigma * z;
   }
+}
+
+// Resident blocks of the trace kernel for C channels (the persistent grid size).
+int trace_grid_limit(int C) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  const cudaError_t e = C == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<1>, kTraceThreads, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<3>, kTraceThreads, 0);
+  if (e != cudaSuccess) return 0;
+  return per * sms;
 }
 
 cudaError_t launch_render(Ctx &c, uint64_t seed, float sigma, const float *lbar, float *out) {
