@@ -245,10 +245,11 @@ def noise(H, W, C, K, seed, obj=0):
 
 
 def render(depth, normals, albedo, lights, env, spp, bounces, seed, sigma, *, shadow_rays=True,
-           fp32=True, threads=0):
+           fp32=True, threads=0, indirect=True):
     """Stage-0 input images A0 (K, C, H, W) float32 of a ground-truth scene:
     A0 = rho * max(0, n.l_k) * V_k + rho * Lbar_gt + sigma * N(0, 1), with Lbar_gt
-    traced on the ground truth with stream 1 and iteration 0xFFFFFFFF."""
+    traced on the ground truth with stream 1 and iteration 0xFFFFFFFF
+    (indirect=False: the direct term and the noise only)."""
     d = np.asarray(depth, np.float32)
     H, W = d.shape
     a = np.asarray(albedo, np.float32)
@@ -256,8 +257,11 @@ def render(depth, normals, albedo, lights, env, spp, bounces, seed, sigma, *, sh
     n = np.asarray(normals, np.float32)
     l = np.asarray(lights, np.float32).reshape(-1, 3)
     K = l.shape[0]
-    lbar, _, _ = trace(d, n, a, l, env, spp, bounces, seed, FORWARD_ITER, stream=1,
-                       shadow_rays=shadow_rays, fp32=fp32, threads=threads)
+    if indirect:
+        lbar, _, _ = trace(d, n, a, l, env, spp, bounces, seed, FORWARD_ITER, stream=1,
+                           shadow_rays=shadow_rays, fp32=fp32, threads=threads)
+    else:
+        lbar = np.zeros((K, C, H * W))
     vis = pixel_visibility(d, n, l, fp32=fp32) if shadow_rays else None
     n64 = n.reshape(-1, 3).astype(np.float64)
     cos = np.maximum(0.0, n64 @ l.astype(np.float64).T).T  # (K, P)

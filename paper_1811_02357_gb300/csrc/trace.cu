@@ -135,10 +135,13 @@ struct TraceArgs {
 #define IRTPS_TRACE_MINB 8
 #endif
 #ifndef IRTPS_MARCH_KEEP
-#define IRTPS_MARCH_KEEP 3
+#define IRTPS_MARCH_KEEP 2
 #endif
 #ifndef IRTPS_LEAF_BATCH
 #define IRTPS_LEAF_BATCH 4
+#endif
+#ifndef IRTPS_LEAF_MODE
+#define IRTPS_LEAF_MODE 0
 #endif
 constexpr int kTraceThreads = 128;
 // leave the march loop when marching lanes <= live lanes / kMarchKeep
@@ -283,6 +286,7 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
     // ---- march while enough of the live lanes are marching; node steps every
     // iteration, leaf steps once enough marching lanes wait for one ----
     while (true) {
+#if IRTPS_LEAF_MODE == 0
       if (phase == PH_MARCH && !at_leaf) {
         if (walker_node_step(m, a.f, lt, w, at_leaf)) phase = PH_RESOLVE;
       }
@@ -294,6 +298,19 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
           if (walker_leaf_step(m, a.f, w)) phase = PH_RESOLVE;
         }
       }
+#else
+      // one kind of step per iteration: leaf steps once enough lanes wait for one
+      const unsigned leaf = __ballot_sync(0xffffffffu, phase == PH_MARCH && at_leaf);
+      const unsigned node = __ballot_sync(0xffffffffu, phase == PH_MARCH && !at_leaf);
+      if (leaf != 0u && kLeafBatch * __popc(leaf) >= __popc(node)) {
+        if (phase == PH_MARCH && at_leaf) {
+          at_leaf = false;
+          if (walker_leaf_step(m, a.f, w)) phase = PH_RESOLVE;
+        }
+      } else if (phase == PH_MARCH && !at_leaf) {
+        if (walker_node_step(m, a.f, lt, w, at_leaf)) phase = PH_RESOLVE;
+      }
+#endif
       if (phase == PH_MARCH && --budget < 0) {
         overflow = 1;
         at_leaf = false;

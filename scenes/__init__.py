@@ -21,6 +21,11 @@ which are not available):
                  RGB albedo piecewise constant U(0.4, 0.9) over 16 Voronoi
                  cells, 32x64 RGB environment of 8 low-frequency cosines
                  (clamped >= 0), K = 12 lights at elevations U(30, 70) degrees.
+  * `bumps_2048`: 2048x2048 RGB, 200 Gaussian bumps and 4 concave bowls
+                 (opening radius U(0.05, 0.15), depth half the radius), 64x128
+                 RGB cosine environment, K = 32 lights on a jittered ring
+                 (azimuth 2 pi (k + U(-1/4, 1/4)) / K, elevation 45 +- U(-10, 10)
+                 degrees); images stored in FP16.
   * `mixed`:     any size: bumps, bowls and grooves mixed at random (for ragged
                  and odd-sized test cases).
 """
@@ -167,6 +172,66 @@ def bumps_512(seed=2, H=512, W=512, K=12, n_bumps=20):
     albedo = voronoi_albedo(X, Y, rng, 16, 3, 0.4, 0.9)
     env = cosine_env(rng, 3, 32, 64)
     lights = ring_lights(K, rng.uniform(30.0, 70.0, K))
+    return _finish(Hf, Hx, Hy, albedo, lights, env, f"bumps_{H}x{W}")
+
+
+def _add_windowed_gauss(Hf, Hx, Hy, h, cx, cy, amp, sigma, reach=7.0):
+    """Add a Gaussian bump evaluated within reach*sigma of its centre (beyond it the
+    bump is below exp(-24.5) of its amplitude and is left out)."""
+    H, W = Hf.shape
+    j0 = max(0, int((cx - reach * sigma) / h - 0.5))
+    j1 = min(W, int((cx + reach * sigma) / h + 1.5))
+    i0 = max(0, int((cy - reach * sigma) / h - 0.5))
+    i1 = min(H, int((cy + reach * sigma) / h + 1.5))
+    if j0 >= j1 or i0 >= i1:
+        return
+    x = (np.arange(j0, j1) + 0.5) * h
+    y = (np.arange(i0, i1) + 0.5) * h
+    X, Y = np.meshgrid(x, y)
+    e, ex, ey = gauss_field(X, Y, cx, cy, amp, sigma)
+    Hf[i0:i1, j0:j1] += e
+    Hx[i0:i1, j0:j1] += ex
+    Hy[i0:i1, j0:j1] += ey
+
+
+def _voronoi_lowmem(X, Y, rng, n_cells, C, lo, hi):
+    """voronoi_albedo computed seed by seed (ties to the lower seed index)."""
+    seeds = np.stack([rng.uniform(0, X.max() + X.min(), n_cells),
+                      rng.uniform(0, Y.max() + Y.min(), n_cells)], axis=1)
+    vals = rng.uniform(lo, hi, (n_cells, C))
+    best = np.full(X.shape, np.inf)
+    cell = np.zeros(X.shape, np.int64)
+    for m in range(n_cells):
+        d2 = (X - seeds[m, 0]) ** 2 + (Y - seeds[m, 1]) ** 2
+        closer = d2 < best
+        best = np.where(closer, d2, best)
+        cell = np.where(closer, m, cell)
+    return np.moveaxis(vals[cell], -1, 0)
+
+
+def bumps_2048(seed=3, H=2048, W=2048, K=32, n_bumps=200, n_bowls=4):
+    """Gaussian bumps + concave bowls, Voronoi RGB albedo, 64x128 environment, jittered light ring."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / W
+    ymax = H / W
+    Hf = np.zeros((H, W))
+    Hx = np.zeros((H, W))
+    Hy = np.zeros((H, W))
+    for _ in range(n_bumps):
+        _add_windowed_gauss(Hf, Hx, Hy, h, rng.uniform(0, 1), rng.uniform(0, ymax), rng.uniform(-0.15, 0.15),
+                            rng.uniform(0.02, 0.1))
+    X, Y = grid(H, W)
+    for _ in range(n_bowls):
+        r = rng.uniform(0.05, 0.15)
+        e, ex, ey = bowl_field(X, Y, rng.uniform(0.15, 0.85), rng.uniform(0.15, 0.85) * ymax, r, 0.5 * r)
+        Hf += e
+        Hx += ex
+        Hy += ey
+    albedo = _voronoi_lowmem(X, Y, rng, 16, 3, 0.4, 0.9)
+    env = cosine_env(rng, 3, 64, 128)
+    az = 2.0 * np.pi * (np.arange(K) + rng.uniform(-0.25, 0.25, K)) / K
+    el = np.radians(45.0 + rng.uniform(-10.0, 10.0, K))
+    lights = np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], axis=1)
     return _finish(Hf, Hx, Hy, albedo, lights, env, f"bumps_{H}x{W}")
 
 
