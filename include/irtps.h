@@ -65,8 +65,9 @@ typedef struct irtps_options {
   float nz_min;       /* n_z clamp of the slopes -n_x/n_z, -n_y/n_z (0.05) */
   double cg_tol;      /* depth solve: stop at FP64 |b - A x| / |b| <= cg_tol (1e-9) */
   int cg_max_iter;    /* depth solve iteration cap (50000) */
-  int cg_check_every; /* FP64 true-residual refresh and convergence test period (50) */
+  int cg_check_every; /* FP64 true-residual refresh and convergence test period (10) */
   double stop_tol;    /* irtps_iterate stops early when D_H < stop_tol; 0 = never (0) */
+  int precond;        /* depth-solve preconditioner: 0 Jacobi (diagonal), 1 multigrid V-cycle (1) */
 } irtps_options;
 
 /* Counters of the last irtps_iterate / irtps_trace / irtps_integrate call. */

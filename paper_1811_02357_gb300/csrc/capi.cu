@@ -47,7 +47,8 @@ int dalloc(Ctx &c, T **p, size_t n, const char *what) {
 
 void release(Ctx &c) {
   void *bufs[] = {c.env, c.images, c.lbar, c.depth, c.depth_prev, c.nrm, c.albedo, c.valid, c.pmin, c.pmax,
-                  c.cg_x, c.cg_b, c.cg_r, c.cg_z, c.cg_p, c.cg_ap, c.part, c.counts, c.cg_ctl};
+                  c.cg_x, c.cg_b, c.cg_r, c.cg_z, c.cg_p, c.cg_ap, c.part, c.counts, c.cg_ctl,
+                  c.mg_x0, c.mg_x1, c.mg_b, c.mg_wh, c.mg_wv};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (c.h_part) cudaFreeHost(c.h_part);
@@ -159,8 +160,9 @@ void irtps_default_options(irtps_options *opt) {
   opt->nz_min = 0.05f;
   opt->cg_tol = 1e-9;
   opt->cg_max_iter = 50000;
-  opt->cg_check_every = 50;
+  opt->cg_check_every = 10;
   opt->stop_tol = 0.0;
+  opt->precond = 1;
 }
 
 int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *lights, const float *env, int EH,
@@ -190,6 +192,8 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
     c.opt = *opt;
   else
     irtps_default_options(&c.opt);
+  if (c.opt.precond != 0 && c.opt.precond != 1)
+    return bail(fail(c, IRTPS_EINVAL, "create: precond must be 0 (Jacobi) or 1 (multigrid)"));
   c.eps = (float)1e-3 / (float)W;  // same expression as the oracle's lift
   // lights and pinv(L) = (L^T L)^-1 L^T in FP64 (Eq. 4)
   c.h_lights.assign(lights, lights + 3 * K);
@@ -258,6 +262,19 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
       (rc = dalloc(c, &c.counts, irtps::kCounters, "counters")) ||
       (rc = dalloc(c, (irtps::CGCtl **)&c.cg_ctl, 1, "solver control")))
     return bail(rc);
+  {  // multigrid hierarchy: layout and Galerkin weights built on the host once
+    int total = 0;
+    irtps::mg_layout(H, W, &c.mg_levels, c.mg_h, c.mg_w, c.mg_off, &total);
+    std::vector<float> wh((size_t)total), wv((size_t)total);
+    irtps::mg_weights(c.mg_levels, c.mg_h, c.mg_w, c.mg_off, wh.data(), wv.data());
+    if ((rc = dalloc(c, &c.mg_x0, (size_t)total, "multigrid")) || (rc = dalloc(c, &c.mg_x1, (size_t)total, "multigrid")) ||
+        (rc = dalloc(c, &c.mg_b, (size_t)total, "multigrid")) || (rc = dalloc(c, &c.mg_wh, (size_t)total, "multigrid")) ||
+        (rc = dalloc(c, &c.mg_wv, (size_t)total, "multigrid")))
+      return bail(rc);
+    e = cudaMemcpy(c.mg_wh, wh.data(), sizeof(float) * total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c.mg_wv, wv.data(), sizeof(float) * total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "create: multigrid weights"));
+  }
   e = cudaMallocHost((void **)&c.h_part, sizeof(double) * c.part_stride);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "create: pinned partials"));
   e = cudaMemcpyAsync(c.env, env, sizeof(float) * C * EH * EW, cudaMemcpyHostToDevice, c.stream);

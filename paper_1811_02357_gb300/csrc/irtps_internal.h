@@ -51,6 +51,10 @@ struct Ctx {
   int part_stride = 0, cg_blocks = 0;
   double *h_part = nullptr;       // pinned host mirror of one partial slot
   void *cg_ctl = nullptr;         // device control block of the cooperative CG loop
+  // multigrid hierarchy of the depth solve (levels of 2x2 aggregates, pooled arrays)
+  int mg_levels = 0;
+  int mg_h[kMaxLevels] = {0}, mg_w[kMaxLevels] = {0}, mg_off[kMaxLevels] = {0};
+  float *mg_x0 = nullptr, *mg_x1 = nullptr, *mg_b = nullptr, *mg_wh = nullptr, *mg_wv = nullptr;
   unsigned long long *counts = nullptr;  // {unused, segments, walk overflows, node visits, triangle tests, sampled directions}
   cudaEvent_t ev[2] = {nullptr, nullptr};
   irtps_stats stats{};
@@ -101,5 +105,7 @@ cudaError_t launch_ps(Ctx &c, bool zero_indirect);
 int solve_depth(Ctx &c);          // IRTPS_OK or an error code (message in c.err)
 int depth_change(Ctx &c, double *dH_max, double *dH_rms);
 int cg_grid_limit();  // co-resident blocks available to the cooperative solve
+void mg_layout(int H, int W, int *levels, int *h, int *w, int *off, int *total);
+void mg_weights(int levels, const int *h, const int *w, const int *off, float *wh, float *wv);
 
 }  // namespace irtps

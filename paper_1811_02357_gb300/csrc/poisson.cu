@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const CG g, int rz_slot) 
 // raises the error flag, and all blocks leave the solve at the next check.
 __device__ __forceinline__ void grid_barrier(unsigned *count, volatile unsigned *gen, int *err) {
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && !*(volatile int *)err) {  // after a failure every barrier is a no-op
     const unsigned g0 = *gen;
     __threadfence();
     if (atomicAdd(count, 1u) == gridDim.x - 1) {
@@ -223,12 +223,203 @@ __device__ __forceinline__ float inv_degree(int i, int j, int H, int W) {
   return d == 4 ? 0.25f : (d == 3 ? (1.0f / 3.0f) : (d == 2 ? 0.5f : 1.0f));
 }
 
-// The whole Jacobi-PCG loop in one cooperative launch.  The iterate is
-// x = x64 + e: the FP64 part changes only at a refresh, the FP32 correction e
-// collects alpha * p in between.  Per iteration:
+// ---------------------------------------------------------------------------
+// Multigrid V-cycle preconditioner (option precond = 1).  Levels coarsen the
+// pixel grid by 2x2 aggregation; the operator of each coarse level is the
+// Galerkin product R A P of the finer one with piecewise-constant P and R = P^T,
+// which is again a weighted 5-point graph Laplacian: its edge weight between two
+// aggregates is the sum of the fine weights crossing between them (weights are
+// built once on the host).  Smoother: two weighted-Jacobi sweeps before and after
+// the coarse correction (symmetric, so the V-cycle is an admissible CG
+// preconditioner).  The fine levels are swept by the whole grid between grid
+// barriers; levels of at most kMgBlockPoints points are handled by block 0
+// alone, the coarsest (<= 16 points) by repeated sweeps and a mean projection.
+// ---------------------------------------------------------------------------
+constexpr int kMgMaxLevels = 16;
+constexpr int kMgBlockPoints = 4096;
+#ifndef IRTPS_MG_CSCALE
+#define IRTPS_MG_CSCALE 1.0f
+#endif
+
+struct MG {
+  int levels, grid_levels;
+  int H[kMgMaxLevels], W[kMgMaxLevels], off[kMgMaxLevels];
+  float *x0, *x1, *b;  // pooled per level at off[l]
+  const float *wh;     // weight of edge (i, j)-(i, j+1), pooled, H*W slots per level
+  const float *wv;     // weight of edge (i, j)-(i+1, j)
+  float omega, cscale;
+};
+
+__device__ __forceinline__ float mg_diag(const MG &m, int l, int i, int j) {
+  const int H = m.H[l], W = m.W[l], o = m.off[l];
+  const int p = i * W + j;
+  float d = 0.0f;
+  if (j > 0) d += m.wh[o + p - 1];
+  if (j < W - 1) d += m.wh[o + p];
+  if (i > 0) d += m.wv[o + p - W];
+  if (i < H - 1) d += m.wv[o + p];
+  return d;
+}
+
+__device__ __forceinline__ float mg_ax(const MG &m, int l, const float *x, int i, int j, float xc, float &d) {
+  const int H = m.H[l], W = m.W[l], o = m.off[l];
+  const int p = i * W + j;
+  float s = 0.0f;
+  d = 0.0f;
+  if (j > 0) { const float w = m.wh[o + p - 1]; s = fmaf(w, x[o + p - 1], s); d += w; }
+  if (j < W - 1) { const float w = m.wh[o + p]; s = fmaf(w, x[o + p + 1], s); d += w; }
+  if (i > 0) { const float w = m.wv[o + p - W]; s = fmaf(w, x[o + p - W], s); d += w; }
+  if (i < H - 1) { const float w = m.wv[o + p]; s = fmaf(w, x[o + p + W], s); d += w; }
+  return fmaf(d, xc, -s);
+}
+
+// The same with the coarse correction of level l+1 added to x on the fly.
+__device__ __forceinline__ float mg_xc(const MG &m, int l, const float *x, int i, int j) {
+  const int Wc = m.W[l + 1];
+  return x[m.off[l] + i * m.W[l] + j] + m.cscale * m.x1[m.off[l + 1] + (i >> 1) * Wc + (j >> 1)];
+}
+
+__device__ __forceinline__ float mg_ax_corr(const MG &m, int l, const float *x, int i, int j, float &d, float &xcen) {
+  const int H = m.H[l], W = m.W[l], o = m.off[l];
+  const int p = i * W + j;
+  float s = 0.0f;
+  d = 0.0f;
+  if (j > 0) { const float w = m.wh[o + p - 1]; s = fmaf(w, mg_xc(m, l, x, i, j - 1), s); d += w; }
+  if (j < W - 1) { const float w = m.wh[o + p]; s = fmaf(w, mg_xc(m, l, x, i, j + 1), s); d += w; }
+  if (i > 0) { const float w = m.wv[o + p - W]; s = fmaf(w, mg_xc(m, l, x, i - 1, j), s); d += w; }
+  if (i < H - 1) { const float w = m.wv[o + p]; s = fmaf(w, mg_xc(m, l, x, i + 1, j), s); d += w; }
+  xcen = mg_xc(m, l, x, i, j);
+  return fmaf(d, xcen, -s);
+}
+
+// Iterate the points of level l: the whole grid (grid levels) or block 0 alone.
+#define MG_FOR(l, pt)                                                                              \
+  for (int pt = (l < m.grid_levels ? blockIdx.x * blockDim.x : 0) + threadIdx.x,                   \
+           pt##_n = m.H[l] * m.W[l], pt##_s = (l < m.grid_levels ? gridDim.x : 1) * blockDim.x; \
+       pt < pt##_n; pt += pt##_s)
+
+// Synchronise after a step on level l: a grid barrier on grid levels, the block on block levels.
+__device__ __forceinline__ void mg_sync(const MG &m, int l, CGCtl *ctl) {
+  if (l < m.grid_levels) grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+  else __syncthreads();
+}
+
+// z = V(r): level-0 right-hand side r (length P), result in x1 of level 0.
+// Called by all blocks; on return all of z is visible to all blocks.
+__device__ void mg_vcycle(const MG &m, const float *r, CGCtl *ctl) {
+  const float om = m.omega;
+  const int L = m.levels;
+  // ---- down ----
+  for (int l = 0; l < L - 1; ++l) {
+    const bool active = l < m.grid_levels || blockIdx.x == 0;
+    const float *b = l == 0 ? r : m.b + m.off[l];
+    const int W = m.W[l], o = m.off[l];
+    if (active) {
+      MG_FOR(l, pt) {  // first sweep from zero: x = omega b / d
+        const int i = pt / W, j = pt - i * W;
+        m.x0[o + pt] = om * b[pt] / mg_diag(m, l, i, j);
+      }
+    }
+    if (l < m.grid_levels) mg_sync(m, l, ctl); else if (active) __syncthreads();
+    if (active) {
+      MG_FOR(l, pt) {  // second sweep
+        const int i = pt / W, j = pt - i * W;
+        float d;
+        const float ax = mg_ax(m, l, m.x0, i, j, m.x0[o + pt], d);
+        m.x1[o + pt] = m.x0[o + pt] + om * (b[pt] - ax) / d;
+      }
+    }
+    if (l < m.grid_levels) mg_sync(m, l, ctl); else if (active) __syncthreads();
+    // residual, summed over each 2x2 aggregate into the next level's right-hand side
+    const int lc = l + 1;
+    const bool active_c = lc < m.grid_levels || blockIdx.x == 0;
+    if (active && active_c) {
+      const int Wc = m.W[lc], Hf = m.H[l];
+      MG_FOR(lc, pt) {
+        const int I = pt / Wc, J = pt - I * Wc;
+        float sum = 0.0f;
+        for (int di = 0; di < 2; ++di) {
+          const int i = 2 * I + di;
+          if (i >= Hf) break;
+          for (int dj = 0; dj < 2; ++dj) {
+            const int j = 2 * J + dj;
+            if (j >= W) break;
+            float d;
+            const float ax = mg_ax(m, l, m.x1, i, j, m.x1[o + i * W + j], d);
+            sum += b[i * W + j] - ax;
+          }
+        }
+        m.b[m.off[lc] + pt] = sum;
+      }
+    }
+    if (l < m.grid_levels) mg_sync(m, l, ctl); else if (active) __syncthreads();
+  }
+  // ---- coarsest: sweeps and a mean projection (block 0) ----
+  if (blockIdx.x == 0) {
+    const int l = L - 1, W = m.W[l], o = m.off[l], n = m.H[l] * m.W[l];
+    const float *b = L == 1 ? r : m.b + o;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) m.x1[o + q] = 0.0f;
+    __syncthreads();
+    for (int sweep = 0; sweep < 64; ++sweep) {
+      float v = 0.0f;
+      if (threadIdx.x < n) {
+        const int i = threadIdx.x / W, j = threadIdx.x - i * W;
+        float d;
+        const float ax = mg_ax(m, l, m.x1, i, j, m.x1[o + threadIdx.x], d);
+        v = d > 0.0f ? m.x1[o + threadIdx.x] + om * (b[threadIdx.x] - ax) / d : 0.0f;
+      }
+      __syncthreads();
+      if (threadIdx.x < n) m.x1[o + threadIdx.x] = v;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      float mean = 0.0f;
+      for (int q = 0; q < n; ++q) mean += m.x1[o + q];
+      mean /= (float)n;
+      for (int q = 0; q < n; ++q) m.x1[o + q] -= mean;
+    }
+    __syncthreads();
+  }
+  // ---- up ----
+  for (int l = L - 2; l >= 0; --l) {
+    const bool active = l < m.grid_levels || blockIdx.x == 0;
+    const float *b = l == 0 ? r : m.b + m.off[l];
+    const int W = m.W[l], o = m.off[l];
+    // the coarse level's result must be visible before it is interpolated
+    if (l + 1 == m.grid_levels || l + 1 == L - 1) {
+      if (l < m.grid_levels) grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+      else if (active) __syncthreads();
+    }
+    if (active) {
+      MG_FOR(l, pt) {  // first sweep on x + P x_coarse
+        const int i = pt / W, j = pt - i * W;
+        float d, xcen;
+        const float ax = mg_ax_corr(m, l, m.x1, i, j, d, xcen);
+        m.x0[o + pt] = xcen + om * (b[pt] - ax) / d;
+      }
+    }
+    if (l < m.grid_levels) mg_sync(m, l, ctl); else if (active) __syncthreads();
+    if (active) {
+      MG_FOR(l, pt) {  // second sweep
+        const int i = pt / W, j = pt - i * W;
+        float d;
+        const float ax = mg_ax(m, l, m.x0, i, j, m.x0[o + pt], d);
+        m.x1[o + pt] = m.x0[o + pt] + om * (b[pt] - ax) / d;
+      }
+    }
+    if (l < m.grid_levels) mg_sync(m, l, ctl); else if (active) __syncthreads();
+  }
+  if (m.grid_levels == 0) grid_barrier(&ctl->count, &ctl->gen, &ctl->err);  // z was written by block 0 alone
+}
+#undef MG_FOR
+
+// The whole PCG loop in one cooperative launch (PRE 0: Jacobi, M = diag(degree);
+// PRE 1: the multigrid V-cycle above).  The iterate is x = x64 + e: the FP64 part
+// changes only at a refresh, the FP32 correction e collects alpha * p in between.
+// Per iteration:
 //  A: beta = rz_{it-1}/rz_{it-2}; p_it = z + beta p_{it-1} (also at the 4
 //     neighbours, recomputed locally); Ap; partial p.Ap       -- barrier --
-//  B: alpha = rz_{it-1}/p.Ap; e += alpha p; r -= alpha Ap; z = r/deg;
+//  B: alpha = rz_{it-1}/p.Ap; e += alpha p; r -= alpha Ap; z = M^-1 r;
 //     partial r.z                                             -- barrier --
 // Every `check` iterations, or as soon as r.z has fallen below 1e-10 of its
 // value at the last refresh (the FP32 recursion has converged and further steps
@@ -237,9 +428,10 @@ __device__ __forceinline__ float inv_degree(int i, int j, int H, int W) {
 // against tol (iterative refinement).  Dot products are FP32 within a block and
 // FP64 across blocks; every block sums the same partials in the same order and
 // so takes the same decisions.
+template <int PRE>
 __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, double bnorm, double tol,
-                                                      int max_iter, int check) {
-  __shared__ double sh[kThreads / 32 + 1 > 33 ? kThreads / 32 + 1 : 33];
+                                                      int max_iter, int check, const MG mg) {
+  __shared__ double sh[33];
   __shared__ float shf[33];
   __shared__ float s_ab[2];
   __shared__ int s_frozen;
@@ -247,8 +439,37 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, do
   int stall = 0, it = 0;
   double rel = ctl->rel;
   float *e = g.ap + g.P;  // correction accumulator (second half of the Ap buffer)
+  float *z = PRE == 1 ? mg.x1 : g.z;  // preconditioned residual (level 0 of the hierarchy for PRE 1)
   for (Stride q(g.W); q.p < g.P; q.next(g.W)) e[q.p] = 0.0f;
-  while (rel > tol && it < max_iter) {
+  // z = M^-1 r and the partial sums of r.z into `slot` (and the refresh reference)
+  auto precondition = [&](int slot, bool refresh) {
+    if (PRE == 1) {
+      grid_barrier(&ctl->count, &ctl->gen, &ctl->err);  // r complete
+      mg_vcycle(mg, g.r, ctl);
+    }
+    float rz = 0.0f;
+    for (Stride q(g.W); q.p < g.P; q.next(g.W)) {
+      const float rf = g.r[q.p];
+      float zf;
+      if (PRE == 1) {
+        zf = z[q.p];
+      } else {
+        zf = rf * inv_degree(q.i, q.j, g.H, g.W);
+        z[q.p] = zf;
+      }
+      rz = fmaf(rf, zf, rz);
+    }
+    rz = block_sum_f(rz, shf);
+    if (threadIdx.x == 0) {
+      g.part[slot * g.stride + blockIdx.x] = (double)rz;
+      if (refresh) g.part[S_RZREF * g.stride + blockIdx.x] = (double)rz;
+    }
+  };
+  if (PRE == 1) {  // the residual kernel left r; z and r.z come from the V-cycle
+    precondition(S_RZ0, true);
+    grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+  }
+  while (rel > tol && it < max_iter && !*(volatile int *)&ctl->err) {
     ++it;
     // ---- A ----
     const double num = total(g.part + (S_RZ0 + ((it - 1) & 1)) * g.stride, g.nblk, sh);
@@ -265,7 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, do
     const bool first = it == 1;
     const float *pold = g.p + (size_t)((it - 1) & 1) * g.P;
     float *pnew = g.p + (size_t)(it & 1) * g.P;
-    auto dir = [&](int r) { return frozen ? 0.0f : (first ? g.z[r] : fmaf(beta, pold[r], g.z[r])); };
+    auto dir = [&](int r) { return frozen ? 0.0f : (first ? z[r] : fmaf(beta, pold[r], z[r])); };
     float pap = 0.0f;
     for (Stride q(g.W); q.p < g.P; q.next(g.W)) {
       const int p = q.p;
@@ -289,18 +510,12 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, do
     if (threadIdx.x == 0) s_ab[0] = (dpap > 0.0 && isfinite(dpap)) ? (float)(num / dpap) : 0.0f;
     __syncthreads();
     const float af = s_ab[0];
-    float rz = 0.0f;
     for (Stride q(g.W); q.p < g.P; q.next(g.W)) {
       const int p = q.p;
       e[p] = fmaf(af, pnew[p], e[p]);
-      const float rf = fmaf(-af, g.ap[p], g.r[p]);
-      const float zf = rf * inv_degree(q.i, q.j, g.H, g.W);
-      g.r[p] = rf;
-      g.z[p] = zf;
-      rz = fmaf(rf, zf, rz);
+      g.r[p] = fmaf(-af, g.ap[p], g.r[p]);
     }
-    rz = block_sum_f(rz, shf);
-    if (threadIdx.x == 0) g.part[(S_RZ0 + (it & 1)) * g.stride + blockIdx.x] = (double)rz;
+    precondition(S_RZ0 + (it & 1), false);
     grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
     if (*(volatile int *)&ctl->err) break;
     // ---- refresh from FP64 ----
@@ -311,32 +526,24 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, do
       }
       grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
       if (*(volatile int *)&ctl->err) break;
-      double rzr = 0.0, rr = 0.0;
+      double rr = 0.0;
       for (Stride q(g.W); q.p < g.P; q.next(g.W)) {
         const double res = g.b[q.p] - lap_at<double>(g.x, q.i, q.j, g.H, g.W);
-        const float rf = (float)res;
-        const float zf = rf * inv_degree(q.i, q.j, g.H, g.W);
-        g.r[q.p] = rf;
-        g.z[q.p] = zf;
-        rzr += (double)rf * (double)zf;
+        g.r[q.p] = (float)res;
         rr += res * res;
-      }
-      rzr = block_reduce<false>(rzr, sh);
-      if (threadIdx.x == 0) {
-        g.part[(S_RZ0 + (it & 1)) * g.stride + blockIdx.x] = rzr;
-        g.part[S_RZREF * g.stride + blockIdx.x] = rzr;
       }
       rr = block_reduce<false>(rr, sh);
       if (threadIdx.x == 0) g.part[S_RR * g.stride + blockIdx.x] = rr;
+      precondition(S_RZ0 + (it & 1), true);
       grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
       if (*(volatile int *)&ctl->err) break;
       rel = sqrt(total(g.part + S_RR * g.stride, g.nblk, sh)) / bnorm;
       if (!isfinite(rel)) break;
       if (rel < 0.95 * best) {
         best = rel;
-        stall = 0;
-      } else if (++stall >= 10) {
-        break;  // the FP64 residual has stopped improving (rounding floor)
+        stall = it;
+      } else if (it - stall >= 1000) {
+        break;  // no 5% gain in 1000 iterations: the FP64 residual is at its rounding floor
       }
     }
   }
@@ -394,9 +601,72 @@ int cg_grid_limit() {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_loop, kThreads, 0) != cudaSuccess) return 1;
+  int per1 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_loop<0>, kThreads, 0) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_cg_loop<1>, kThreads, 0) != cudaSuccess) return 1;
+  per = per < per1 ? per : per1;
   per = per < IRTPS_CG_BLOCKS_PER_SM ? per : IRTPS_CG_BLOCKS_PER_SM;
   return per * sms > 0 ? per * sms : 1;
+}
+
+static MG make_mg(const Ctx &c) {
+  MG m{};
+  m.levels = c.mg_levels;
+  m.grid_levels = 0;
+  for (int l = 0; l < c.mg_levels; ++l) {
+    m.H[l] = c.mg_h[l];
+    m.W[l] = c.mg_w[l];
+    m.off[l] = c.mg_off[l];
+    if (c.mg_h[l] * c.mg_w[l] > kMgBlockPoints) m.grid_levels = l + 1;
+  }
+  m.x0 = c.mg_x0;
+  m.x1 = c.mg_x1;
+  m.b = c.mg_b;
+  m.wh = c.mg_wh;
+  m.wv = c.mg_wv;
+  m.omega = 0.8f;
+  m.cscale = IRTPS_MG_CSCALE;
+  return m;
+}
+
+// Levels and Galerkin edge weights of the multigrid hierarchy (host, once per context).
+void mg_layout(int H, int W, int *levels, int *h, int *w, int *off, int *total) {
+  int l = 0, o = 0;
+  h[0] = H;
+  w[0] = W;
+  while (true) {
+    off[l] = o;
+    o += h[l] * w[l];
+    if (h[l] * w[l] <= 16 || l + 1 >= kMgMaxLevels) break;
+    h[l + 1] = (h[l] + 1) / 2;
+    w[l + 1] = (w[l] + 1) / 2;
+    ++l;
+  }
+  *levels = l + 1;
+  *total = o;
+}
+
+void mg_weights(int levels, const int *h, const int *w, const int *off, float *wh, float *wv) {
+  for (int i = 0; i < h[0]; ++i)
+    for (int j = 0; j < w[0]; ++j) {
+      wh[off[0] + i * w[0] + j] = j < w[0] - 1 ? 1.0f : 0.0f;
+      wv[off[0] + i * w[0] + j] = i < h[0] - 1 ? 1.0f : 0.0f;
+    }
+  for (int l = 0; l + 1 < levels; ++l) {
+    const int Hf = h[l], Wf = w[l], Hc = h[l + 1], Wc = w[l + 1];
+    const float *fh = wh + off[l], *fv = wv + off[l];
+    float *ch = wh + off[l + 1], *cv = wv + off[l + 1];
+    for (int I = 0; I < Hc; ++I)
+      for (int J = 0; J < Wc; ++J) {
+        float sh = 0.0f, sv = 0.0f;
+        if (2 * J + 2 < Wf)
+          for (int i = 2 * I; i < 2 * I + 2 && i < Hf; ++i) sh += fh[i * Wf + 2 * J + 1];
+        if (2 * I + 2 < Hf)
+          for (int j = 2 * J; j < 2 * J + 2 && j < Wf; ++j) sv += fv[(2 * I + 1) * Wf + j];
+        ch[I * Wc + J] = sh;
+        cv[I * Wc + J] = sv;
+      }
+  }
 }
 
 static CG make_cg(Ctx &c) {
@@ -486,8 +756,11 @@ int solve_depth(Ctx &c) {
     double tol = c.opt.cg_tol;
     int max_iter = c.opt.cg_max_iter;
     irtps::CGCtl *ctl = (irtps::CGCtl *)c.cg_ctl;
-    void *args[] = {(void *)&g, (void *)&ctl, (void *)&bnorm, (void *)&tol, (void *)&max_iter, (void *)&m};
-    e = cudaLaunchCooperativeKernel((const void *)k_cg_loop, dim3(nb), dim3(kThreads), args, 0, c.stream);
+    const MG mg = make_mg(c);
+    void *args[] = {(void *)&g, (void *)&ctl, (void *)&bnorm, (void *)&tol, (void *)&max_iter, (void *)&m,
+                    (void *)&mg};
+    const void *fn = c.opt.precond == 1 ? (const void *)k_cg_loop<1> : (const void *)k_cg_loop<0>;
+    e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(kThreads), args, 0, c.stream);
     ++c.stats.launches;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c.cg_ctl, sizeof(h), cudaMemcpyDeviceToHost, c.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
@@ -649,8 +922,10 @@ extern "C" int irtps_integrate_noalloc(const float *normals, int H, int W, float
     CGCtl h{0u, 0u, 0, 0, rel};  // barrier counters start at zero on every call
     if (cudaMemcpyAsync(ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s) != cudaSuccess) return IRTPS_ECUDA;
     int m = 50;
-    void *args[] = {(void *)&g, (void *)&ctl, (void *)&bnorm, (void *)&tol, (void *)&max_iter, (void *)&m};
-    if (cudaLaunchCooperativeKernel((const void *)k_cg_loop, dim3(nb), dim3(kThreads), args, 0, s) != cudaSuccess)
+    const MG none{};
+    void *args[] = {(void *)&g, (void *)&ctl, (void *)&bnorm, (void *)&tol, (void *)&max_iter, (void *)&m,
+                    (void *)&none};
+    if (cudaLaunchCooperativeKernel((const void *)k_cg_loop<0>, dim3(nb), dim3(kThreads), args, 0, s) != cudaSuccess)
       return IRTPS_ECUDA;
     if (cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return IRTPS_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return IRTPS_ECUDA;

@@ -39,12 +39,12 @@ def test_default_options(binding):
     o = binding.irtps_default_options()
     assert o.shadow_rays == 1 and abs(o.tau_lo - 0.02) < 1e-8 and abs(o.tau_hi - 0.98) < 1e-7
     assert o.cond_max == 1e8 and abs(o.nz_min - 0.05) < 1e-8 and o.cg_tol == 1e-9
-    assert o.stop_tol == 0.0
+    assert o.stop_tol == 0.0 and o.precond == 1
 
 
 def test_struct_layouts_match_header(binding):
     # sizes of the option / stats structs as the C compiler lays them out
-    assert ctypes.sizeof(binding.irtps_options) == 56
+    assert ctypes.sizeof(binding.irtps_options) == 64
     assert ctypes.sizeof(binding.irtps_stats) == 8 * 3 + 8 + 8 * 3 + 8 + 8 * 2 + 8 * 3 + 8 + 8
 
 

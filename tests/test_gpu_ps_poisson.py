@@ -44,14 +44,17 @@ def test_ps_stage(lib, oracle_mod, case, f16):
     assert n1[..., 3].reshape(-1)[ok].min() > 0
 
 
-@pytest.mark.parametrize("H,W", [(64, 64), (37, 53), (256, 256), (2, 5)])
-def test_integrate(lib, oracle_mod, H, W):
-    sc = scenes.mixed(H * 7 + W, H, W, K=3, C=1) if H > 2 else None
+@pytest.mark.parametrize("precond", [0, 1])
+@pytest.mark.parametrize("H,W", [(64, 64), (37, 53), (256, 256), (2, 5), (3, 301)])
+def test_integrate(lib, oracle_mod, H, W, precond):
+    sc = scenes.mixed(H * 7 + W, H, W, K=3, C=1) if H > 3 else None
+    rs = np.random.default_rng(H * W)
     normals = sc.normals if sc is not None else scenes.normals_from_gradient(
-        np.array([[0.1, 0.2, 0.0, -0.1, 0.3], [0.0, -0.2, 0.1, 0.2, 0.0]]),
-        np.array([[0.3, 0.0, -0.1, 0.0, 0.1], [0.1, 0.1, 0.0, -0.3, 0.2]])).astype(np.float32)
+        rs.uniform(-0.3, 0.3, (H, W)), rs.uniform(-0.3, 0.3, (H, W))).astype(np.float32)
     lights = scenes.ring_lights(3, 45.0)
-    with lib.Context(H, W, lights, np.zeros((1, 2, 2), np.float32)) as ctx:
+    opt = lib.irtps_default_options()
+    opt.precond = precond
+    with lib.Context(H, W, lights, np.zeros((1, 2, 2), np.float32), opt) as ctx:
         ctx.set_state(depth=np.zeros((H, W), np.float32), normals=normals)
         ctx.integrate()
         d = ctx.depth()
