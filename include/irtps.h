@@ -68,6 +68,8 @@ typedef struct irtps_options {
   int cg_check_every; /* FP64 true-residual refresh and convergence test period (10) */
   double stop_tol;    /* irtps_iterate stops early when D_H < stop_tol; 0 = never (0) */
   int precond;        /* depth-solve preconditioner: 0 Jacobi (diagonal), 1 multigrid V-cycle (1) */
+  int use_graph;      /* 1: irtps_iterate captures one iteration as a CUDA graph and replays it (0);
+                         per-stage times are then not measured (reported as 0) */
 } irtps_options;
 
 /* Counters of the last irtps_iterate / irtps_trace / irtps_integrate call. */

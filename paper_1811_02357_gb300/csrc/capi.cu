@@ -47,13 +47,16 @@ int dalloc(Ctx &c, T **p, size_t n, const char *what) {
 
 void release(Ctx &c) {
   void *bufs[] = {c.env, c.images, c.lbar, c.depth, c.depth_prev, c.nrm, c.albedo, c.valid, c.pmin, c.pmax,
-                  c.cg_x, c.cg_b, c.cg_r, c.cg_z, c.cg_p, c.cg_ap, c.part, c.counts, c.cg_ctl,
-                  c.mg_x0, c.mg_x1, c.mg_b, c.mg_wh, c.mg_wv};
+                  c.cg_x, c.cg_b, c.cg_r, c.cg_z, c.cg_p, c.cg_ap, c.part, c.dstats, c.next_item, c.cg_ctl,
+                  c.mg_x0, c.mg_x1, c.mg_b, c.mg_wh, c.mg_wv, c.iter_dev};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (c.h_part) cudaFreeHost(c.h_part);
   for (cudaEvent_t ev : c.ev)
     if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : c.tev)
+    if (ev) cudaEventDestroy(ev);
+  if (c.graph) cudaGraphExecDestroy(c.graph);
   if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
 }
 
@@ -72,34 +75,83 @@ int copy_in(Ctx &c, void *dst, const void *src, size_t bytes, int on_device) {
   return IRTPS_OK;
 }
 
-int read_counts(Ctx &c) {
-  unsigned long long h[irtps::kCounters];
-  CK(cudaMemcpyAsync(h, c.counts, sizeof(h), cudaMemcpyDeviceToHost, c.stream), "counts");
-  CK(cudaStreamSynchronize(c.stream), "counts");
-  float ms = 0.0f;
-  CK(cudaEventElapsedTime(&ms, c.ev[0], c.ev[1]), "trace timing");
-  c.stats.trace_ms += ms;
-  c.stats.segments = h[1];
-  c.stats.walk_overflows = h[2];
-  c.stats.node_visits += h[3];
-  c.stats.tri_tests += h[4];
-  c.stats.draws += h[5];
-  if (h[2]) return fail(c, IRTPS_ETIMEOUT, "trace: a heightfield march exhausted its step budget");
+// ---- per-call bookkeeping: device statistics cleared at the start, read once at the end ----
+enum Stage { ST_TRACE = 0, ST_PS = 1, ST_DEPTH = 2 };
+
+int begin_call(Ctx &c) {
+  CK(cudaMemsetAsync(c.dstats, 0, sizeof(irtps::DevStats), c.stream), "statistics reset");
+  c.stats.trace_ms = c.stats.ps_ms = c.stats.depth_ms = 0.0;
+  c.stats.node_visits = c.stats.tri_tests = c.stats.draws = 0;
+  c.stats.segments = c.stats.walk_overflows = c.stats.primary_segments = 0;
+  c.tev_used = 0;
+  return IRTPS_OK;
+}
+
+// CUDA events around one stage on the context stream (pairs, summed at the end of the call).
+int stage_mark(Ctx &c, int stage, bool start) {
+  const int need = c.tev_used + 1;
+  while ((int)c.tev.size() < 2 * need) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e), "timing events");
+    c.tev.push_back(e);
+  }
+  if (start) {
+    c.tev_stage.resize(need);
+    c.tev_stage[c.tev_used] = stage;
+    CK(cudaEventRecord(c.tev[2 * c.tev_used], c.stream), "timing");
+  } else {
+    CK(cudaEventRecord(c.tev[2 * c.tev_used + 1], c.stream), "timing");
+    ++c.tev_used;
+  }
+  return IRTPS_OK;
+}
+
+#define STAGE(stage, start)                        \
+  do {                                             \
+    int rc_ = stage_mark(c, stage, start);         \
+    if (rc_) return rc_;                           \
+  } while (0)
+
+// Wait for the call's work, read the device statistics and turn failures into codes.
+int end_call(Ctx &c, bool had_solve) {
+  irtps::DevStats h;
+  CK(cudaMemcpyAsync(&h, c.dstats, sizeof(h), cudaMemcpyDeviceToHost, c.stream), "statistics");
+  CK(cudaStreamSynchronize(c.stream), "call");
+  for (int i = 0; i < c.tev_used; ++i) {
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, c.tev[2 * i], c.tev[2 * i + 1]), "timing");
+    double *dst = c.tev_stage[i] == ST_TRACE ? &c.stats.trace_ms : (c.tev_stage[i] == ST_PS ? &c.stats.ps_ms : &c.stats.depth_ms);
+    *dst += ms;
+  }
+  c.stats.segments = h.counts[1];
+  c.stats.walk_overflows = h.counts[2];
+  c.stats.node_visits = h.counts[3];
+  c.stats.tri_tests = h.counts[4];
+  c.stats.draws = h.counts[5];
+  c.stats.dH_max = h.dh_max;
+  c.stats.dH_rms = h.dh_rms;
+  if (had_solve) {
+    c.stats.cg_iterations = h.cg.last_iters;
+    c.stats.cg_rel_residual = h.cg.rel_last;
+  }
+  if (h.counts[2]) return fail(c, IRTPS_ETIMEOUT, "trace: a heightfield march exhausted its step budget");
+  if (had_solve && h.cg.err) return fail(c, IRTPS_ETIMEOUT, "depth solve: a grid barrier timed out");
+  if (had_solve && h.cg.bad)
+    return fail(c, IRTPS_ENUMERIC, "depth solve: relative residual " + std::to_string(h.cg.rel_last) +
+                                       " above cg_tol or not finite (" + std::to_string(h.cg.last_iters) +
+                                       " iterations)");
   return IRTPS_OK;
 }
 
 int trace_into(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed, uint32_t iter,
-               uint32_t stream_tag, float *out, int32_t *rec) {
+               uint32_t stream_tag, float *out, int32_t *rec, bool iter_from_device = false) {
   CK(irtps::build_pyramid(c), "pyramid build");
-  CK(cudaMemcpyAsync(&c.zmax, c.pmax + c.off[c.levels - 1], sizeof(float), cudaMemcpyDeviceToHost, c.stream),
-     "pyramid top");
-  CK(cudaStreamSynchronize(c.stream), "pyramid top");
-  CK(cudaMemsetAsync(c.counts, 0, irtps::kCounters * sizeof(unsigned long long), c.stream), "counts");
-  CK(cudaEventRecord(c.ev[0], c.stream), "trace timing");
-  CK(irtps::launch_trace(c, pixels, n_pix, spp, bounces, seed, iter, stream_tag, out, rec), "trace launch");
-  CK(cudaEventRecord(c.ev[1], c.stream), "trace timing");
-  c.stats.primary_segments = (unsigned long long)n_pix * c.K * spp;
-  return read_counts(c);
+  if (!iter_from_device) STAGE(ST_TRACE, true);
+  CK(irtps::launch_trace(c, pixels, n_pix, spp, bounces, seed, iter, stream_tag, out, rec, iter_from_device),
+     "trace launch");
+  if (!iter_from_device) STAGE(ST_TRACE, false);
+  c.stats.primary_segments += (unsigned long long)n_pix * c.K * spp;
+  return IRTPS_OK;
 }
 
 bool trace_args_ok(Ctx &c, int spp, int bounces) {
@@ -110,34 +162,18 @@ bool trace_args_ok(Ctx &c, int spp, int bounces) {
   return true;
 }
 
-// Subtract + PS, timed with events on the context stream.
 int run_ps(Ctx &c, bool zero_indirect) {
-  CK(cudaEventRecord(c.ev[0], c.stream), "ps timing");
+  STAGE(ST_PS, true);
   CK(irtps::launch_ps(c, zero_indirect), "ps launch");
-  CK(cudaEventRecord(c.ev[1], c.stream), "ps timing");
-  CK(cudaEventSynchronize(c.ev[1]), "ps");
-  float ms = 0.0f;
-  CK(cudaEventElapsedTime(&ms, c.ev[0], c.ev[1]), "ps timing");
-  c.stats.ps_ms += ms;
+  STAGE(ST_PS, false);
   return IRTPS_OK;
 }
 
-// Depth solve, timed with events (the solve itself synchronises for its convergence tests).
 int run_depth(Ctx &c) {
-  CK(cudaEventRecord(c.ev[0], c.stream), "depth timing");
-  int rc = irtps::solve_depth(c);
-  if (rc) return rc;
-  CK(cudaEventRecord(c.ev[1], c.stream), "depth timing");
-  CK(cudaEventSynchronize(c.ev[1]), "depth");
-  float ms = 0.0f;
-  CK(cudaEventElapsedTime(&ms, c.ev[0], c.ev[1]), "depth timing");
-  c.stats.depth_ms += ms;
+  STAGE(ST_DEPTH, true);
+  CK(irtps::solve_depth_async(c), "depth solve launch");
+  STAGE(ST_DEPTH, false);
   return IRTPS_OK;
-}
-
-void reset_timers(Ctx &c) {
-  c.stats.trace_ms = c.stats.ps_ms = c.stats.depth_ms = 0.0;
-  c.stats.node_visits = c.stats.tri_tests = c.stats.draws = 0;
 }
 
 int iteration_zero(Ctx &c) {
@@ -145,6 +181,57 @@ int iteration_zero(Ctx &c) {
   if (rc) return rc;
   CK(cudaMemsetAsync(c.depth, 0, sizeof(float) * c.H * c.W, c.stream), "depth reset");
   return run_depth(c);
+}
+
+// One IRT iteration enqueued on the context stream.  With `captured`, the trace
+// reads the iteration index from iter_dev and the iteration ends by advancing it,
+// so that a captured copy can be replayed for every iteration; stage timing events
+// are then left out.
+int enqueue_iteration(Ctx &c, int spp, int bounces, uint64_t seed, bool captured) {
+  int rc;
+  CK(cudaMemcpyAsync(c.depth_prev, c.depth, sizeof(float) * c.H * c.W, cudaMemcpyDeviceToDevice, c.stream),
+     "iterate");
+  if ((rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, c.t, 0u, c.lbar, nullptr, captured))) return rc;
+  if (captured) {
+    CK(irtps::launch_ps(c, false), "ps launch");
+    CK(irtps::solve_depth_async(c), "depth solve launch");
+  } else {
+    if ((rc = run_ps(c, false))) return rc;
+    if ((rc = run_depth(c))) return rc;
+  }
+  CK(irtps::depth_change_async(c), "depth change");
+  if (captured) CK(irtps::launch_next_iter(c), "iteration counter");
+  return IRTPS_OK;
+}
+
+// Capture one iteration as a CUDA graph (again when spp, bounces or seed change).
+int capture_iteration(Ctx &c, int spp, int bounces, uint64_t seed) {
+  if (c.graph && c.graph_spp == spp && c.graph_bounces == bounces && c.graph_seed == seed) return IRTPS_OK;
+  if (c.graph) {
+    cudaGraphExecDestroy(c.graph);
+    c.graph = nullptr;
+  }
+  CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+  const unsigned long long launches = c.stats.launches;
+  int rc = enqueue_iteration(c, spp, bounces, seed, true);
+  c.stats.launches = launches;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c.stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
+  const cudaError_t e2 = cudaGraphInstantiate(&c.graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    c.graph = nullptr;
+    return cuda_fail(c, e2, "graph instantiate");
+  }
+  c.graph_spp = spp;
+  c.graph_bounces = bounces;
+  c.graph_seed = seed;
+  return IRTPS_OK;
 }
 
 }  // namespace
@@ -163,6 +250,7 @@ void irtps_default_options(irtps_options *opt) {
   opt->cg_check_every = 10;
   opt->stop_tol = 0.0;
   opt->precond = 1;
+  opt->use_graph = 0;
 }
 
 int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *lights, const float *env, int EH,
@@ -259,7 +347,8 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
       (rc = dalloc(c, &c.cg_r, P, "cg")) || (rc = dalloc(c, &c.cg_z, P, "cg")) ||
       (rc = dalloc(c, &c.cg_p, 2 * P, "cg")) || (rc = dalloc(c, &c.cg_ap, 2 * P, "cg")) ||
       (rc = dalloc(c, &c.part, (size_t)irtps::kPartSlots * c.part_stride, "partials")) ||
-      (rc = dalloc(c, &c.counts, irtps::kCounters, "counters")) ||
+      (rc = dalloc(c, &c.dstats, 1, "statistics")) || (rc = dalloc(c, &c.next_item, 1, "work counter")) ||
+      (rc = dalloc(c, &c.iter_dev, 1, "iteration counter")) ||
       (rc = dalloc(c, (irtps::CGCtl **)&c.cg_ctl, 1, "solver control")))
     return bail(rc);
   {  // multigrid hierarchy: layout and Galerkin weights built on the host once
@@ -315,8 +404,8 @@ int irtps_set_images(irtps_ctx *ctx, const void *images, int dtype, int on_devic
   if (rc) return rc;
   c.have_images = true;
   c.t = 0;
-  reset_timers(c);
-  return iteration_zero(c);
+  if ((rc = begin_call(c)) || (rc = iteration_zero(c))) return rc;
+  return end_call(c, true);
 }
 
 int irtps_iterate(irtps_ctx *ctx, int n_iter, int spp, int bounces, uint64_t seed, double *out_dH) {
@@ -325,51 +414,60 @@ int irtps_iterate(irtps_ctx *ctx, int n_iter, int spp, int bounces, uint64_t see
   if (!c.have_images) return fail(c, IRTPS_ENOTREADY, "iterate: call irtps_set_images first");
   if (n_iter < 0 || !trace_args_ok(c, spp, bounces)) return fail(c, IRTPS_EINVAL, c.err.empty() ? "iterate" : c.err);
   c.stats.iterations_done = 0;
-  reset_timers(c);
-  unsigned long long prim = 0, segs = 0;
+  int rc = begin_call(c);
+  if (rc) return rc;
+  if (c.opt.use_graph && n_iter > 0) {
+    if ((rc = capture_iteration(c, spp, bounces, seed))) return rc;
+    CK(cudaMemcpyAsync(c.iter_dev, &c.t, sizeof(uint32_t), cudaMemcpyHostToDevice, c.stream), "iteration counter");
+  }
+  // One iteration is enqueued without host round trips; the host waits once at
+  // the end (and after each iteration only when early stopping is requested).
   for (int it = 0; it < n_iter; ++it) {
-    CK(cudaMemcpyAsync(c.depth_prev, c.depth, sizeof(float) * c.H * c.W, cudaMemcpyDeviceToDevice, c.stream),
-       "iterate");
-    int rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, c.t, 0u, c.lbar, nullptr);
-    if (rc) return rc;
-    prim += c.stats.primary_segments;
-    segs += c.stats.segments;
-    rc = run_ps(c, false);
-    if (rc) return rc;
-    rc = run_depth(c);
-    if (rc) return rc;
-    rc = irtps::depth_change(c, &c.stats.dH_max, &c.stats.dH_rms);
-    if (rc) return rc;
+    if (c.opt.use_graph) {
+      CK(cudaGraphLaunch(c.graph, c.stream), "graph launch");
+      c.stats.primary_segments += (unsigned long long)c.H * c.W * c.K * spp;
+    } else if ((rc = enqueue_iteration(c, spp, bounces, seed, false))) {
+      return rc;
+    }
     ++c.t;
     c.stats.iterations_done = it + 1;
-    if (c.opt.stop_tol > 0.0 && c.stats.dH_max < c.opt.stop_tol) break;
+    if (c.opt.stop_tol > 0.0) {
+      double dh = 0.0;
+      CK(cudaMemcpyAsync(&dh, &c.dstats->dh_max, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "D_H");
+      CK(cudaStreamSynchronize(c.stream), "D_H");
+      if (dh < c.opt.stop_tol) break;
+    }
   }
-  c.stats.primary_segments = prim;
-  c.stats.segments = segs;
+  rc = end_call(c, c.stats.iterations_done > 0);
   if (out_dH) *out_dH = c.stats.dH_max;
-  return IRTPS_OK;
+  return rc;
 }
 
 int irtps_trace(irtps_ctx *ctx, int spp, int bounces, uint64_t seed, uint32_t iteration, uint32_t stream_tag) {
   if (!ctx) return IRTPS_EINVAL;
   Ctx &c = ctx->c;
   if (!trace_args_ok(c, spp, bounces) || stream_tag > 15) return fail(c, IRTPS_EINVAL, "trace: bad arguments");
-  reset_timers(c);
-  return trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, iteration, stream_tag, c.lbar, nullptr);
+  int rc = begin_call(c);
+  if (rc || (rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, iteration, stream_tag, c.lbar, nullptr)))
+    return rc;
+  return end_call(c, false);
 }
 
 int irtps_solve_normals(irtps_ctx *ctx) {
   if (!ctx) return IRTPS_EINVAL;
   Ctx &c = ctx->c;
   if (!c.have_images) return fail(c, IRTPS_ENOTREADY, "solve_normals: call irtps_set_images first");
-  reset_timers(c);
-  return run_ps(c, false);
+  int rc = begin_call(c);
+  if (rc || (rc = run_ps(c, false))) return rc;
+  return end_call(c, false);
 }
 
 int irtps_integrate(irtps_ctx *ctx) {
   if (!ctx) return IRTPS_EINVAL;
-  reset_timers(ctx->c);
-  return run_depth(ctx->c);
+  Ctx &c = ctx->c;
+  int rc = begin_call(c);
+  if (rc || (rc = run_depth(c))) return rc;
+  return end_call(c, true);
 }
 
 int irtps_trace_pixels(irtps_ctx *ctx, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
@@ -393,7 +491,9 @@ int irtps_trace_pixels(irtps_ctx *ctx, const int32_t *pixels, int n_pix, int spp
   }
   cudaError_t e = cudaMemcpyAsync(d_pix, pixels, sizeof(int32_t) * n_pix, cudaMemcpyHostToDevice, c.stream);
   if (e == cudaSuccess) {
-    rc = trace_into(c, d_pix, n_pix, spp, bounces, seed, iteration, stream_tag, d_out, d_rec);
+    rc = begin_call(c);
+    if (rc == IRTPS_OK) rc = trace_into(c, d_pix, n_pix, spp, bounces, seed, iteration, stream_tag, d_out, d_rec);
+    if (rc == IRTPS_OK) rc = end_call(c, false);
     if (rc == IRTPS_OK) {
       e = cudaMemcpyAsync(out_lbar, d_out, sizeof(float) * c.K * c.C * n_pix, cudaMemcpyDeviceToHost, c.stream);
       if (e == cudaSuccess && out_rec)
@@ -452,8 +552,10 @@ int irtps_render(irtps_ctx *ctx, int spp, int bounces, uint64_t seed, float sigm
   if (!ctx) return IRTPS_EINVAL;
   Ctx &c = ctx->c;
   if (!out || !trace_args_ok(c, spp, bounces) || !(sigma >= 0.0f)) return fail(c, IRTPS_EINVAL, "render: bad arguments");
-  int rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, 0xFFFFFFFFu, 1u, c.lbar, nullptr);
-  if (rc) return rc;
+  int rc = begin_call(c);
+  if (rc || (rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, 0xFFFFFFFFu, 1u, c.lbar, nullptr)) ||
+      (rc = end_call(c, false)))
+    return rc;
   const size_t n = (size_t)c.K * c.C * c.H * c.W;
   float *dst = out;
   float *tmp = nullptr;
@@ -527,9 +629,6 @@ int irtps_probe_rays(irtps_ctx *ctx, int n, const float *rays, float *out_t, int
   Ctx &c = ctx->c;
   if (n < 1 || !rays || !out_t || !out_tri) return fail(c, IRTPS_EINVAL, "probe_rays: bad arguments");
   CK(irtps::build_pyramid(c), "pyramid build");
-  CK(cudaMemcpyAsync(&c.zmax, c.pmax + c.off[c.levels - 1], sizeof(float), cudaMemcpyDeviceToHost, c.stream),
-     "pyramid top");
-  CK(cudaStreamSynchronize(c.stream), "pyramid top");
   float *dr = nullptr, *dt = nullptr;
   int32_t *dtri = nullptr;
   int *dov = nullptr;

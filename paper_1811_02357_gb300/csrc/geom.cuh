@@ -147,20 +147,26 @@ struct Field {
   int levels;
   int off[kMaxLevels];
   int lw[kMaxLevels];
-  float zmax_margin;        // (max height) + 1e-4, the upward-escape bound
-  float dz;                 // node-skip margin on heights
 };
 
 struct LevelTable {
   int off[kMaxLevels];
   int lw[kMaxLevels];
+  float zmax_margin;  // (max height) + 1e-4: above it a rising ray can hit nothing
+  float dz;           // node-skip margin on heights, 1e-5 (1 + |max height|)
 };
 
-// Copy the level table of f into shared memory (whole block; ends with a barrier).
+// Copy the level table of f into shared memory and derive the height bounds from
+// the top pyramid node (whole block; ends with a barrier).
 __device__ __forceinline__ void load_levels(const Field &f, LevelTable *t) {
   if (threadIdx.x < kMaxLevels) {
     t->off[threadIdx.x] = f.off[threadIdx.x];
     t->lw[threadIdx.x] = f.lw[threadIdx.x];
+  }
+  if (threadIdx.x == 0) {
+    const float zmax = __ldg(f.pmax + f.off[f.levels - 1]);
+    t->zmax_margin = zmax + 1e-4f;
+    t->dz = 1e-5f * (1.0f + fabsf(zmax));
   }
   __syncthreads();
 }
@@ -317,10 +323,10 @@ __device__ __forceinline__ bool walker_finish_walk(Walker &m) {
   return true;
 }
 
-__device__ __forceinline__ bool walker_walk_over(const Walker &m, const Field &f) {
+__device__ __forceinline__ bool walker_walk_over(const Walker &m, const Field &f, const LevelTable &lt) {
   return (unsigned)m.cx >= (unsigned)f.Wc || (unsigned)m.cy >= (unsigned)f.Hc ||
          (m.btri >= 0 && m.t_entry > radd(m.bt, kHitMargin)) ||
-         (m.d.z > 0.0f && radd(m.o.z, rmul(m.t_entry, m.d.z)) > f.zmax_margin);
+         (m.d.z > 0.0f && radd(m.o.z, rmul(m.t_entry, m.d.z)) > lt.zmax_margin);
 }
 
 // Node step.  Returns true when the march is over; sets at_leaf when the walker
@@ -328,7 +334,7 @@ __device__ __forceinline__ bool walker_walk_over(const Walker &m, const Field &f
 __device__ __forceinline__ bool walker_node_step(Walker &m, const Field &f, const LevelTable &lt, Work &w,
                                                  bool &at_leaf) {
   const float inf = __int_as_float(0x7f800000);
-  if (walker_walk_over(m, f)) return walker_finish_walk(m);
+  if (walker_walk_over(m, f, lt)) return walker_finish_walk(m);
   const int sx = m.d.x > 0.0f ? 1 : (m.d.x < 0.0f ? -1 : 0);
   const int sy = m.d.y > 0.0f ? 1 : (m.d.y < 0.0f ? -1 : 0);
   const int lv = m.lv;
@@ -342,7 +348,7 @@ __device__ __forceinline__ bool walker_node_step(Walker &m, const Field &f, cons
   const float t_exit = fminf(tX, tY);
   // lowest height of the ray over the node: at entry when rising, else at exit
   const float zlow = fmaf(m.d.z >= 0.0f ? m.t_entry : t_exit, m.d.z, m.o.z);
-  if (zlow > nmax + f.dz) {
+  if (zlow > nmax + lt.dz) {
     if (t_exit == inf) return walker_finish_walk(m);  // vertical ray above everything below it
     if (tX < tY) {
       m.cx = sx > 0 ? X1 : X0 - 1;

@@ -14,6 +14,33 @@ namespace irtps {
 
 constexpr int kMaxLights = 64;
 
+// Control block of the cooperative depth-solve loop (see poisson.cu).
+struct CGCtl {
+  unsigned count, gen;  // grid-barrier state
+  int err;              // a barrier poll ran out
+  int iters;            // iterations of the last solve
+  double rel;           // FP64 |b - A x| / |b| (start, then at the end)
+  double bnorm;         // |b|; 0 for a flat right-hand side
+};
+
+// Accumulated over the depth solves of one call (read once at its end).
+struct CGAcc {
+  unsigned long long iters;  // all iterations
+  double rel_last;           // relative residual of the last solve
+  int err;                   // some barrier timed out
+  int bad;                   // some solve ended above tolerance or non-finite
+  int last_iters;            // iterations of the last solve
+  int pad;
+};
+
+// Device-side results of one call, read by the host once at its end.
+struct DevStats {
+  unsigned long long counts[8];  // {unused, segments, walk overflows, node visits, triangle tests, draws}
+  CGAcc cg;
+  double dh_max, dh_rms;         // D_H of the last iteration
+};
+constexpr int kCounters = 6;  // used slots of DevStats::counts
+
 struct Ctx {
   int H = 0, W = 0, K = 0, C = 0, EH = 0, EW = 0;
   uint32_t obj = 0;
@@ -43,7 +70,6 @@ struct Ctx {
   int levels = 0;
   int trace_blocks = 0;           // resident blocks of the persistent trace grid (0: one lane per item)
   int off[kMaxLevels] = {0}, lw[kMaxLevels] = {0}, lh[kMaxLevels] = {0};
-  float zmax = 0.0f;              // host copy of the top pyramid node
   // depth solve
   double *cg_x = nullptr, *cg_b = nullptr;
   float *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_ap = nullptr;
@@ -55,8 +81,16 @@ struct Ctx {
   int mg_levels = 0;
   int mg_h[kMaxLevels] = {0}, mg_w[kMaxLevels] = {0}, mg_off[kMaxLevels] = {0};
   float *mg_x0 = nullptr, *mg_x1 = nullptr, *mg_b = nullptr, *mg_wh = nullptr, *mg_wv = nullptr;
-  unsigned long long *counts = nullptr;  // {unused, segments, walk overflows, node visits, triangle tests, sampled directions}
+  DevStats *dstats = nullptr;     // device counters of the current call
+  unsigned *next_item = nullptr;  // work-item counter of the trace launch
+  uint32_t *iter_dev = nullptr;   // IRT iteration index read by replayed graphs
+  cudaGraphExec_t graph = nullptr;  // one captured IRT iteration
+  int graph_spp = 0, graph_bounces = 0;
+  uint64_t graph_seed = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> tev;   // start/stop event pairs of the timed stages of one call
+  std::vector<int> tev_stage;     // stage of each pair (trace, PS, depth)
+  int tev_used = 0;
   irtps_stats stats{};
 
   Field field() const {
@@ -72,28 +106,17 @@ struct Ctx {
       f.off[l] = off[l];
       f.lw[l] = lw[l];
     }
-    f.zmax_margin = zmax + 1e-4f;
-    float a = zmax < 0 ? -zmax : zmax;
-    f.dz = 1e-5f * (1.0f + a);
     return f;
   }
 };
 
 constexpr int kPartSlots = 12;
 
-// Control block of the cooperative depth-solve loop (see poisson.cu).
-struct CGCtl {
-  unsigned count, gen;
-  int err;
-  int iters;
-  double rel;
-};
-constexpr int kCounters = 6;
-
 // trace.cu
 cudaError_t build_pyramid(Ctx &c);
 cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
-                         uint32_t iter, uint32_t stream, float *out, int32_t *rec);
+                         uint32_t iter, uint32_t stream, float *out, int32_t *rec, bool iter_from_device = false);
+cudaError_t launch_next_iter(Ctx &c);  // iter_dev += 1 (end of a captured iteration)
 cudaError_t launch_render(Ctx &c, uint64_t seed, float sigma, const float *lbar, float *out);
 int trace_grid_limit(int C);  // resident blocks of the trace kernel, 0 if unknown
 cudaError_t launch_probe_dirs(cudaStream_t s, int n, const float *normals, const uint32_t *x0, const uint32_t *x1,
@@ -102,8 +125,9 @@ cudaError_t launch_probe_rays(Ctx &c, int n, const float *rays, float *t_out, in
 // ps.cu
 cudaError_t launch_ps(Ctx &c, bool zero_indirect);
 // poisson.cu
-int solve_depth(Ctx &c);          // IRTPS_OK or an error code (message in c.err)
-int depth_change(Ctx &c, double *dH_max, double *dH_rms);
+cudaError_t solve_depth_async(Ctx &c);  // enqueue one depth solve (results accumulate in dstats->cg)
+cudaError_t depth_change_async(Ctx &c);  // enqueue D_H of depth against depth_prev into dstats
+int solve_depth(Ctx &c);                 // one solve, waited for (IRTPS_OK or an error code, message in c.err)
 int cg_grid_limit();  // co-resident blocks available to the cooperative solve
 void mg_layout(int H, int W, int *levels, int *h, int *w, int *off, int *total);
 void mg_weights(int levels, const int *h, const int *w, const int *off, float *wh, float *wv);

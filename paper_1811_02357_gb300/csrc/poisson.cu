@@ -109,7 +109,7 @@ __device__ __forceinline__ void slopes(const float4 *nrm, size_t p, float nz_min
 
 // b = D^T g (FP64) and |b|^2 partials.
 __global__ void __launch_bounds__(kThreads) k_rhs(const CG g) {
-  __shared__ double sh[kThreads / 32 + 1 > 33 ? kThreads / 32 + 1 : 33];
+  __shared__ double sh[33];
   double bb = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
     const int i = p / g.W, j = p - i * g.W;
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kThreads) k_load_x(const CG g) {
 
 // True residual r = b - A x in FP64 (stored FP32), z = r / deg, partials of r.z and |r|^2 (FP64).
 __global__ void __launch_bounds__(kThreads) k_residual(const CG g, int rz_slot) {
-  __shared__ double sh[kThreads / 32 + 1 > 33 ? kThreads / 32 + 1 : 33];
+  __shared__ double sh[33];
   double rz = 0.0, rr = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
     const int i = p / g.W, j = p - i * g.W;
@@ -429,8 +429,8 @@ __device__ void mg_vcycle(const MG &m, const float *r, CGCtl *ctl) {
 // FP64 across blocks; every block sums the same partials in the same order and
 // so takes the same decisions.
 template <int PRE>
-__global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, double bnorm, double tol,
-                                                      int max_iter, int check, const MG mg) {
+__global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, CGAcc *acc, double tol, int max_iter,
+                                                      int check, const MG mg) {
   __shared__ double sh[33];
   __shared__ float shf[33];
   __shared__ float s_ab[2];
@@ -438,6 +438,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, do
   double best = INFINITY;
   int stall = 0, it = 0;
   double rel = ctl->rel;
+  const double bnorm = ctl->bnorm;
+  if (!(bnorm > 0.0) || !isfinite(bnorm)) rel = 0.0;  // flat (or broken) right-hand side: nothing to solve
   float *e = g.ap + g.P;  // correction accumulator (second half of the Ap buffer)
   float *z = PRE == 1 ? mg.x1 : g.z;  // preconditioned residual (level 0 of the hierarchy for PRE 1)
   for (Stride q(g.W); q.p < g.P; q.next(g.W)) e[q.p] = 0.0f;
@@ -465,7 +467,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, do
       if (refresh) g.part[S_RZREF * g.stride + blockIdx.x] = (double)rz;
     }
   };
-  if (PRE == 1) {  // the residual kernel left r; z and r.z come from the V-cycle
+  if (PRE == 1 && rel > tol) {  // the residual kernel left r; z and r.z come from the V-cycle
     precondition(S_RZ0, true);
     grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
   }
@@ -552,22 +554,50 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, do
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->iters = it;
     ctl->rel = rel;
+    if (acc) {
+      acc->iters += it;
+      acc->last_iters = it;
+      acc->rel_last = rel;
+      if (*(volatile int *)&ctl->err) acc->err = 1;
+      if (!isfinite(bnorm) || !isfinite(rel) || rel > tol) acc->bad = 1;
+    }
+  }
+}
+
+// Start of a solve: |b| and the warm start's relative residual from the partials,
+// barrier state reset (one warp).
+__global__ void k_cg_start(const CG g, CGCtl *ctl) {
+  double bb = 0.0, rr = 0.0;
+  for (int i = threadIdx.x; i < g.nblk; i += 32) {
+    bb += g.part[S_BB * g.stride + i];
+    rr += g.part[S_RR * g.stride + i];
+  }
+  bb = warp_sum(bb);
+  rr = warp_sum(rr);
+  if (threadIdx.x == 0) {
+    ctl->count = 0u;
+    ctl->gen = 0u;
+    ctl->err = 0;
+    ctl->iters = 0;
+    ctl->bnorm = sqrt(bb);
+    ctl->rel = bb > 0.0 ? sqrt(rr) / sqrt(bb) : 0.0;
   }
 }
 
 __global__ void __launch_bounds__(kThreads) k_sum_x(const CG g) {
-  __shared__ double sh[kThreads / 32 + 1 > 33 ? kThreads / 32 + 1 : 33];
+  __shared__ double sh[33];
   double s = 0.0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) s += g.x[p];
   s = block_reduce<false>(s, sh);
   if (threadIdx.x == 0) g.part[S_SUMX * g.stride + blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(kThreads) k_store_depth(const CG g) {
-  __shared__ double sh[kThreads / 32 + 1 > 33 ? kThreads / 32 + 1 : 33];
+__global__ void __launch_bounds__(kThreads) k_store_depth(const CG g, const CGCtl *ctl) {
+  __shared__ double sh[33];
   const double mean = total(g.part + S_SUMX * g.stride, g.nblk, sh) / (double)g.P;
+  const bool flat = !(ctl->bnorm > 0.0);  // zero slopes everywhere: the surface is the plane H = 0
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x)
-    g.depth[p] = (float)(g.x[p] - mean);
+    g.depth[p] = flat ? 0.0f : (float)(g.x[p] - mean);
 }
 
 __global__ void __launch_bounds__(kThreads) k_zero_depth(const CG g) {
@@ -576,7 +606,7 @@ __global__ void __launch_bounds__(kThreads) k_zero_depth(const CG g) {
 
 // D_H partials: max |H_new - H_old|, sum (H_new - H_old)^2, max H_new, -min H_new.
 __global__ void __launch_bounds__(kThreads) k_depth_change(const CG g, const float *old) {
-  __shared__ double sh[kThreads / 32 + 1 > 33 ? kThreads / 32 + 1 : 33];
+  __shared__ double sh[33];
   double dmax = 0.0, dsq = 0.0, hmax = -INFINITY, hmin = -INFINITY;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
     const double a = g.depth[p], d = a - (double)old[p];
@@ -690,124 +720,75 @@ static CG make_cg(Ctx &c) {
   return g;
 }
 
-// Copy one partial slot to the host and combine it there (fixed order).
-static int read_slot(Ctx &c, int slot, bool is_max, double *out) {
-  cudaError_t e = cudaMemcpyAsync(c.h_part, c.part + (size_t)slot * c.part_stride, sizeof(double) * c.cg_blocks,
-                                  cudaMemcpyDeviceToHost, c.stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+#define LAUNCH_CHECK()                      \
+  do {                                      \
+    cudaError_t e_ = cudaGetLastError();    \
+    if (e_ != cudaSuccess) return e_;       \
+  } while (0)
+
+// D_H of the last iteration into the device statistics (one warp).
+__global__ void k_dh_final(const CG g, DevStats *ds) {
+  double dmax = 0.0, dsq = 0.0, hmax = -INFINITY, hmin = -INFINITY;
+  for (int i = threadIdx.x; i < g.nblk; i += 32) {
+    dmax = fmax(dmax, g.part[S_DMAX * g.stride + i]);
+    dsq += g.part[S_DSQ * g.stride + i];
+    hmax = fmax(hmax, g.part[S_HMAX * g.stride + i]);
+    hmin = fmax(hmin, g.part[S_HMIN * g.stride + i]);
+  }
+  dmax = warp_max(dmax);
+  dsq = warp_sum(dsq);
+  hmax = warp_max(hmax);
+  hmin = warp_max(hmin);
+  if (threadIdx.x == 0) {
+    const double range = hmax + hmin;  // max H - min H
+    ds->dh_max = range > 0.0 ? dmax / range : 0.0;
+    ds->dh_rms = sqrt(dsq / (double)g.P);
+  }
+}
+
+// One depth solve, enqueued without host round trips: right-hand side, warm
+// start, residual, |b| on the device, the cooperative PCG loop, mean removal.
+cudaError_t solve_depth_async(Ctx &c) {
+  const CG g = make_cg(c);
+  const int nb = c.cg_blocks;
+  CGCtl *ctl = (CGCtl *)c.cg_ctl;
+  CGAcc *acc = &c.dstats->cg;
+  k_rhs<<<nb, kThreads, 0, c.stream>>>(g);
+  k_load_x<<<nb, kThreads, 0, c.stream>>>(g);
+  k_residual<<<nb, kThreads, 0, c.stream>>>(g, S_RZ0);
+  k_cg_start<<<1, 32, 0, c.stream>>>(g, ctl);
+  LAUNCH_CHECK();
+  int m = c.opt.cg_check_every > 0 ? c.opt.cg_check_every : 10;
+  double tol = c.opt.cg_tol;
+  int max_iter = c.opt.cg_max_iter;
+  const MG mg = make_mg(c);
+  void *args[] = {(void *)&g, (void *)&ctl, (void *)&acc, (void *)&tol, (void *)&max_iter, (void *)&m, (void *)&mg};
+  const void *fn = c.opt.precond == 1 ? (const void *)k_cg_loop<1> : (const void *)k_cg_loop<0>;
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(kThreads), args, 0, c.stream);
+  if (e != cudaSuccess) return e;
+  k_sum_x<<<nb, kThreads, 0, c.stream>>>(g);
+  k_store_depth<<<nb, kThreads, 0, c.stream>>>(g, ctl);
+  c.stats.launches += 7;
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+int solve_depth(Ctx &c) {
+  const cudaError_t e = solve_depth_async(c);
   if (e != cudaSuccess) {
     c.err = std::string("depth solve: ") + cudaGetErrorString(e);
     return IRTPS_ECUDA;
   }
-  double v = is_max ? -INFINITY : 0.0;
-  for (int i = 0; i < c.cg_blocks; ++i) v = is_max ? std::fmax(v, c.h_part[i]) : v + c.h_part[i];
-  *out = v;
   return IRTPS_OK;
 }
 
-#define LAUNCH_CHECK()                                              \
-  do {                                                              \
-    cudaError_t e_ = cudaGetLastError();                            \
-    if (e_ != cudaSuccess) {                                        \
-      c.err = std::string("depth solve: ") + cudaGetErrorString(e_); \
-      return IRTPS_ECUDA;                                           \
-    }                                                               \
-  } while (0)
-
-int solve_depth(Ctx &c) {
-  const CG g = make_cg(c);
-  const int nb = c.cg_blocks;
-  k_rhs<<<nb, kThreads, 0, c.stream>>>(g);
-  ++c.stats.launches;
-  LAUNCH_CHECK();
-  double bb;
-  int rc = read_slot(c, S_BB, false, &bb);
-  if (rc) return rc;
-  if (!std::isfinite(bb)) {
-    c.err = "depth solve: non-finite right-hand side";
-    return IRTPS_ENUMERIC;
-  }
-  c.stats.cg_iterations = 0;
-  c.stats.cg_rel_residual = 0.0;
-  if (bb == 0.0) {
-    k_zero_depth<<<nb, kThreads, 0, c.stream>>>(g);
-    ++c.stats.launches;
-    LAUNCH_CHECK();
-    return IRTPS_OK;
-  }
-  const double bnorm = std::sqrt(bb);
-  k_load_x<<<nb, kThreads, 0, c.stream>>>(g);
-  k_residual<<<nb, kThreads, 0, c.stream>>>(g, S_RZ0);
-  c.stats.launches += 2;
-  LAUNCH_CHECK();
-  double rr;
-  rc = read_slot(c, S_RR, false, &rr);
-  if (rc) return rc;
-  double rel = std::sqrt(rr) / bnorm;
-  int it = 0;
-  if (rel > c.opt.cg_tol) {
-    irtps::CGCtl h{0u, 0u, 0, 0, rel};
-    cudaError_t e = cudaMemcpyAsync(c.cg_ctl, &h, sizeof(h), cudaMemcpyHostToDevice, c.stream);
-    if (e != cudaSuccess) {
-      c.err = std::string("depth solve: ") + cudaGetErrorString(e);
-      return IRTPS_ECUDA;
-    }
-    const int m = c.opt.cg_check_every > 0 ? c.opt.cg_check_every : 50;
-    double tol = c.opt.cg_tol;
-    int max_iter = c.opt.cg_max_iter;
-    irtps::CGCtl *ctl = (irtps::CGCtl *)c.cg_ctl;
-    const MG mg = make_mg(c);
-    void *args[] = {(void *)&g, (void *)&ctl, (void *)&bnorm, (void *)&tol, (void *)&max_iter, (void *)&m,
-                    (void *)&mg};
-    const void *fn = c.opt.precond == 1 ? (const void *)k_cg_loop<1> : (const void *)k_cg_loop<0>;
-    e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(kThreads), args, 0, c.stream);
-    ++c.stats.launches;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c.cg_ctl, sizeof(h), cudaMemcpyDeviceToHost, c.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
-    if (e != cudaSuccess) {
-      c.err = std::string("depth solve: ") + cudaGetErrorString(e);
-      return IRTPS_ECUDA;
-    }
-    if (h.err) {
-      c.err = "depth solve: a grid barrier timed out";
-      return IRTPS_ETIMEOUT;
-    }
-    it = h.iters;
-    rel = h.rel;
-  }
-  c.stats.cg_iterations = it;
-  c.stats.cg_rel_residual = rel;
-  k_sum_x<<<nb, kThreads, 0, c.stream>>>(g);
-  k_store_depth<<<nb, kThreads, 0, c.stream>>>(g);
-  c.stats.launches += 2;
-  LAUNCH_CHECK();
-  if (!std::isfinite(rel)) {
-    c.err = "depth solve: non-finite residual";
-    return IRTPS_ENUMERIC;
-  }
-  if (rel > c.opt.cg_tol) {
-    c.err = "depth solve: relative residual " + std::to_string(rel) + " above cg_tol after " + std::to_string(it) +
-            " iterations";
-    return IRTPS_ENUMERIC;
-  }
-  return IRTPS_OK;
-}
-
-int depth_change(Ctx &c, double *dH_max, double *dH_rms) {
+cudaError_t depth_change_async(Ctx &c) {
   const CG g = make_cg(c);
   k_depth_change<<<c.cg_blocks, kThreads, 0, c.stream>>>(g, c.depth_prev);
-  ++c.stats.launches;
+  k_dh_final<<<1, 32, 0, c.stream>>>(g, c.dstats);
+  c.stats.launches += 2;
   LAUNCH_CHECK();
-  double dmax, dsq, hmax, hmin;
-  int rc = read_slot(c, S_DMAX, true, &dmax);
-  if (!rc) rc = read_slot(c, S_DSQ, false, &dsq);
-  if (!rc) rc = read_slot(c, S_HMAX, true, &hmax);
-  if (!rc) rc = read_slot(c, S_HMIN, true, &hmin);
-  if (rc) return rc;
-  const double range = hmax + hmin;  // max H - min H
-  *dH_max = range > 0.0 ? dmax / range : 0.0;
-  *dH_rms = std::sqrt(dsq / (double)g.P);
-  return IRTPS_OK;
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------
@@ -829,18 +810,9 @@ constexpr size_t kNaP = kNaZ + 4ull * kNoAllocMaxPixels;               // p: 2 x
 constexpr size_t kNaAp = kNaP + 8ull * kNoAllocMaxPixels;              // Ap and correction: 2 x floats
 constexpr size_t kNaPart = kNaAp + 8ull * kNoAllocMaxPixels;           // partials: doubles
 constexpr size_t kNaCtl = kNaPart + 8ull * kPartSlots * kNoAllocMaxBlocks;
-constexpr size_t kNaScal = kNaCtl + 256;                                // two scalar totals
-constexpr size_t kNaBytes = kNaScal + 256;
+constexpr size_t kNaBytes = kNaCtl + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
-
-// Sum of n partials into *out (one warp, fixed order).
-__global__ void k_total_to(const double *part, int n, double *out) {
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += 32) v += part[i];
-  v = warp_sum(v);
-  if (threadIdx.x == 0) *out = v;
-}
 
 // Device address of the scratch array on the current device: looked up once per
 // device (the first call on a device does it) and cached.
@@ -856,13 +828,6 @@ static unsigned char *noalloc_base() {
     base[dev] = (unsigned char *)p;
   }
   return base[dev];
-}
-
-static int noalloc_read(cudaStream_t s, const double *part, int n, double *scal, double *out) {
-  k_total_to<<<1, 32, 0, s>>>(part, n, scal);
-  if (cudaGetLastError() != cudaSuccess) return IRTPS_ECUDA;
-  if (cudaMemcpyAsync(out, scal, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return IRTPS_ECUDA;
-  return cudaStreamSynchronize(s) == cudaSuccess ? IRTPS_OK : IRTPS_ECUDA;
 }
 
 }  // namespace irtps
@@ -897,45 +862,27 @@ extern "C" int irtps_integrate_noalloc(const float *normals, int H, int W, float
   g.stride = kNoAllocMaxBlocks;
   g.nblk = nb;
   CGCtl *ctl = reinterpret_cast<CGCtl *>(base + kNaCtl);
-  double *scal = reinterpret_cast<double *>(base + kNaScal);
 
   k_rhs<<<nb, kThreads, 0, s>>>(g);
-  if (cudaGetLastError() != cudaSuccess) return IRTPS_ECUDA;
-  double bb = 0.0;
-  int rc = noalloc_read(s, g.part + S_BB * g.stride, nb, scal, &bb);
-  if (rc) return rc;
-  if (!std::isfinite(bb)) return IRTPS_ENUMERIC;
-  if (bb == 0.0) {
-    k_zero_depth<<<nb, kThreads, 0, s>>>(g);
-    if (cudaGetLastError() != cudaSuccess) return IRTPS_ECUDA;
-    return cudaStreamSynchronize(s) == cudaSuccess ? IRTPS_OK : IRTPS_ECUDA;
-  }
-  double bnorm = std::sqrt(bb);
   k_load_x<<<nb, kThreads, 0, s>>>(g);
   k_residual<<<nb, kThreads, 0, s>>>(g, S_RZ0);
+  k_cg_start<<<1, 32, 0, s>>>(g, ctl);  // also clears the barrier state left by the previous call
   if (cudaGetLastError() != cudaSuccess) return IRTPS_ECUDA;
-  double rr = 0.0;
-  rc = noalloc_read(s, g.part + S_RR * g.stride, nb, scal + 1, &rr);
-  if (rc) return rc;
-  double rel = std::sqrt(rr) / bnorm;
-  if (rel > tol) {
-    CGCtl h{0u, 0u, 0, 0, rel};  // barrier counters start at zero on every call
-    if (cudaMemcpyAsync(ctl, &h, sizeof(h), cudaMemcpyHostToDevice, s) != cudaSuccess) return IRTPS_ECUDA;
-    int m = 50;
-    const MG none{};
-    void *args[] = {(void *)&g, (void *)&ctl, (void *)&bnorm, (void *)&tol, (void *)&max_iter, (void *)&m,
-                    (void *)&none};
-    if (cudaLaunchCooperativeKernel((const void *)k_cg_loop<0>, dim3(nb), dim3(kThreads), args, 0, s) != cudaSuccess)
-      return IRTPS_ECUDA;
-    if (cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return IRTPS_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return IRTPS_ECUDA;
-    if (h.err) return IRTPS_ETIMEOUT;
-    rel = h.rel;
-  }
+  int m = 10;
+  const MG none{};
+  CGAcc *acc = nullptr;
+  void *args[] = {(void *)&g, (void *)&ctl, (void *)&acc, (void *)&tol, (void *)&max_iter, (void *)&m, (void *)&none};
+  if (cudaLaunchCooperativeKernel((const void *)k_cg_loop<0>, dim3(nb), dim3(kThreads), args, 0, s) != cudaSuccess)
+    return IRTPS_ECUDA;
   k_sum_x<<<nb, kThreads, 0, s>>>(g);
-  k_store_depth<<<nb, kThreads, 0, s>>>(g);
+  k_store_depth<<<nb, kThreads, 0, s>>>(g, ctl);
   if (cudaGetLastError() != cudaSuccess) return IRTPS_ECUDA;
+  CGCtl h;
+  if (cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return IRTPS_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return IRTPS_ECUDA;
-  return (std::isfinite(rel) && rel <= tol) ? IRTPS_OK : IRTPS_ENUMERIC;
+  if (h.err) return IRTPS_ETIMEOUT;
+  if (!std::isfinite(h.bnorm)) return IRTPS_ENUMERIC;
+  return (std::isfinite(h.rel) && h.rel <= tol) ? IRTPS_OK : IRTPS_ENUMERIC;
 }
+
 

@@ -128,6 +128,7 @@ struct TraceArgs {
   int32_t *rec;           // optional n_pix*K*spp*B*2
   unsigned long long *counts;  // {unused, segments, walk overflows, node visits, triangle tests, draws}
   unsigned *next_item;         // work-item counter, zero before the launch
+  const uint32_t *iter_dev;    // when set, the iteration field is read here (graph replays)
   float3 light[kMaxLights];
 };
 
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
     return F3{l3.x, l3.y, l3.z};
   };
   const int budget0 = 8 * (a.f.Wc + a.f.Hc + 8) * (a.f.levels + 1);
+  const uint32_t iter = a.iter_dev ? *a.iter_dev : a.iter;
 
   int phase = alive ? PH_SETUP : PH_DONE;
   int s = 0, b = 1, qp = 0, budget = budget0;
@@ -246,7 +248,8 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
       const int lane = threadIdx.x & 31;
       const int leader = __ffs(need) - 1;
       unsigned base = 0;
-      if (lane == leader) base = atomicAdd(a.next_item, (unsigned)__popc(need));
+      // the counter counts claims beyond the lanes' start items (one per thread of the grid)
+      if (lane == leader) base = atomicAdd(a.next_item, (unsigned)__popc(need)) + gridDim.x * blockDim.x;
       base = __shfl_sync(0xffffffffu, base, leader);
       if (item_done) {
         const unsigned mine = base + (unsigned)__popc(need & ((1u << lane) - 1u));
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
           for (int j = 0; j < 2 * a.bounces; ++j) r[j] = -2;
         }
         const uint4 x = philox4x32_10(
-            make_uint4((uint32_t)p, (uint32_t)s, ((uint32_t)k << 8) | ((uint32_t)b << 4) | a.stream, a.iter), a.key);
+            make_uint4((uint32_t)p, (uint32_t)s, ((uint32_t)k << 8) | ((uint32_t)b << 4) | a.stream, iter), a.key);
         // bounce 1 leaves the pixel's own vertex about its normal; later bounces the
         // previous hit point (m.o) about the hit pixel's normal
         const F3 org = b == 1 ? pixel_origin() : m.o;
@@ -405,14 +408,23 @@ static void fill_trace_args(const Ctx &c, TraceArgs &a) {
   a.shadow = c.opt.shadow_rays;
   a.eps = c.eps;
   a.Wf = (float)c.W;
-  a.counts = c.counts;
+  a.counts = c.dstats->counts;
   for (int k = 0; k < c.K; ++k) a.light[k] = make_float3(c.h_lights[3 * k], c.h_lights[3 * k + 1], c.h_lights[3 * k + 2]);
 }
 
+__global__ void k_next_iter(uint32_t *iter) { *iter += 1u; }
+
+cudaError_t launch_next_iter(Ctx &c) {
+  k_next_iter<<<1, 1, 0, c.stream>>>(c.iter_dev);
+  ++c.stats.launches;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
-                         uint32_t iter, uint32_t stream, float *out, int32_t *rec) {
+                         uint32_t iter, uint32_t stream, float *out, int32_t *rec, bool iter_from_device) {
   TraceArgs a;
   fill_trace_args(c, a);
+  a.iter_dev = iter_from_device ? c.iter_dev : nullptr;
   a.pixels = pixels;
   a.n_pix = n_pix;
   a.spp = spp;
@@ -427,11 +439,8 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
   // a persistent grid: as many blocks as stay resident, each lane claiming items until none remain
   long long blocks = (n + threads - 1) / threads;
   if (c.trace_blocks > 0 && blocks > c.trace_blocks) blocks = c.trace_blocks;
-  a.next_item = reinterpret_cast<unsigned *>(c.counts);  // slot 0, zeroed with the counters
-  const unsigned first_free = (unsigned)(blocks * threads);   // items taken by the lanes' start indices
-  if (cudaMemcpyAsync(a.next_item, &first_free, sizeof(unsigned), cudaMemcpyHostToDevice, c.stream) != cudaSuccess)
-    return cudaGetLastError();
-  if (cudaStreamSynchronize(c.stream) != cudaSuccess) return cudaGetLastError();
+  a.next_item = c.next_item;
+  if (cudaMemsetAsync(a.next_item, 0, sizeof(unsigned), c.stream) != cudaSuccess) return cudaGetLastError();
   ++c.stats.launches;
   if (c.C == 1)
     k_trace<1><<<(unsigned)blocks, threads, 0, c.stream>>>(a);
