@@ -193,6 +193,59 @@ int irtps_integrate_noalloc(const float *normals, int H, int W, float nz_min, do
 const char *irtps_last_error(const irtps_ctx *ctx);
 void irtps_destroy(irtps_ctx *ctx);
 
+/* Object index of a context: the `object` term of its Philox key
+ * {seed_lo ^ object, seed_hi} (0 after irtps_create). */
+int irtps_set_object(irtps_ctx *ctx, uint32_t object);
+
+/* Scheduling tunables of a context's trace, chosen by irtps_autotune or set
+ * directly.  Neither changes any result bit: work items are traced one per lane
+ * in sample order whatever the grid, and the pyramid skip lands in the cell the
+ * plain walk reaches whatever the number of levels.
+ *   blocks_per_sm : resident 128-thread blocks per SM of the persistent trace
+ *                   grid (1 .. occupancy limit; 0 = the occupancy limit)
+ *   mip_cut       : top levels of the min/max pyramid the march leaves out
+ *                   (0 = full depth; clamped so that two levels remain) */
+int irtps_set_tuning(irtps_ctx *ctx, int blocks_per_sm, int mip_cut);
+int irtps_get_tuning(irtps_ctx *ctx, int *blocks_per_sm, int *mip_cut);
+/* Time the trace of the current state with spp_probe samples for each candidate
+ * (blocks_per_sm, mip_cut) and keep the fastest.  Writes the indirect buffer
+ * (re-trace before using it).  out_ms (nullable) receives the best time. */
+int irtps_autotune(irtps_ctx *ctx, int spp_probe, int bounces, uint64_t seed, double *out_ms);
+
+/* ---- Batches: many objects, one launch per IRT stage ----
+ * A batch runs the IRT loop of n_obj contexts together: per iteration one
+ * batched pyramid launch per level, ONE persistent trace launch whose lanes take
+ * (object, light, pixel) work items from a shared queue (objects of larger
+ * per-item cost first), one PS launch, one cooperative depth-solve launch in
+ * which each object's solve runs on its own team of blocks, and one D_H launch.
+ * Objects may differ in H, W, K, spp, bounces and options; all must have the
+ * same C and image dtype.  Every object's results are bit-identical to its own
+ * irtps_iterate in the trace and the normal solve; the depth solve differs from
+ * it only by the summation order of its reductions (team size), within cg_tol.
+ *
+ * The batch keeps pointers to the caller's contexts, which must outlive it and
+ * must not be used concurrently with a batch call.  irtps_batch_create sets the
+ * object index of context i to i (irtps_set_object).  n_obj in 1..64. */
+typedef struct irtps_batch irtps_batch;
+int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int use_graph);
+/* n_iter IRT iterations of every object (each context must have images set):
+ * spp[i], bounces[i] for object i (host arrays of n_obj; bounces in 1..3); seed
+ * as in irtps_iterate.  Object i's iteration index advances by n_iter.
+ * out_dH (nullable, host, n_obj) receives each object's D_H of the last
+ * iteration.  With use_graph, one iteration is captured as a CUDA graph and
+ * replayed (re-captured when spp, bounces or seed change). */
+int irtps_batch_iterate(irtps_batch *b, int n_iter, const int *spp, const int *bounces, uint64_t seed, double *out_dH);
+/* Sums over the objects of the last irtps_batch_iterate (cg_iterations: the
+ * largest of the last solves, cg_rel_residual: the largest, dH_max: the largest). */
+int irtps_batch_get_stats(irtps_batch *b, irtps_stats *out);
+/* Trace grid of the batch, as irtps_set_tuning (mip_cut applies to every object). */
+int irtps_batch_set_tuning(irtps_batch *b, int blocks_per_sm, int mip_cut);
+int irtps_batch_get_tuning(irtps_batch *b, int *blocks_per_sm, int *mip_cut);
+/* As irtps_autotune for the batched trace launch (writes every object's indirect buffer). */
+int irtps_batch_autotune(irtps_batch *b, const int *spp_probe, const int *bounces, uint64_t seed, double *out_ms);
+const char *irtps_batch_last_error(const irtps_batch *b);
+void irtps_batch_destroy(irtps_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -426,10 +426,11 @@ def ps_step(A0, rho_t, lbar, lights, tau_lo=TAU_LO, tau_hi=TAU_HI, cond_max=COND
 
 
 def irtps_run(A0, lights, env, n_iter, spp, bounces, seed, *, shadow_rays=True, fp32=True, threads=0,
-              tau_lo=TAU_LO, tau_hi=TAU_HI):
+              tau_lo=TAU_LO, tau_hi=TAU_HI, obj=0):
     """The IRT-PS loop: iteration 0 is classic PS + integration; each further
     iteration traces Lbar on the current estimate (iteration index t), subtracts
     rho_t * Lbar_t from the ORIGINAL images, re-solves PS and re-integrates.
+    `obj` is the object index in the Philox key {seed_lo ^ obj, seed_hi}.
     Returns a list of per-iteration dicts (depth, normals, albedo, lbar, dH)."""
     A0 = np.asarray(A0, np.float32)
     K, C, H, W = A0.shape
@@ -443,7 +444,7 @@ def irtps_run(A0, lights, env, n_iter, spp, bounces, seed, *, shadow_rays=True, 
         st = hist[-1]
         lbar, _, counts = trace(st["depth"].astype(np.float32), st["normals"].astype(np.float32),
                                 st["albedo"].astype(np.float32), lights, env, spp, bounces, seed, t,
-                                shadow_rays=shadow_rays, fp32=fp32, threads=threads)
+                                obj=obj, shadow_rays=shadow_rays, fp32=fp32, threads=threads)
         n, rho, ok = ps_step(A0, st["albedo"].astype(np.float32).reshape(C, -1), lbar, lights, tau_lo,
                              tau_hi)
         depth = poisson_solve(n.reshape(H, W, 3), h)

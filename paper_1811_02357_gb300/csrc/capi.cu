@@ -1,6 +1,7 @@
 // C ABI of the IRT-PS library: context life cycle, buffers, and the stage
 // sequence of one IRT iteration (Sec. IV): pyramid -> trace -> subtract + PS ->
 // integration -> D_H.  Declarations and argument contracts: include/irtps.h.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -10,10 +11,6 @@
 #include "irtps_internal.h"
 
 using irtps::Ctx;
-
-struct irtps_ctx {
-  Ctx c;
-};
 
 namespace {
 
@@ -46,7 +43,7 @@ int dalloc(Ctx &c, T **p, size_t n, const char *what) {
 }
 
 void release(Ctx &c) {
-  void *bufs[] = {c.env, c.images, c.lbar, c.depth, c.depth_prev, c.nrm, c.albedo, c.valid, c.pmin, c.pmax,
+  void *bufs[] = {c.env, c.d_lights, c.images, c.lbar, c.depth, c.depth_prev, c.nrm, c.albedo, c.valid, c.pmin, c.pmax,
                   c.cg_x, c.cg_b, c.cg_r, c.cg_z, c.cg_p, c.cg_ap, c.part, c.dstats, c.next_item, c.cg_ctl,
                   c.mg_x0, c.mg_x1, c.mg_b, c.mg_wh, c.mg_wv, c.iter_dev};
   for (void *b : bufs)
@@ -336,8 +333,14 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
   }
   c.cg_blocks = (int)std::min<size_t>((P + 255) / 256, (size_t)irtps::cg_grid_limit());
   c.trace_blocks = irtps::trace_grid_limit(C);
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
+    c.trace_per_sm_max = c.sms > 0 ? c.trace_blocks / c.sms : 0;
+  }
   c.part_stride = c.cg_blocks;
   if ((rc = dalloc(c, &c.env, (size_t)C * EH * EW, "environment")) ||
+      (rc = dalloc(c, &c.d_lights, (size_t)K * 3, "lights")) ||
       (rc = dalloc(c, (float **)&c.images, (size_t)K * C * P, "images")) ||
       (rc = dalloc(c, &c.lbar, (size_t)K * C * P, "indirect")) || (rc = dalloc(c, &c.depth, P, "depth")) ||
       (rc = dalloc(c, &c.depth_prev, P, "depth")) || (rc = dalloc(c, &c.nrm, P, "normals")) ||
@@ -367,6 +370,8 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
   e = cudaMallocHost((void **)&c.h_part, sizeof(double) * c.part_stride);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "create: pinned partials"));
   e = cudaMemcpyAsync(c.env, env, sizeof(float) * C * EH * EW, cudaMemcpyHostToDevice, c.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c.d_lights, c.h_lights.data(), sizeof(float) * K * 3, cudaMemcpyHostToDevice, c.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c.lbar, 0, sizeof(float) * K * C * P, c.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c.depth, 0, sizeof(float) * P, c.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c.albedo, 0, sizeof(float) * C * P, c.stream);
@@ -655,6 +660,84 @@ int irtps_probe_rays(irtps_ctx *ctx, int n, const float *rays, float *out_t, int
   if (e != cudaSuccess) return cuda_fail(c, e, "probe_rays");
   if (ov) return fail(c, IRTPS_ETIMEOUT, "probe_rays: a march exhausted its step budget");
   return IRTPS_OK;
+}
+
+int irtps_set_object(irtps_ctx *ctx, uint32_t object) {
+  if (!ctx) return IRTPS_EINVAL;
+  if (ctx->c.graph) {  // a captured iteration holds the old key
+    cudaGraphExecDestroy(ctx->c.graph);
+    ctx->c.graph = nullptr;
+  }
+  ctx->c.obj = object;
+  return IRTPS_OK;
+}
+
+int irtps_set_tuning(irtps_ctx *ctx, int blocks_per_sm, int mip_cut) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (blocks_per_sm < 0 || blocks_per_sm > c.trace_per_sm_max || mip_cut < 0 || mip_cut >= irtps::kMaxLevels)
+    return fail(c, IRTPS_EINVAL, "tuning: blocks_per_sm in 0.." + std::to_string(c.trace_per_sm_max) +
+                                     ", mip_cut in 0..15");
+  c.trace_blocks = (blocks_per_sm == 0 ? c.trace_per_sm_max : blocks_per_sm) * c.sms;
+  c.mip_cut = mip_cut;
+  if (c.graph) {
+    cudaGraphExecDestroy(c.graph);
+    c.graph = nullptr;
+  }
+  return IRTPS_OK;
+}
+
+int irtps_get_tuning(irtps_ctx *ctx, int *blocks_per_sm, int *mip_cut) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (blocks_per_sm) *blocks_per_sm = c.sms > 0 ? c.trace_blocks / c.sms : 0;
+  if (mip_cut) *mip_cut = c.mip_cut;
+  return IRTPS_OK;
+}
+
+int irtps_autotune(irtps_ctx *ctx, int spp_probe, int bounces, uint64_t seed, double *out_ms) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (!trace_args_ok(c, spp_probe, bounces)) return fail(c, IRTPS_EINVAL, "autotune: bad arguments");
+  const int mx = c.trace_per_sm_max;
+  std::vector<int> per_sm;
+  for (int v : {mx, mx - 1, mx - 2, (mx + 1) / 2})
+    if (v >= 1 && std::find(per_sm.begin(), per_sm.end(), v) == per_sm.end()) per_sm.push_back(v);
+  std::vector<int> cuts;
+  for (int v = 0; v <= 3 && v < c.levels - 1; ++v) cuts.push_back(v);
+  int rc = begin_call(c);
+  if (rc) return rc;
+  double best = INFINITY;
+  int best_ps = c.trace_blocks / (c.sms > 0 ? c.sms : 1), best_cut = c.mip_cut;
+  for (int cut : cuts)
+    for (int ps : per_sm) {
+      c.trace_blocks = ps * c.sms;
+      c.mip_cut = cut;
+      for (int rep = 0; rep < 2; ++rep) {  // the first run warms the caches; the second is timed
+        c.tev_used = 0;
+        if ((rc = trace_into(c, nullptr, c.H * c.W, spp_probe, bounces, seed, c.t, 0u, c.lbar, nullptr))) break;
+      }
+      if (rc) break;
+      float ms = 0.0f;
+      CK(cudaEventSynchronize(c.tev[1]), "autotune");
+      CK(cudaEventElapsedTime(&ms, c.tev[0], c.tev[1]), "autotune");
+      if (ms < best) {
+        best = ms;
+        best_ps = ps;
+        best_cut = cut;
+      }
+    }
+  c.trace_blocks = best_ps * c.sms;
+  c.mip_cut = best_cut;
+  c.tev_used = 0;
+  if (c.graph) {
+    cudaGraphExecDestroy(c.graph);
+    c.graph = nullptr;
+  }
+  if (rc) return rc;
+  rc = end_call(c, false);
+  if (out_ms) *out_ms = best;
+  return rc;
 }
 
 const char *irtps_last_error(const irtps_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }

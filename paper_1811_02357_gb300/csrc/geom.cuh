@@ -144,7 +144,8 @@ struct Field {
   const float *depth;       // H*W
   const float *pmax;        // all levels, level l at off[l], row-major lw[l] wide
   int H, W, Wc, Hc;         // Wc = W-1, Hc = H-1 cells
-  int levels;
+  int levels;               // levels the march uses (the top one may hold several nodes)
+  int top_off;              // offset of the single node of the full pyramid (the surface maximum)
   int off[kMaxLevels];
   int lw[kMaxLevels];
 };
@@ -156,6 +157,13 @@ struct LevelTable {
   float dz;           // node-skip margin on heights, 1e-5 (1 + |max height|)
 };
 
+// Height bounds of a surface from its top pyramid node.
+__device__ __forceinline__ void set_height_bounds(const Field &f, LevelTable *t) {
+  const float zmax = __ldg(f.pmax + f.top_off);
+  t->zmax_margin = zmax + 1e-4f;
+  t->dz = 1e-5f * (1.0f + fabsf(zmax));
+}
+
 // Copy the level table of f into shared memory and derive the height bounds from
 // the top pyramid node (whole block; ends with a barrier).
 __device__ __forceinline__ void load_levels(const Field &f, LevelTable *t) {
@@ -163,11 +171,7 @@ __device__ __forceinline__ void load_levels(const Field &f, LevelTable *t) {
     t->off[threadIdx.x] = f.off[threadIdx.x];
     t->lw[threadIdx.x] = f.lw[threadIdx.x];
   }
-  if (threadIdx.x == 0) {
-    const float zmax = __ldg(f.pmax + f.off[f.levels - 1]);
-    t->zmax_margin = zmax + 1e-4f;
-    t->dz = 1e-5f * (1.0f + fabsf(zmax));
-  }
+  if (threadIdx.x == 0) set_height_bounds(f, t);
   __syncthreads();
 }
 

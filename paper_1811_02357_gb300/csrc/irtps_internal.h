@@ -41,6 +41,29 @@ struct DevStats {
 };
 constexpr int kCounters = 6;  // used slots of DevStats::counts
 
+// Per-object trace descriptor: the current surface and state estimates, the
+// environment, the lights and the output of one object.
+struct ObjTrace {
+  Field f;
+  const float4 *nrm;      // H*W (nx, ny, nz, mean albedo)
+  const float *albedo;    // C*H*W
+  const float *env;       // C*EH*EW
+  const float *lights;    // K*3, unit, z > 0
+  float *out;             // K*C*n_pix
+  uint2 key;              // Philox key {seed_lo ^ object, seed_hi}
+  int EH, EW, K, spp, bounces, n_pix, shadow;
+  float eps, Wf;          // ray-origin lift; W (grid units per world unit in x and y)
+  unsigned item_begin;    // first work item of the object (batched launches)
+  uint32_t iter0;         // added to the launch's iteration field
+};
+
+
+// Pyramid levels the march uses when the top `cut` levels are left out (at least two remain).
+inline int march_levels(int levels, int cut) {
+  const int keep = levels < 2 ? levels : 2;
+  return levels - cut > keep ? levels - cut : keep;
+}
+
 struct Ctx {
   int H = 0, W = 0, K = 0, C = 0, EH = 0, EW = 0;
   uint32_t obj = 0;
@@ -55,6 +78,7 @@ struct Ctx {
   // host copies
   std::vector<float> h_lights;    // K*3
   std::vector<float> h_pinv;      // 3*K, (L^T L)^-1 L^T rounded to float
+  float *d_lights = nullptr;      // K*3 on the device (read at trace hits)
 
   // device buffers (owned)
   float *env = nullptr;           // C*EH*EW
@@ -69,6 +93,8 @@ struct Ctx {
   float *pmin = nullptr, *pmax = nullptr;  // pyramid, all levels
   int levels = 0;
   int trace_blocks = 0;           // resident blocks of the persistent trace grid (0: one lane per item)
+  int mip_cut = 0;                // top pyramid levels the march leaves out (tuning; results do not change)
+  int sms = 0, trace_per_sm_max = 0;  // SM count; resident trace blocks per SM at full occupancy
   int off[kMaxLevels] = {0}, lw[kMaxLevels] = {0}, lh[kMaxLevels] = {0};
   // depth solve
   double *cg_x = nullptr, *cg_b = nullptr;
@@ -101,7 +127,8 @@ struct Ctx {
     f.W = W;
     f.Wc = W - 1;
     f.Hc = H - 1;
-    f.levels = levels;
+    f.levels = march_levels(levels, mip_cut);
+    f.top_off = off[levels - 1];
     for (int l = 0; l < kMaxLevels; ++l) {
       f.off[l] = off[l];
       f.lw[l] = lw[l];
@@ -112,23 +139,58 @@ struct Ctx {
 
 constexpr int kPartSlots = 12;
 
+}  // namespace irtps
+
+struct irtps_ctx {
+  irtps::Ctx c;
+};
+
+namespace irtps {
+
+// Pyramid of one object in a batched build.
+struct PyrObj {
+  const float *depth;
+  float *prev;  // when set, level 0 also copies depth here (D_H reference)
+  float *pmin, *pmax;
+  int H, W, levels;
+  int off[kMaxLevels], lw[kMaxLevels], lh[kMaxLevels];
+  int blk[kMaxLevels];  // first block of the object in the launch of each level
+};
+constexpr int kPyrThreads = 256;
+
 // trace.cu
 cudaError_t build_pyramid(Ctx &c);
+void fill_pyr_obj(const Ctx &c, PyrObj &o);
+cudaError_t build_pyramid_batch(cudaStream_t s, const PyrObj *d_objs, int n, int levels, const int *blocks);
 cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
                          uint32_t iter, uint32_t stream, float *out, int32_t *rec, bool iter_from_device = false);
 cudaError_t launch_next_iter(Ctx &c);  // iter_dev += 1 (end of a captured iteration)
+cudaError_t launch_next_iter(cudaStream_t s, uint32_t *iter_dev);
 cudaError_t launch_render(Ctx &c, uint64_t seed, float sigma, const float *lbar, float *out);
-int trace_grid_limit(int C);  // resident blocks of the trace kernel, 0 if unknown
+int trace_grid_limit(int C, int n_obj = 0);  // resident blocks of the (batched) trace kernel, 0 if unknown
+void fill_obj_trace(const Ctx &c, ObjTrace &o);  // descriptor of a context's object (no sampling fields)
+cudaError_t launch_trace_batch(cudaStream_t s, int C, const ObjTrace *d_objs, int n_obj, unsigned n_items,
+                               unsigned long long *counts, unsigned *next_item, const uint32_t *iter_dev,
+                               uint32_t iter, int grid_limit);
 cudaError_t launch_probe_dirs(cudaStream_t s, int n, const float *normals, const uint32_t *x0, const uint32_t *x1,
                               float *out);
 cudaError_t launch_probe_rays(Ctx &c, int n, const float *rays, float *t_out, int32_t *tri_out, int *overflow);
 // ps.cu
 cudaError_t launch_ps(Ctx &c, bool zero_indirect);
+size_t ps_args_bytes();
+void ps_fill_args(const Ctx &c, bool zero_indirect, int blk_begin, void *dst);
+cudaError_t launch_ps_batch(cudaStream_t s, int C, int dtype, const void *d_args, int n, int blocks);
 // poisson.cu
 cudaError_t solve_depth_async(Ctx &c);  // enqueue one depth solve (results accumulate in dstats->cg)
 cudaError_t depth_change_async(Ctx &c);  // enqueue D_H of depth against depth_prev into dstats
 int solve_depth(Ctx &c);                 // one solve, waited for (IRTPS_OK or an error code, message in c.err)
 int cg_grid_limit();  // co-resident blocks available to the cooperative solve
+// batched solves: one job per object, teams of blocks in one launch per step
+size_t cg_job_bytes();
+void cg_fill_job(Ctx &c, int nblk, int blk_begin, DevStats *ds, void *dst);
+int cg_batch_grid_limit();
+cudaError_t solve_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks);
+cudaError_t depth_change_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks);
 void mg_layout(int H, int W, int *levels, int *h, int *w, int *off, int *total);
 void mg_weights(int levels, const int *h, const int *w, const int *off, float *wh, float *wv);
 

@@ -14,6 +14,7 @@
 // against cg_tol.  Reductions are two-stage and deterministic: each block writes
 // one partial, and every consumer block sums all partials in the same order.
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -88,6 +89,13 @@ __device__ __forceinline__ int degree(int i, int j, int H, int W) {
   return (j > 0) + (j < W - 1) + (i > 0) + (i < H - 1);
 }
 
+// The blocks that work on one solve: all of a plain launch, or the range of a
+// batched launch that belongs to one object (bid = block index within it).
+struct Team {
+  int bid, nblk;
+};
+__device__ __forceinline__ Team whole_grid() { return Team{(int)blockIdx.x, (int)gridDim.x}; }
+
 struct CG {
   int H, W, P;
   double h;
@@ -108,10 +116,10 @@ __device__ __forceinline__ void slopes(const float4 *nrm, size_t p, float nz_min
 }
 
 // b = D^T g (FP64) and |b|^2 partials.
-__global__ void __launch_bounds__(kThreads) k_rhs(const CG g) {
+__device__ __forceinline__ void rhs_body(const CG &g, Team t) {
   __shared__ double sh[33];
   double bb = 0.0;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
+  for (int p = t.bid * blockDim.x + threadIdx.x; p < g.P; p += t.nblk * blockDim.x) {
     const int i = p / g.W, j = p - i * g.W;
     double pc, qc, pn, qn;
     slopes(g.nrm, p, g.nz_min, pc, qc);
@@ -124,18 +132,18 @@ __global__ void __launch_bounds__(kThreads) k_rhs(const CG g) {
     bb += v * v;
   }
   bb = block_reduce<false>(bb, sh);
-  if (threadIdx.x == 0) g.part[S_BB * g.stride + blockIdx.x] = bb;
+  if (threadIdx.x == 0) g.part[S_BB * g.stride + t.bid] = bb;
 }
 
-__global__ void __launch_bounds__(kThreads) k_load_x(const CG g) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) g.x[p] = (double)g.depth[p];
+__device__ __forceinline__ void load_x_body(const CG &g, Team t) {
+  for (int p = t.bid * blockDim.x + threadIdx.x; p < g.P; p += t.nblk * blockDim.x) g.x[p] = (double)g.depth[p];
 }
 
 // True residual r = b - A x in FP64 (stored FP32), z = r / deg, partials of r.z and |r|^2 (FP64).
-__global__ void __launch_bounds__(kThreads) k_residual(const CG g, int rz_slot) {
+__device__ __forceinline__ void residual_body(const CG &g, int rz_slot, Team t) {
   __shared__ double sh[33];
   double rz = 0.0, rr = 0.0;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
+  for (int p = t.bid * blockDim.x + threadIdx.x; p < g.P; p += t.nblk * blockDim.x) {
     const int i = p / g.W, j = p - i * g.W;
     const double res = g.b[p] - lap_at<double>(g.x, i, j, g.H, g.W);
     const float rf = (float)res;
@@ -147,23 +155,23 @@ __global__ void __launch_bounds__(kThreads) k_residual(const CG g, int rz_slot) 
   }
   rz = block_reduce<false>(rz, sh);
   if (threadIdx.x == 0) {
-    g.part[rz_slot * g.stride + blockIdx.x] = rz;
-    g.part[S_RZREF * g.stride + blockIdx.x] = rz;
+    g.part[rz_slot * g.stride + t.bid] = rz;
+    g.part[S_RZREF * g.stride + t.bid] = rz;
   }
   rr = block_reduce<false>(rr, sh);
-  if (threadIdx.x == 0) g.part[S_RR * g.stride + blockIdx.x] = rr;
+  if (threadIdx.x == 0) g.part[S_RR * g.stride + t.bid] = rr;
 }
 
-// Grid-wide barrier of a cooperative launch (all blocks co-resident).  Thread 0
-// of each block arrives on a counter; the last one resets it and advances the
+// Barrier of the nblk blocks of a team in a cooperative launch (all blocks
+// co-resident).  Thread 0 of each block arrives on a counter; the last one resets it and advances the
 // generation word the others poll.  Every poll loop is bounded: on running out it
 // raises the error flag, and all blocks leave the solve at the next check.
-__device__ __forceinline__ void grid_barrier(unsigned *count, volatile unsigned *gen, int *err) {
+__device__ __forceinline__ void grid_barrier(unsigned *count, volatile unsigned *gen, int *err, int nblk) {
   __syncthreads();
   if (threadIdx.x == 0 && !*(volatile int *)err) {  // after a failure every barrier is a no-op
     const unsigned g0 = *gen;
     __threadfence();
-    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+    if (atomicAdd(count, 1u) == (unsigned)nblk - 1u) {
       *count = 0u;
       __threadfence();
       atomicAdd((unsigned *)gen, 1u);
@@ -199,11 +207,11 @@ __device__ __forceinline__ float block_sum_f(float v, float *shf) {
 // Pixel coordinates of a grid-stride loop, advanced without divisions.
 struct Stride {
   int p, i, j, dp, di, dj;
-  __device__ __forceinline__ Stride(int W) {
-    p = blockIdx.x * blockDim.x + threadIdx.x;
+  __device__ __forceinline__ Stride(int W, Team t) {
+    p = t.bid * blockDim.x + threadIdx.x;
     i = p / W;
     j = p - i * W;
-    dp = gridDim.x * blockDim.x;
+    dp = t.nblk * blockDim.x;
     di = dp / W;
     dj = dp - di * W;
   }
@@ -294,24 +302,24 @@ __device__ __forceinline__ float mg_ax_corr(const MG &m, int l, const float *x, 
 
 // Iterate the points of level l: the whole grid (grid levels) or block 0 alone.
 #define MG_FOR(l, pt)                                                                              \
-  for (int pt = (l < m.grid_levels ? blockIdx.x * blockDim.x : 0) + threadIdx.x,                   \
-           pt##_n = m.H[l] * m.W[l], pt##_s = (l < m.grid_levels ? gridDim.x : 1) * blockDim.x; \
+  for (int pt = (l < m.grid_levels ? t.bid * (int)blockDim.x : 0) + threadIdx.x,                 \
+           pt##_n = m.H[l] * m.W[l], pt##_s = (l < m.grid_levels ? t.nblk : 1) * blockDim.x;   \
        pt < pt##_n; pt += pt##_s)
 
 // Synchronise after a step on level l: a grid barrier on grid levels, the block on block levels.
-__device__ __forceinline__ void mg_sync(const MG &m, int l, CGCtl *ctl) {
-  if (l < m.grid_levels) grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+__device__ __forceinline__ void mg_sync(const MG &m, int l, CGCtl *ctl, Team t) {
+  if (l < m.grid_levels) grid_barrier(&ctl->count, &ctl->gen, &ctl->err, t.nblk);
   else __syncthreads();
 }
 
 // z = V(r): level-0 right-hand side r (length P), result in x1 of level 0.
 // Called by all blocks; on return all of z is visible to all blocks.
-__device__ void mg_vcycle(const MG &m, const float *r, CGCtl *ctl) {
+__device__ void mg_vcycle(const MG &m, const float *r, CGCtl *ctl, Team t) {
   const float om = m.omega;
   const int L = m.levels;
   // ---- down ----
   for (int l = 0; l < L - 1; ++l) {
-    const bool active = l < m.grid_levels || blockIdx.x == 0;
+    const bool active = l < m.grid_levels || t.bid == 0;
     const float *b = l == 0 ? r : m.b + m.off[l];
     const int W = m.W[l], o = m.off[l];
     if (active) {
@@ -320,7 +328,7 @@ __device__ void mg_vcycle(const MG &m, const float *r, CGCtl *ctl) {
         m.x0[o + pt] = om * b[pt] / mg_diag(m, l, i, j);
       }
     }
-    if (l < m.grid_levels) mg_sync(m, l, ctl); else if (active) __syncthreads();
+    if (l < m.grid_levels) mg_sync(m, l, ctl, t); else if (active) __syncthreads();
     if (active) {
       MG_FOR(l, pt) {  // second sweep
         const int i = pt / W, j = pt - i * W;
@@ -329,10 +337,10 @@ __device__ void mg_vcycle(const MG &m, const float *r, CGCtl *ctl) {
         m.x1[o + pt] = m.x0[o + pt] + om * (b[pt] - ax) / d;
       }
     }
-    if (l < m.grid_levels) mg_sync(m, l, ctl); else if (active) __syncthreads();
+    if (l < m.grid_levels) mg_sync(m, l, ctl, t); else if (active) __syncthreads();
     // residual, summed over each 2x2 aggregate into the next level's right-hand side
     const int lc = l + 1;
-    const bool active_c = lc < m.grid_levels || blockIdx.x == 0;
+    const bool active_c = lc < m.grid_levels || t.bid == 0;
     if (active && active_c) {
       const int Wc = m.W[lc], Hf = m.H[l];
       MG_FOR(lc, pt) {
@@ -352,10 +360,10 @@ __device__ void mg_vcycle(const MG &m, const float *r, CGCtl *ctl) {
         m.b[m.off[lc] + pt] = sum;
       }
     }
-    if (l < m.grid_levels) mg_sync(m, l, ctl); else if (active) __syncthreads();
+    if (l < m.grid_levels) mg_sync(m, l, ctl, t); else if (active) __syncthreads();
   }
   // ---- coarsest: sweeps and a mean projection (block 0) ----
-  if (blockIdx.x == 0) {
+  if (t.bid == 0) {
     const int l = L - 1, W = m.W[l], o = m.off[l], n = m.H[l] * m.W[l];
     const float *b = L == 1 ? r : m.b + o;
     for (int q = threadIdx.x; q < n; q += blockDim.x) m.x1[o + q] = 0.0f;
@@ -382,12 +390,12 @@ __device__ void mg_vcycle(const MG &m, const float *r, CGCtl *ctl) {
   }
   // ---- up ----
   for (int l = L - 2; l >= 0; --l) {
-    const bool active = l < m.grid_levels || blockIdx.x == 0;
+    const bool active = l < m.grid_levels || t.bid == 0;
     const float *b = l == 0 ? r : m.b + m.off[l];
     const int W = m.W[l], o = m.off[l];
     // the coarse level's result must be visible before it is interpolated
     if (l + 1 == m.grid_levels || l + 1 == L - 1) {
-      if (l < m.grid_levels) grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+      if (l < m.grid_levels) grid_barrier(&ctl->count, &ctl->gen, &ctl->err, t.nblk);
       else if (active) __syncthreads();
     }
     if (active) {
@@ -398,7 +406,7 @@ __device__ void mg_vcycle(const MG &m, const float *r, CGCtl *ctl) {
         m.x0[o + pt] = xcen + om * (b[pt] - ax) / d;
       }
     }
-    if (l < m.grid_levels) mg_sync(m, l, ctl); else if (active) __syncthreads();
+    if (l < m.grid_levels) mg_sync(m, l, ctl, t); else if (active) __syncthreads();
     if (active) {
       MG_FOR(l, pt) {  // second sweep
         const int i = pt / W, j = pt - i * W;
@@ -407,9 +415,9 @@ __device__ void mg_vcycle(const MG &m, const float *r, CGCtl *ctl) {
         m.x1[o + pt] = m.x0[o + pt] + om * (b[pt] - ax) / d;
       }
     }
-    if (l < m.grid_levels) mg_sync(m, l, ctl); else if (active) __syncthreads();
+    if (l < m.grid_levels) mg_sync(m, l, ctl, t); else if (active) __syncthreads();
   }
-  if (m.grid_levels == 0) grid_barrier(&ctl->count, &ctl->gen, &ctl->err);  // z was written by block 0 alone
+  if (m.grid_levels == 0) grid_barrier(&ctl->count, &ctl->gen, &ctl->err, t.nblk);  // z was written by block 0 alone
 }
 #undef MG_FOR
 
@@ -429,8 +437,8 @@ __device__ void mg_vcycle(const MG &m, const float *r, CGCtl *ctl) {
 // FP64 across blocks; every block sums the same partials in the same order and
 // so takes the same decisions.
 template <int PRE>
-__global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, CGAcc *acc, double tol, int max_iter,
-                                                      int check, const MG mg) {
+__device__ __forceinline__ void cg_loop_body(const CG &g, CGCtl *ctl, CGAcc *acc, double tol, int max_iter, int check,
+                                             const MG &mg, Team t) {
   __shared__ double sh[33];
   __shared__ float shf[33];
   __shared__ float s_ab[2];
@@ -442,15 +450,15 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, CG
   if (!(bnorm > 0.0) || !isfinite(bnorm)) rel = 0.0;  // flat (or broken) right-hand side: nothing to solve
   float *e = g.ap + g.P;  // correction accumulator (second half of the Ap buffer)
   float *z = PRE == 1 ? mg.x1 : g.z;  // preconditioned residual (level 0 of the hierarchy for PRE 1)
-  for (Stride q(g.W); q.p < g.P; q.next(g.W)) e[q.p] = 0.0f;
+  for (Stride q(g.W, t); q.p < g.P; q.next(g.W)) e[q.p] = 0.0f;
   // z = M^-1 r and the partial sums of r.z into `slot` (and the refresh reference)
   auto precondition = [&](int slot, bool refresh) {
     if (PRE == 1) {
-      grid_barrier(&ctl->count, &ctl->gen, &ctl->err);  // r complete
-      mg_vcycle(mg, g.r, ctl);
+      grid_barrier(&ctl->count, &ctl->gen, &ctl->err, t.nblk);  // r complete
+      mg_vcycle(mg, g.r, ctl, t);
     }
     float rz = 0.0f;
-    for (Stride q(g.W); q.p < g.P; q.next(g.W)) {
+    for (Stride q(g.W, t); q.p < g.P; q.next(g.W)) {
       const float rf = g.r[q.p];
       float zf;
       if (PRE == 1) {
@@ -463,13 +471,13 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, CG
     }
     rz = block_sum_f(rz, shf);
     if (threadIdx.x == 0) {
-      g.part[slot * g.stride + blockIdx.x] = (double)rz;
-      if (refresh) g.part[S_RZREF * g.stride + blockIdx.x] = (double)rz;
+      g.part[slot * g.stride + t.bid] = (double)rz;
+      if (refresh) g.part[S_RZREF * g.stride + t.bid] = (double)rz;
     }
   };
   if (PRE == 1 && rel > tol) {  // the residual kernel left r; z and r.z come from the V-cycle
     precondition(S_RZ0, true);
-    grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+    grid_barrier(&ctl->count, &ctl->gen, &ctl->err, t.nblk);
   }
   while (rel > tol && it < max_iter && !*(volatile int *)&ctl->err) {
     ++it;
@@ -490,7 +498,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, CG
     float *pnew = g.p + (size_t)(it & 1) * g.P;
     auto dir = [&](int r) { return frozen ? 0.0f : (first ? z[r] : fmaf(beta, pold[r], z[r])); };
     float pap = 0.0f;
-    for (Stride q(g.W); q.p < g.P; q.next(g.W)) {
+    for (Stride q(g.W, t); q.p < g.P; q.next(g.W)) {
       const int p = q.p;
       const float pc = dir(p);
       float s = 0.0f, deg = 0.0f;
@@ -504,40 +512,40 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, CG
       pap = fmaf(pc, apv, pap);
     }
     pap = block_sum_f(pap, shf);
-    if (threadIdx.x == 0) g.part[S_PAP * g.stride + blockIdx.x] = (double)pap;
-    grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+    if (threadIdx.x == 0) g.part[S_PAP * g.stride + t.bid] = (double)pap;
+    grid_barrier(&ctl->count, &ctl->gen, &ctl->err, t.nblk);
     if (*(volatile int *)&ctl->err) break;
     // ---- B ----
     const double dpap = total(g.part + S_PAP * g.stride, g.nblk, sh);
     if (threadIdx.x == 0) s_ab[0] = (dpap > 0.0 && isfinite(dpap)) ? (float)(num / dpap) : 0.0f;
     __syncthreads();
     const float af = s_ab[0];
-    for (Stride q(g.W); q.p < g.P; q.next(g.W)) {
+    for (Stride q(g.W, t); q.p < g.P; q.next(g.W)) {
       const int p = q.p;
       e[p] = fmaf(af, pnew[p], e[p]);
       g.r[p] = fmaf(-af, g.ap[p], g.r[p]);
     }
     precondition(S_RZ0 + (it & 1), false);
-    grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+    grid_barrier(&ctl->count, &ctl->gen, &ctl->err, t.nblk);
     if (*(volatile int *)&ctl->err) break;
     // ---- refresh from FP64 ----
     if (it % check == 0 || frozen) {
-      for (Stride q(g.W); q.p < g.P; q.next(g.W)) {
+      for (Stride q(g.W, t); q.p < g.P; q.next(g.W)) {
         g.x[q.p] += (double)e[q.p];
         e[q.p] = 0.0f;
       }
-      grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+      grid_barrier(&ctl->count, &ctl->gen, &ctl->err, t.nblk);
       if (*(volatile int *)&ctl->err) break;
       double rr = 0.0;
-      for (Stride q(g.W); q.p < g.P; q.next(g.W)) {
+      for (Stride q(g.W, t); q.p < g.P; q.next(g.W)) {
         const double res = g.b[q.p] - lap_at<double>(g.x, q.i, q.j, g.H, g.W);
         g.r[q.p] = (float)res;
         rr += res * res;
       }
       rr = block_reduce<false>(rr, sh);
-      if (threadIdx.x == 0) g.part[S_RR * g.stride + blockIdx.x] = rr;
+      if (threadIdx.x == 0) g.part[S_RR * g.stride + t.bid] = rr;
       precondition(S_RZ0 + (it & 1), true);
-      grid_barrier(&ctl->count, &ctl->gen, &ctl->err);
+      grid_barrier(&ctl->count, &ctl->gen, &ctl->err, t.nblk);
       if (*(volatile int *)&ctl->err) break;
       rel = sqrt(total(g.part + S_RR * g.stride, g.nblk, sh)) / bnorm;
       if (!isfinite(rel)) break;
@@ -550,8 +558,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, CG
     }
   }
   // fold in a correction collected since the last refresh (none when the loop ended on a refresh)
-  for (Stride q(g.W); q.p < g.P; q.next(g.W)) g.x[q.p] += (double)e[q.p];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  for (Stride q(g.W, t); q.p < g.P; q.next(g.W)) g.x[q.p] += (double)e[q.p];
+  if (t.bid == 0 && threadIdx.x == 0) {
     ctl->iters = it;
     ctl->rel = rel;
     if (acc) {
@@ -564,9 +572,15 @@ __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, CG
   }
 }
 
+template <int PRE>
+__global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, CGAcc *acc, double tol, int max_iter,
+                                                      int check, const MG mg) {
+  cg_loop_body<PRE>(g, ctl, acc, tol, max_iter, check, mg, whole_grid());
+}
+
 // Start of a solve: |b| and the warm start's relative residual from the partials,
 // barrier state reset (one warp).
-__global__ void k_cg_start(const CG g, CGCtl *ctl) {
+__device__ __forceinline__ void cg_start_body(const CG &g, CGCtl *ctl) {
   double bb = 0.0, rr = 0.0;
   for (int i = threadIdx.x; i < g.nblk; i += 32) {
     bb += g.part[S_BB * g.stride + i];
@@ -584,19 +598,19 @@ __global__ void k_cg_start(const CG g, CGCtl *ctl) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_sum_x(const CG g) {
+__device__ __forceinline__ void sum_x_body(const CG &g, Team t) {
   __shared__ double sh[33];
   double s = 0.0;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) s += g.x[p];
+  for (int p = t.bid * blockDim.x + threadIdx.x; p < g.P; p += t.nblk * blockDim.x) s += g.x[p];
   s = block_reduce<false>(s, sh);
-  if (threadIdx.x == 0) g.part[S_SUMX * g.stride + blockIdx.x] = s;
+  if (threadIdx.x == 0) g.part[S_SUMX * g.stride + t.bid] = s;
 }
 
-__global__ void __launch_bounds__(kThreads) k_store_depth(const CG g, const CGCtl *ctl) {
+__device__ __forceinline__ void store_depth_body(const CG &g, const CGCtl *ctl, Team t) {
   __shared__ double sh[33];
   const double mean = total(g.part + S_SUMX * g.stride, g.nblk, sh) / (double)g.P;
   const bool flat = !(ctl->bnorm > 0.0);  // zero slopes everywhere: the surface is the plane H = 0
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x)
+  for (int p = t.bid * blockDim.x + threadIdx.x; p < g.P; p += t.nblk * blockDim.x)
     g.depth[p] = flat ? 0.0f : (float)(g.x[p] - mean);
 }
 
@@ -605,10 +619,10 @@ __global__ void __launch_bounds__(kThreads) k_zero_depth(const CG g) {
 }
 
 // D_H partials: max |H_new - H_old|, sum (H_new - H_old)^2, max H_new, -min H_new.
-__global__ void __launch_bounds__(kThreads) k_depth_change(const CG g, const float *old) {
+__device__ __forceinline__ void depth_change_body(const CG &g, const float *old, Team t) {
   __shared__ double sh[33];
   double dmax = 0.0, dsq = 0.0, hmax = -INFINITY, hmin = -INFINITY;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
+  for (int p = t.bid * blockDim.x + threadIdx.x; p < g.P; p += t.nblk * blockDim.x) {
     const double a = g.depth[p], d = a - (double)old[p];
     dmax = fmax(dmax, fabs(d));
     dsq += d * d;
@@ -616,13 +630,28 @@ __global__ void __launch_bounds__(kThreads) k_depth_change(const CG g, const flo
     hmin = fmax(hmin, -a);
   }
   dmax = block_reduce<true>(dmax, sh);
-  if (threadIdx.x == 0) g.part[S_DMAX * g.stride + blockIdx.x] = dmax;
+  if (threadIdx.x == 0) g.part[S_DMAX * g.stride + t.bid] = dmax;
   dsq = block_reduce<false>(dsq, sh);
-  if (threadIdx.x == 0) g.part[S_DSQ * g.stride + blockIdx.x] = dsq;
+  if (threadIdx.x == 0) g.part[S_DSQ * g.stride + t.bid] = dsq;
   hmax = block_reduce<true>(hmax, sh);
-  if (threadIdx.x == 0) g.part[S_HMAX * g.stride + blockIdx.x] = hmax;
+  if (threadIdx.x == 0) g.part[S_HMAX * g.stride + t.bid] = hmax;
   hmin = block_reduce<true>(hmin, sh);
-  if (threadIdx.x == 0) g.part[S_HMIN * g.stride + blockIdx.x] = hmin;
+  if (threadIdx.x == 0) g.part[S_HMIN * g.stride + t.bid] = hmin;
+}
+
+// Plain (one solve per launch) forms of the solver's kernels.
+__global__ void __launch_bounds__(kThreads) k_rhs(const CG g) { rhs_body(g, whole_grid()); }
+__global__ void __launch_bounds__(kThreads) k_load_x(const CG g) { load_x_body(g, whole_grid()); }
+__global__ void __launch_bounds__(kThreads) k_residual(const CG g, int rz_slot) {
+  residual_body(g, rz_slot, whole_grid());
+}
+__global__ void k_cg_start(const CG g, CGCtl *ctl) { cg_start_body(g, ctl); }
+__global__ void __launch_bounds__(kThreads) k_sum_x(const CG g) { sum_x_body(g, whole_grid()); }
+__global__ void __launch_bounds__(kThreads) k_store_depth(const CG g, const CGCtl *ctl) {
+  store_depth_body(g, ctl, whole_grid());
+}
+__global__ void __launch_bounds__(kThreads) k_depth_change(const CG g, const float *old) {
+  depth_change_body(g, old, whole_grid());
 }
 
 // Blocks of the cooperative solve: all must be co-resident; two per SM keep the
@@ -727,7 +756,7 @@ static CG make_cg(Ctx &c) {
   } while (0)
 
 // D_H of the last iteration into the device statistics (one warp).
-__global__ void k_dh_final(const CG g, DevStats *ds) {
+__device__ __forceinline__ void dh_final_body(const CG &g, DevStats *ds) {
   double dmax = 0.0, dsq = 0.0, hmax = -INFINITY, hmin = -INFINITY;
   for (int i = threadIdx.x; i < g.nblk; i += 32) {
     dmax = fmax(dmax, g.part[S_DMAX * g.stride + i]);
@@ -745,6 +774,7 @@ __global__ void k_dh_final(const CG g, DevStats *ds) {
     ds->dh_rms = sqrt(dsq / (double)g.P);
   }
 }
+__global__ void k_dh_final(const CG g, DevStats *ds) { dh_final_body(g, ds); }
 
 // One depth solve, enqueued without host round trips: right-hand side, warm
 // start, residual, |b| on the device, the cooperative PCG loop, mean removal.
@@ -787,6 +817,125 @@ cudaError_t depth_change_async(Ctx &c) {
   k_depth_change<<<c.cg_blocks, kThreads, 0, c.stream>>>(g, c.depth_prev);
   k_dh_final<<<1, 32, 0, c.stream>>>(g, c.dstats);
   c.stats.launches += 2;
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Batched depth solves: the solves of many objects in one launch per step.
+// The blocks of a batched launch are split into contiguous teams, one per
+// object (job o owns blocks [blk_begin(o), blk_begin(o + 1))); each team runs
+// the plain solver on its object with barriers of its own, so objects of any
+// size proceed independently within one co-resident cooperative grid.
+// ---------------------------------------------------------------------------
+struct CGJob {
+  CG g;            // g.nblk: the team's block count
+  MG mg;
+  CGCtl *ctl;
+  DevStats *ds;    // the object's statistics (solver accumulators, D_H)
+  const float *old;  // previous surface (D_H)
+  double tol;
+  int max_iter, check, pre;
+  int blk_begin;
+};
+
+// Copy the job of this block's team into shared memory and run body(job, team).
+template <typename F>
+__device__ __forceinline__ void for_team(const CGJob *__restrict__ jobs, int n, F &&body) {
+  __shared__ CGJob sj;
+  __shared__ int s_bid;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n - 1;  // last job whose range starts at or before this block
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].blk_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    sj = jobs[lo];
+    s_bid = (int)blockIdx.x - jobs[lo].blk_begin;
+  }
+  __syncthreads();
+  body(sj, Team{s_bid, sj.g.nblk});
+}
+
+__global__ void __launch_bounds__(kThreads) k_rhs_b(const CGJob *jobs, int n) {
+  for_team(jobs, n, [](const CGJob &j, Team t) { rhs_body(j.g, t); });
+}
+__global__ void __launch_bounds__(kThreads) k_load_x_b(const CGJob *jobs, int n) {
+  for_team(jobs, n, [](const CGJob &j, Team t) { load_x_body(j.g, t); });
+}
+__global__ void __launch_bounds__(kThreads) k_residual_b(const CGJob *jobs, int n) {
+  for_team(jobs, n, [](const CGJob &j, Team t) { residual_body(j.g, S_RZ0, t); });
+}
+// one warp per job
+__global__ void k_cg_start_b(const CGJob *jobs) { cg_start_body(jobs[blockIdx.x].g, jobs[blockIdx.x].ctl); }
+__global__ void __launch_bounds__(kThreads) k_cg_loop_b(const CGJob *jobs, int n) {
+  for_team(jobs, n, [](const CGJob &j, Team t) {
+    if (j.pre == 1)
+      cg_loop_body<1>(j.g, j.ctl, &j.ds->cg, j.tol, j.max_iter, j.check, j.mg, t);
+    else
+      cg_loop_body<0>(j.g, j.ctl, &j.ds->cg, j.tol, j.max_iter, j.check, j.mg, t);
+  });
+}
+__global__ void __launch_bounds__(kThreads) k_sum_x_b(const CGJob *jobs, int n) {
+  for_team(jobs, n, [](const CGJob &j, Team t) { sum_x_body(j.g, t); });
+}
+__global__ void __launch_bounds__(kThreads) k_store_depth_b(const CGJob *jobs, int n) {
+  for_team(jobs, n, [](const CGJob &j, Team t) { store_depth_body(j.g, j.ctl, t); });
+}
+__global__ void __launch_bounds__(kThreads) k_depth_change_b(const CGJob *jobs, int n) {
+  for_team(jobs, n, [](const CGJob &j, Team t) { depth_change_body(j.g, j.old, t); });
+}
+__global__ void k_dh_final_b(const CGJob *jobs) { dh_final_body(jobs[blockIdx.x].g, jobs[blockIdx.x].ds); }
+
+size_t cg_job_bytes() { return sizeof(CGJob); }
+
+// Co-resident blocks of the batched solve loop (at most IRTPS_CG_BLOCKS_PER_SM per SM).
+int cg_batch_grid_limit() {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_loop_b, kThreads, 0) != cudaSuccess) return 0;
+  per = per < IRTPS_CG_BLOCKS_PER_SM ? per : IRTPS_CG_BLOCKS_PER_SM;
+  return per * sms;
+}
+
+void cg_fill_job(Ctx &c, int nblk, int blk_begin, DevStats *ds, void *dst) {
+  CGJob j{};
+  j.g = make_cg(c);
+  j.g.nblk = nblk;
+  j.mg = make_mg(c);
+  if (nblk == 1) j.mg.grid_levels = 0;  // a one-block team sweeps every level alone
+  j.ctl = (CGCtl *)c.cg_ctl;
+  j.ds = ds;
+  j.old = c.depth_prev;
+  j.tol = c.opt.cg_tol;
+  j.max_iter = c.opt.cg_max_iter;
+  j.check = c.opt.cg_check_every > 0 ? c.opt.cg_check_every : 10;
+  j.pre = c.opt.precond == 1 ? 1 : 0;
+  j.blk_begin = blk_begin;
+  std::memcpy(dst, &j, sizeof(j));
+}
+
+cudaError_t solve_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks) {
+  const CGJob *jobs = (const CGJob *)d_jobs;
+  k_rhs_b<<<blocks, kThreads, 0, s>>>(jobs, n);
+  k_load_x_b<<<blocks, kThreads, 0, s>>>(jobs, n);
+  k_residual_b<<<blocks, kThreads, 0, s>>>(jobs, n);
+  k_cg_start_b<<<n, 32, 0, s>>>(jobs);
+  LAUNCH_CHECK();
+  void *args[] = {(void *)&jobs, (void *)&n};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_cg_loop_b, dim3(blocks), dim3(kThreads), args, 0, s);
+  if (e != cudaSuccess) return e;
+  k_sum_x_b<<<blocks, kThreads, 0, s>>>(jobs, n);
+  k_store_depth_b<<<blocks, kThreads, 0, s>>>(jobs, n);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t depth_change_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks) {
+  const CGJob *jobs = (const CGJob *)d_jobs;
+  k_depth_change_b<<<blocks, kThreads, 0, s>>>(jobs, n);
+  k_dh_final_b<<<n, 32, 0, s>>>(jobs);
   LAUNCH_CHECK();
   return cudaSuccess;
 }

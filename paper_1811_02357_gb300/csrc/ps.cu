@@ -12,6 +12,7 @@
 // 6*K*C flops: far below the tensor-core ridge, so it runs on the FP32 pipes
 // with coalesced [k][c][p] loads and the pixel's state written once.
 #include <cstdint>
+#include <cstring>
 #include <cuda_fp16.h>
 
 #include "irtps_internal.h"
@@ -30,6 +31,7 @@ struct PSArgs {
   int zero_indirect;    // 1: Lbar taken as 0 (iteration 0, classic PS)
   float pinv[3][kMaxLights];
   float light[kMaxLights][3];
+  int blk_begin;        // first block of the object in a batched launch
 };
 
 template <typename TI>
@@ -40,9 +42,7 @@ template <>
 __device__ __forceinline__ float load_img<__half>(const __half *p) { return __half2float(__ldg(p)); }
 
 template <int C, typename TI>
-__global__ void __launch_bounds__(256) k_ps(const PSArgs a) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= a.P) return;
+__device__ __forceinline__ void ps_pixel(const PSArgs &a, int p) {
   const TI *img = reinterpret_cast<const TI *>(a.images);
   const size_t P = (size_t)a.P;
   float rho[C];
@@ -157,8 +157,31 @@ __global__ void __launch_bounds__(256) k_ps(const PSArgs a) {
   a.valid[p] = ok ? 1 : 0;
 }
 
-cudaError_t launch_ps(Ctx &c, bool zero_indirect) {
-  PSArgs a;
+template <int C, typename TI>
+__global__ void __launch_bounds__(256) k_ps(const PSArgs a) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < a.P) ps_pixel<C, TI>(a, p);
+}
+
+// Batched: the blocks of object o are [objs[o].blk_begin, objs[o + 1].blk_begin).
+template <int C, typename TI>
+__global__ void __launch_bounds__(256) k_ps_b(const PSArgs *__restrict__ objs, int n) {
+  __shared__ int s_o;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (objs[mid].blk_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    s_o = lo;
+  }
+  __syncthreads();
+  const PSArgs &a = objs[s_o];
+  const int p = ((int)blockIdx.x - a.blk_begin) * blockDim.x + threadIdx.x;
+  if (p < a.P) ps_pixel<C, TI>(a, p);
+}
+
+static void fill_ps_args(const Ctx &c, bool zero_indirect, PSArgs &a) {
   a.images = c.images;
   a.lbar = c.lbar;
   a.albedo = c.albedo;
@@ -176,6 +199,37 @@ cudaError_t launch_ps(Ctx &c, bool zero_indirect) {
       a.light[k][r] = c.h_lights[3 * k + r];
     }
   }
+  a.blk_begin = 0;
+}
+
+size_t ps_args_bytes() { return sizeof(PSArgs); }
+
+void ps_fill_args(const Ctx &c, bool zero_indirect, int blk_begin, void *dst) {
+  PSArgs a;
+  fill_ps_args(c, zero_indirect, a);
+  a.blk_begin = blk_begin;
+  std::memcpy(dst, &a, sizeof(a));
+}
+
+cudaError_t launch_ps_batch(cudaStream_t s, int C, int dtype, const void *d_args, int n, int blocks) {
+  const PSArgs *a = (const PSArgs *)d_args;
+  if (C == 1) {
+    if (dtype == IRTPS_F16)
+      k_ps_b<1, __half><<<blocks, 256, 0, s>>>(a, n);
+    else
+      k_ps_b<1, float><<<blocks, 256, 0, s>>>(a, n);
+  } else {
+    if (dtype == IRTPS_F16)
+      k_ps_b<3, __half><<<blocks, 256, 0, s>>>(a, n);
+    else
+      k_ps_b<3, float><<<blocks, 256, 0, s>>>(a, n);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ps(Ctx &c, bool zero_indirect) {
+  PSArgs a;
+  fill_ps_args(c, zero_indirect, a);
   const int threads = 256;
   const unsigned blocks = (unsigned)((a.P + threads - 1) / threads);
   ++c.stats.launches;

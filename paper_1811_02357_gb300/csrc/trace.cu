@@ -2,6 +2,7 @@
 // per-(pixel, light) trace kernel, the stage-0 forward render, and geometry
 // probes used by the parity tests.
 #include <cstdint>
+#include <cstring>
 #include <cuda_fp16.h>
 
 #include "geom.cuh"
@@ -13,38 +14,104 @@ namespace irtps {
 // Min / max pyramid.  Level 0: one node per cell, over its 4 vertex heights.
 // Level l: one node per 2x2 block of level l-1 nodes (clipped at the border).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void pyramid_leaf_node(const float *__restrict__ depth, int W, int Wc, int i,
+                                                  float *__restrict__ pmin, float *__restrict__ pmax) {
+  const int cy = i / Wc, cx = i - cy * Wc;
+  const float *r = depth + (size_t)cy * W + cx;
+  const float a = r[0], b = r[1], c = r[W], d = r[W + 1];
+  pmin[i] = fminf(fminf(a, b), fminf(c, d));
+  pmax[i] = fmaxf(fmaxf(a, b), fmaxf(c, d));
+}
+
+__device__ __forceinline__ void pyramid_up_node(const float *__restrict__ cmin, const float *__restrict__ cmax,
+                                                int cw, int ch, int w, int i, float *__restrict__ pmin,
+                                                float *__restrict__ pmax) {
+  const int y = i / w, x = i - y * w;
+  float lo = __int_as_float(0x7f800000), hi = -lo;
+  for (int dy = 0; dy < 2; ++dy) {
+    const int yy = 2 * y + dy;
+    if (yy >= ch) break;
+    for (int dx = 0; dx < 2; ++dx) {
+      const int xx = 2 * x + dx;
+      if (xx >= cw) break;
+      lo = fminf(lo, cmin[yy * cw + xx]);
+      hi = fmaxf(hi, cmax[yy * cw + xx]);
+    }
+  }
+  pmin[i] = lo;
+  pmax[i] = hi;
+}
+
 __global__ void k_pyramid_leaf(const float *__restrict__ depth, int H, int W, float *__restrict__ pmin,
                                float *__restrict__ pmax) {
   const int Wc = W - 1, Hc = H - 1;
   const int n = Wc * Hc;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int cy = i / Wc, cx = i - cy * Wc;
-    const float *r = depth + (size_t)cy * W + cx;
-    const float a = r[0], b = r[1], c = r[W], d = r[W + 1];
-    pmin[i] = fminf(fminf(a, b), fminf(c, d));
-    pmax[i] = fmaxf(fmaxf(a, b), fmaxf(c, d));
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    pyramid_leaf_node(depth, W, Wc, i, pmin, pmax);
 }
 
 __global__ void k_pyramid_up(const float *__restrict__ cmin, const float *__restrict__ cmax, int cw, int ch,
                              float *__restrict__ pmin, float *__restrict__ pmax, int w, int h) {
   const int n = w * h;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int y = i / w, x = i - y * w;
-    float lo = __int_as_float(0x7f800000), hi = -lo;
-    for (int dy = 0; dy < 2; ++dy) {
-      const int yy = 2 * y + dy;
-      if (yy >= ch) break;
-      for (int dx = 0; dx < 2; ++dx) {
-        const int xx = 2 * x + dx;
-        if (xx >= cw) break;
-        lo = fminf(lo, cmin[yy * cw + xx]);
-        hi = fmaxf(hi, cmax[yy * cw + xx]);
-      }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    pyramid_up_node(cmin, cmax, cw, ch, w, i, pmin, pmax);
+}
+
+// Batched pyramid level l over many objects: object o owns the blocks
+// [blk[l] of o, blk[l] of o + 1) of the launch (none once its levels run out).
+__global__ void k_pyramid_b(const PyrObj *__restrict__ objs, int n, int l) {
+  __shared__ int s_o;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (objs[mid].blk[l] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
     }
-    pmin[i] = lo;
-    pmax[i] = hi;
+    s_o = lo;
   }
+  __syncthreads();
+  const PyrObj &o = objs[s_o];
+  if (l >= o.levels) return;
+  const int i = ((int)blockIdx.x - o.blk[l]) * blockDim.x + threadIdx.x;
+  if (i >= o.lw[l] * o.lh[l]) return;
+  if (l == 0) {
+    const int W = o.W, Wc = W - 1;
+    pyramid_leaf_node(o.depth, W, Wc, i, o.pmin, o.pmax);
+    if (o.prev) {  // each cell saves its lower-left vertex; the last row and column their others
+      const int cy = i / Wc, cx = i - cy * Wc;
+      const size_t v = (size_t)cy * W + cx;
+      o.prev[v] = o.depth[v];
+      const bool last_x = cx == Wc - 1, last_y = cy == o.H - 2;
+      if (last_x) o.prev[v + 1] = o.depth[v + 1];
+      if (last_y) o.prev[v + W] = o.depth[v + W];
+      if (last_x && last_y) o.prev[v + W + 1] = o.depth[v + W + 1];
+    }
+  } else
+    pyramid_up_node(o.pmin + o.off[l - 1], o.pmax + o.off[l - 1], o.lw[l - 1], o.lh[l - 1], o.lw[l], i,
+                    o.pmin + o.off[l], o.pmax + o.off[l]);
+}
+
+void fill_pyr_obj(const Ctx &c, PyrObj &o) {
+  o.depth = c.depth;
+  o.prev = c.depth_prev;
+  o.pmin = c.pmin;
+  o.pmax = c.pmax;
+  o.H = c.H;
+  o.W = c.W;
+  o.levels = c.levels;
+  for (int l = 0; l < kMaxLevels; ++l) {
+    o.off[l] = c.off[l];
+    o.lw[l] = c.lw[l];
+    o.lh[l] = c.lh[l];
+    o.blk[l] = 0;
+  }
+}
+
+// One launch per level; blocks[l] = total blocks of level l (objects' ranges set in d_objs).
+cudaError_t build_pyramid_batch(cudaStream_t s, const PyrObj *d_objs, int n, int levels, const int *blocks) {
+  for (int l = 0; l < levels; ++l)
+    if (blocks[l] > 0) k_pyramid_b<<<blocks[l], kPyrThreads, 0, s>>>(d_objs, n, l);
+  return cudaGetLastError();
 }
 
 cudaError_t build_pyramid(Ctx &c) {
@@ -113,36 +180,32 @@ __device__ __forceinline__ void env_lookup(const float *__restrict__ env, int EH
 // busy although path lengths differ widely, while each lane's own sequence of
 // operations - and so every result bit - is that of a plain sequential trace.
 // ---------------------------------------------------------------------------
+// One trace launch: a single object (`one`) or a batch of objects whose work
+// items follow one another in descriptor order.
 struct TraceArgs {
-  Field f;
-  const float4 *nrm;      // H*W (nx, ny, nz, mean albedo)
-  const float *albedo;    // C*H*W
-  const float *env;       // C*EH*EW
-  int EH, EW;
-  const int32_t *pixels;  // optional pixel list
-  int n_pix, K, spp, bounces, shadow;
-  uint32_t iter, stream;
-  uint2 key;
-  float eps, Wf;
-  float *out;             // K*C*n_pix
-  int32_t *rec;           // optional n_pix*K*spp*B*2
+  ObjTrace one;
+  const ObjTrace *objs;        // batched launch: n_obj descriptors in device memory
+  int n_obj;
+  unsigned n_items;            // all work items of the launch
+  const int32_t *pixels;       // optional pixel list (single object)
+  int32_t *rec;                // optional n_pix*K*spp*B*2 records (single object)
   unsigned long long *counts;  // {unused, segments, walk overflows, node visits, triangle tests, draws}
   unsigned *next_item;         // work-item counter, zero before the launch
   const uint32_t *iter_dev;    // when set, the iteration field is read here (graph replays)
-  float3 light[kMaxLights];
+  uint32_t iter, stream;
 };
 
 #ifndef IRTPS_TRACE_MINB
 #define IRTPS_TRACE_MINB 8
+#endif
+#ifndef IRTPS_TRACE_MINB_BATCH
+#define IRTPS_TRACE_MINB_BATCH 6
 #endif
 #ifndef IRTPS_MARCH_KEEP
 #define IRTPS_MARCH_KEEP 2
 #endif
 #ifndef IRTPS_LEAF_BATCH
 #define IRTPS_LEAF_BATCH 4
-#endif
-#ifndef IRTPS_LEAF_MODE
-#define IRTPS_LEAF_MODE 0
 #endif
 constexpr int kTraceThreads = 128;
 // leave the march loop when marching lanes <= live lanes / kMarchKeep
@@ -151,41 +214,72 @@ constexpr int kMarchKeep = IRTPS_MARCH_KEEP;
 constexpr int kLeafBatch = IRTPS_LEAF_BATCH;
 enum : int { PH_SETUP = 0, PH_MARCH = 1, PH_RESOLVE = 2, PH_DONE = 3 };
 
-template <int C>
-__global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const TraceArgs a) {
-  __shared__ LevelTable lt;
-  load_levels(a.f, &lt);
-  // Work items are (light, pixel) pairs, item = k * n_pix + ip.  Each lane starts
-  // with the item of its global index and, when done, takes the next unclaimed
-  // item from a counter (claimed a warp at a time), so that no lane idles while
-  // items remain.  An item is always traced by one lane, samples in order.
-  const int n_items = a.n_pix * a.K;
-  int item = blockIdx.x * blockDim.x + threadIdx.x;
+// Dynamic shared memory of a trace launch over n objects: level tables and item ranges.
+static size_t trace_smem_bytes(int n) { return (size_t)n * sizeof(LevelTable) + (size_t)(n + 1) * sizeof(unsigned); }
+
+template <int C, bool BATCH>
+__global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH : IRTPS_TRACE_MINB) k_trace(const __grid_constant__ TraceArgs a) {
+  extern __shared__ __align__(16) unsigned char trace_smem[];
+  LevelTable *lts = reinterpret_cast<LevelTable *>(trace_smem);
+  const int n_obj = BATCH ? a.n_obj : 1;
+  unsigned *s_begin = reinterpret_cast<unsigned *>(lts + n_obj);
+  if constexpr (BATCH) {
+    for (int i = threadIdx.x; i < n_obj * kMaxLevels; i += blockDim.x) {
+      const int o = i / kMaxLevels, l = i - o * kMaxLevels;
+      lts[o].off[l] = a.objs[o].f.off[l];
+      lts[o].lw[l] = a.objs[o].f.lw[l];
+    }
+    for (int o = threadIdx.x; o < n_obj; o += blockDim.x) {
+      set_height_bounds(a.objs[o].f, lts + o);
+      s_begin[o] = a.objs[o].item_begin;
+    }
+    __syncthreads();
+  } else {
+    load_levels(a.one.f, lts);
+  }
+  // Work items are (object, light, pixel) triples, within an object
+  // item = k * n_pix + ip.  Each lane starts with the item of its global index
+  // and, when done, takes the next unclaimed item from a counter (claimed a warp
+  // at a time), so that no lane idles while items remain.  An item is always
+  // traced by one lane, samples in order.
+  const unsigned n_items = a.n_items;
+  unsigned item = blockIdx.x * blockDim.x + threadIdx.x;
+  const ObjTrace *ob = &a.one;
+  const LevelTable *lt = lts;
   int k = 0, ip = 0, p = 0;
-  auto take = [&](int it) {
+  auto take = [&](unsigned it) {
     item = it;
-    k = it / a.n_pix;
-    ip = it - k * a.n_pix;
+    if constexpr (BATCH) {
+      int lo = 0, hi = n_obj - 1;  // last object whose range starts at or before it
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_begin[mid] <= it) lo = mid; else hi = mid - 1;
+      }
+      ob = a.objs + lo;
+      lt = lts + lo;
+      it -= s_begin[lo];
+    }
+    k = (int)(it / (unsigned)ob->n_pix);
+    ip = (int)it - k * ob->n_pix;
     p = a.pixels ? a.pixels[ip] : ip;
   };
   const bool alive = item < n_items;
   if (alive) take(item);
-  const int W = a.f.W, H = a.f.H;
-  const size_t P = (size_t)H * W;
   // the pixel's own vertex, lifted: origin of every primary ray of this lane
   auto pixel_origin = [&]() -> F3 {
+    const int W = ob->f.W;
     const int pi = p / W, pj = p - pi * W;
-    return F3{(float)pj, (float)pi, radd(__ldg(a.f.depth + p), a.eps)};
+    return F3{(float)pj, (float)pi, radd(__ldg(ob->f.depth + p), ob->eps)};
   };
   auto light = [&]() -> F3 {
-    const float3 l3 = a.light[k];
-    return F3{l3.x, l3.y, l3.z};
+    const float *l = ob->lights + 3 * k;
+    return F3{__ldg(l), __ldg(l + 1), __ldg(l + 2)};
   };
-  const int budget0 = 8 * (a.f.Wc + a.f.Hc + 8) * (a.f.levels + 1);
-  const uint32_t iter = a.iter_dev ? *a.iter_dev : a.iter;
+  auto budget0 = [&]() -> int { return 8 * (ob->f.Wc + ob->f.Hc + 8) * (ob->f.levels + 1); };
+  const uint32_t iter_base = a.iter_dev ? *a.iter_dev : a.iter;
 
   int phase = alive ? PH_SETUP : PH_DONE;
-  int s = 0, b = 1, qp = 0, budget = budget0;
+  int s = 0, b = 1, qp = 0, budget = alive ? budget0() : 0;
   bool shadow = false;
   float cosv = 0.0f;
   float thr[C], acc[C], sum[C], comp[C];
@@ -194,7 +288,6 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
     thr[c] = 1.0f;
     acc[c] = sum[c] = comp[c] = 0.0f;
   }
-  int32_t *rec = nullptr;
   Walker m;
   bool at_leaf = false;
   Work w;
@@ -202,7 +295,10 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
   int overflow = 0;
 
   auto rec_slot = [&](int bb) -> int32_t * {
-    return a.rec + ((((size_t)ip * a.K + k) * a.spp + s) * a.bounces + (bb - 1)) * 2;
+    return a.rec + ((((size_t)ip * ob->K + k) * ob->spp + s) * ob->bounces + (bb - 1)) * 2;
+  };
+  auto albedo_at = [&](int c, int q) -> float {
+    return __ldg(ob->albedo + (size_t)c * ob->f.H * ob->f.W + q);
   };
   auto end_sample = [&]() {
 #pragma unroll
@@ -216,15 +312,15 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
     }
     ++s;
     b = 1;
-    budget = budget0;
+    budget = budget0();
     phase = PH_SETUP;
   };
   // after a hit at pixel q (qp) the next bounce starts from the lifted hit point,
   // which the walker keeps as its origin m.o until the next set-up
   auto continue_path = [&](int q) {
 #pragma unroll
-    for (int c = 0; c < C; ++c) thr[c] *= __ldg(a.albedo + c * P + q);
-    if (b < a.bounces) {
+    for (int c = 0; c < C; ++c) thr[c] *= albedo_at(c, q);
+    if (b < ob->bounces) {
       ++b;
       phase = PH_SETUP;
     } else {
@@ -234,14 +330,14 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
 
   while (true) {
     // ---- finished items: store the mean and claim the next item ----
-    const bool item_done = phase == PH_SETUP && s >= a.spp;
+    const bool item_done = phase == PH_SETUP && s >= ob->spp;
     const unsigned need = __ballot_sync(0xffffffffu, item_done);
     if (need) {
       if (item_done) {
-        const float inv = 1.0f / (float)a.spp;
+        const float inv = 1.0f / (float)ob->spp;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          a.out[((size_t)k * C + c) * a.n_pix + ip] = sum[c] * inv;
+          ob->out[((size_t)k * C + c) * ob->n_pix + ip] = sum[c] * inv;
           sum[c] = comp[c] = 0.0f;
         }
       }
@@ -253,11 +349,11 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
       base = __shfl_sync(0xffffffffu, base, leader);
       if (item_done) {
         const unsigned mine = base + (unsigned)__popc(need & ((1u << lane) - 1u));
-        if (mine < (unsigned)n_items) {
-          take((int)mine);
+        if (mine < n_items) {
+          take(mine);
           s = 0;
           b = 1;
-          budget = budget0;
+          budget = budget0();
         } else {
           phase = PH_DONE;
         }
@@ -265,55 +361,41 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
     }
     // ---- set up the next primary or bounce segment ----
     if (phase == PH_SETUP) {
-      {
-        if (a.rec && b == 1) {
-          int32_t *r = rec_slot(1);
-          for (int j = 0; j < 2 * a.bounces; ++j) r[j] = -2;
-        }
-        const uint4 x = philox4x32_10(
-            make_uint4((uint32_t)p, (uint32_t)s, ((uint32_t)k << 8) | ((uint32_t)b << 4) | a.stream, iter), a.key);
-        // bounce 1 leaves the pixel's own vertex about its normal; later bounces the
-        // previous hit point (m.o) about the hit pixel's normal
-        const F3 org = b == 1 ? pixel_origin() : m.o;
-        const float4 n4 = __ldg(a.nrm + (b == 1 ? p : qp));
-        const F3 dw = cosine_dir(F3{n4.x, n4.y, n4.z}, x.x, x.y);
-        walker_init(m, org, F3{rmul(dw.x, a.Wf), rmul(dw.y, a.Wf), dw.z}, false);
-        shadow = false;
-        ++segs;
-        ++w.draws;
-        phase = PH_MARCH;
+      if (a.rec && b == 1) {
+        int32_t *r = rec_slot(1);
+        for (int j = 0; j < 2 * ob->bounces; ++j) r[j] = -2;
       }
+      const uint4 x = philox4x32_10(
+          make_uint4((uint32_t)p, (uint32_t)s, ((uint32_t)k << 8) | ((uint32_t)b << 4) | a.stream,
+                     ob->iter0 + iter_base),
+          ob->key);
+      // bounce 1 leaves the pixel's own vertex about its normal; later bounces the
+      // previous hit point (m.o) about the hit pixel's normal
+      const F3 org = b == 1 ? pixel_origin() : m.o;
+      const float4 n4 = __ldg(ob->nrm + (b == 1 ? p : qp));
+      const F3 dw = cosine_dir(F3{n4.x, n4.y, n4.z}, x.x, x.y);
+      walker_init(m, org, F3{rmul(dw.x, ob->Wf), rmul(dw.y, ob->Wf), dw.z}, false);
+      shadow = false;
+      ++segs;
+      ++w.draws;
+      phase = PH_MARCH;
     }
     const unsigned live = __ballot_sync(0xffffffffu, phase != PH_DONE);  // no lane finishes inside the march loop
     if (live == 0u) break;
     // ---- march while enough of the live lanes are marching; node steps every
     // iteration, leaf steps once enough marching lanes wait for one ----
     while (true) {
-#if IRTPS_LEAF_MODE == 0
       if (phase == PH_MARCH && !at_leaf) {
-        if (walker_node_step(m, a.f, lt, w, at_leaf)) phase = PH_RESOLVE;
+        if (walker_node_step(m, ob->f, *lt, w, at_leaf)) phase = PH_RESOLVE;
       }
       const unsigned leaf = __ballot_sync(0xffffffffu, phase == PH_MARCH && at_leaf);
       const unsigned node = __ballot_sync(0xffffffffu, phase == PH_MARCH && !at_leaf);
       if (leaf != 0u && kLeafBatch * __popc(leaf) >= __popc(node)) {
         if (phase == PH_MARCH && at_leaf) {
           at_leaf = false;
-          if (walker_leaf_step(m, a.f, w)) phase = PH_RESOLVE;
+          if (walker_leaf_step(m, ob->f, w)) phase = PH_RESOLVE;
         }
       }
-#else
-      // one kind of step per iteration: leaf steps once enough lanes wait for one
-      const unsigned leaf = __ballot_sync(0xffffffffu, phase == PH_MARCH && at_leaf);
-      const unsigned node = __ballot_sync(0xffffffffu, phase == PH_MARCH && !at_leaf);
-      if (leaf != 0u && kLeafBatch * __popc(leaf) >= __popc(node)) {
-        if (phase == PH_MARCH && at_leaf) {
-          at_leaf = false;
-          if (walker_leaf_step(m, a.f, w)) phase = PH_RESOLVE;
-        }
-      } else if (phase == PH_MARCH && !at_leaf) {
-        if (walker_node_step(m, a.f, lt, w, at_leaf)) phase = PH_RESOLVE;
-      }
-#endif
       if (phase == PH_MARCH && --budget < 0) {
         overflow = 1;
         at_leaf = false;
@@ -329,14 +411,14 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
         if (a.rec) rec_slot(b)[1] = vis;
         if (vis) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * __ldg(a.albedo + c * P + qp), cosv, acc[c]);
+          for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * albedo_at(c, qp), cosv, acc[c]);
         }
         continue_path(qp);
       } else if (m.btri < 0) {
         // escaped: environment radiance along the (world) direction
-        const F3 dw = {m.d.x / a.Wf, m.d.y / a.Wf, m.d.z};
+        const F3 dw = {m.d.x / ob->Wf, m.d.y / ob->Wf, m.d.z};
         float e[C];
-        env_lookup<C>(a.env, a.EH, a.EW, dw, e);
+        env_lookup<C>(ob->env, ob->EH, ob->EW, dw, e);
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c], e[c], acc[c]);
         if (a.rec) {
@@ -346,12 +428,13 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
         }
         end_sample();
       } else {
+        const int W = ob->f.W, H = ob->f.H;
         const float t = m.bt;
         const F3 q = {radd(m.o.x, rmul(t, m.d.x)), radd(m.o.y, rmul(t, m.d.y)), radd(m.o.z, rmul(t, m.d.z))};
         qp = nearest_index(q.y, H) * W + nearest_index(q.x, W);
-        const float4 m4 = __ldg(a.nrm + qp);
+        const float4 m4 = __ldg(ob->nrm + qp);
         const F3 nq = {m4.x, m4.y, m4.z};
-        const F3 o2 = {q.x, q.y, radd(q.z, a.eps)};
+        const F3 o2 = {q.x, q.y, radd(q.z, ob->eps)};
         if (a.rec) {
           int32_t *r = rec_slot(b);
           r[0] = qp;
@@ -360,15 +443,15 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
         const F3 l = light();
         if (f3dot(nq, l) > 0.0f) {
           cosv = fmaxf(0.0f, nq.x * l.x + nq.y * l.y + nq.z * l.z);
-          if (a.shadow) {
-            walker_init(m, o2, F3{rmul(l.x, a.Wf), rmul(l.y, a.Wf), l.z}, true);
+          if (ob->shadow) {
+            walker_init(m, o2, F3{rmul(l.x, ob->Wf), rmul(l.y, ob->Wf), l.z}, true);
             shadow = true;
             ++segs;
             phase = PH_MARCH;
           } else {
             if (a.rec) rec_slot(b)[1] = 1;
 #pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * __ldg(a.albedo + c * P + qp), cosv, acc[c]);
+            for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * albedo_at(c, qp), cosv, acc[c]);
             m.o = o2;
             continue_path(qp);
           }
@@ -397,55 +480,101 @@ __global__ void __launch_bounds__(kTraceThreads, IRTPS_TRACE_MINB) k_trace(const
   }
 }
 
-static void fill_trace_args(const Ctx &c, TraceArgs &a) {
-  a.f = c.field();
-  a.nrm = c.nrm;
-  a.albedo = c.albedo;
-  a.env = c.env;
-  a.EH = c.EH;
-  a.EW = c.EW;
-  a.K = c.K;
-  a.shadow = c.opt.shadow_rays;
-  a.eps = c.eps;
-  a.Wf = (float)c.W;
-  a.counts = c.dstats->counts;
-  for (int k = 0; k < c.K; ++k) a.light[k] = make_float3(c.h_lights[3 * k], c.h_lights[3 * k + 1], c.h_lights[3 * k + 2]);
+// The descriptor of a context's object (no output or sampling fields set).
+void fill_obj_trace(const Ctx &c, ObjTrace &o) {
+  o.f = c.field();
+  o.nrm = c.nrm;
+  o.albedo = c.albedo;
+  o.env = c.env;
+  o.lights = c.d_lights;
+  o.out = nullptr;
+  o.key = make_uint2(0u, 0u);
+  o.EH = c.EH;
+  o.EW = c.EW;
+  o.K = c.K;
+  o.spp = 0;
+  o.bounces = 0;
+  o.n_pix = c.H * c.W;
+  o.shadow = c.opt.shadow_rays;
+  o.eps = c.eps;
+  o.Wf = (float)c.W;
+  o.item_begin = 0;
+  o.iter0 = 0;
 }
 
 __global__ void k_next_iter(uint32_t *iter) { *iter += 1u; }
 
 cudaError_t launch_next_iter(Ctx &c) {
-  k_next_iter<<<1, 1, 0, c.stream>>>(c.iter_dev);
   ++c.stats.launches;
+  return launch_next_iter(c.stream, c.iter_dev);
+}
+
+cudaError_t launch_next_iter(cudaStream_t s, uint32_t *iter_dev) {
+  k_next_iter<<<1, 1, 0, s>>>(iter_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
                          uint32_t iter, uint32_t stream, float *out, int32_t *rec, bool iter_from_device) {
   TraceArgs a;
-  fill_trace_args(c, a);
-  a.iter_dev = iter_from_device ? c.iter_dev : nullptr;
+  fill_obj_trace(c, a.one);
+  a.one.n_pix = n_pix;
+  a.one.spp = spp;
+  a.one.bounces = bounces;
+  a.one.key = make_uint2((uint32_t)seed ^ c.obj, (uint32_t)(seed >> 32));
+  a.one.out = out;
+  a.objs = nullptr;
+  a.n_obj = 1;
+  a.n_items = (unsigned)n_pix * (unsigned)c.K;
   a.pixels = pixels;
-  a.n_pix = n_pix;
-  a.spp = spp;
-  a.bounces = bounces;
+  a.rec = rec;
+  a.counts = c.dstats->counts;
+  a.next_item = c.next_item;
+  a.iter_dev = iter_from_device ? c.iter_dev : nullptr;
   a.iter = iter;
   a.stream = stream;
-  a.key = make_uint2((uint32_t)seed ^ c.obj, (uint32_t)(seed >> 32));
-  a.out = out;
-  a.rec = rec;
   const long long n = (long long)n_pix * c.K;
   const int threads = kTraceThreads;
   // a persistent grid: as many blocks as stay resident, each lane claiming items until none remain
   long long blocks = (n + threads - 1) / threads;
   if (c.trace_blocks > 0 && blocks > c.trace_blocks) blocks = c.trace_blocks;
-  a.next_item = c.next_item;
   if (cudaMemsetAsync(a.next_item, 0, sizeof(unsigned), c.stream) != cudaSuccess) return cudaGetLastError();
   ++c.stats.launches;
+  const size_t smem = trace_smem_bytes(1);
   if (c.C == 1)
-    k_trace<1><<<(unsigned)blocks, threads, 0, c.stream>>>(a);
+    k_trace<1, false><<<(unsigned)blocks, threads, smem, c.stream>>>(a);
   else
-    k_trace<3><<<(unsigned)blocks, threads, 0, c.stream>>>(a);
+    k_trace<3, false><<<(unsigned)blocks, threads, smem, c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+// Batched trace: one persistent launch over the work items of n objects (all of
+// C channels); descriptors in device memory, items in descriptor order.
+cudaError_t launch_trace_batch(cudaStream_t s, int C, const ObjTrace *d_objs, int n_obj, unsigned n_items,
+                               unsigned long long *counts, unsigned *next_item, const uint32_t *iter_dev,
+                               uint32_t iter, int grid_limit) {
+  TraceArgs a;
+  std::memset(&a.one, 0, sizeof(a.one));
+  a.objs = d_objs;
+  a.n_obj = n_obj;
+  a.n_items = n_items;
+  a.pixels = nullptr;
+  a.rec = nullptr;
+  a.counts = counts;
+  a.next_item = next_item;
+  a.iter_dev = iter_dev;
+  a.iter = iter;
+  a.stream = 0u;
+  const int threads = kTraceThreads;
+  long long blocks = ((long long)n_items + threads - 1) / threads;
+  if (grid_limit > 0 && blocks > grid_limit) blocks = grid_limit;
+  if (blocks < 1) blocks = 1;
+  if (cudaMemsetAsync(next_item, 0, sizeof(unsigned), s) != cudaSuccess) return cudaGetLastError();
+  const size_t smem = trace_smem_bytes(n_obj);
+  if (C == 1)
+    k_trace<1, true><<<(unsigned)blocks, threads, smem, s>>>(a);
+  else
+    k_trace<3, true><<<(unsigned)blocks, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -456,7 +585,7 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
 // z standard normal by Box-Muller on Philox counter {p, 0, (k<<8)|(c<<4)|2, ~0}.
 // ---------------------------------------------------------------------------
 template <int C>
-__global__ void k_render(const TraceArgs a, const float *__restrict__ lbar, float sigma, float *__restrict__ out) {
+__global__ void k_render(const ObjTrace a, const float *__restrict__ lbar, float sigma, float *__restrict__ out) {
   __shared__ LevelTable lt;
   load_levels(a.f, &lt);
   const int P = a.f.H * a.f.W;
@@ -466,8 +595,7 @@ __global__ void k_render(const TraceArgs a, const float *__restrict__ lbar, floa
   const int pi = p / a.f.W, pj = p - pi * a.f.W;
   const float4 n4 = a.nrm[p];
   const F3 n = {n4.x, n4.y, n4.z};
-  const float3 l3 = a.light[k];
-  const F3 l = {l3.x, l3.y, l3.z};
+  const F3 l = {a.lights[3 * k], a.lights[3 * k + 1], a.lights[3 * k + 2]};
   float cosv = 0.0f;
   if (f3dot(n, l) > 0.0f) {
     int vis = 1;
@@ -495,20 +623,27 @@ __global__ void k_render(const TraceArgs a, const float *__restrict__ lbar, floa
   }
 }
 
-// Resident blocks of the trace kernel for C channels (the persistent grid size).
-int trace_grid_limit(int C) {
+// Resident blocks of the trace kernel for C channels (the persistent grid size);
+// n_obj > 0: the batched kernel over n_obj objects.
+int trace_grid_limit(int C, int n_obj) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  const cudaError_t e = C == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<1>, kTraceThreads, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<3>, kTraceThreads, 0);
+  const size_t smem = trace_smem_bytes(n_obj > 0 ? n_obj : 1);
+  cudaError_t e;
+  if (n_obj > 0)
+    e = C == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<1, true>, kTraceThreads, smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<3, true>, kTraceThreads, smem);
+  else
+    e = C == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<1, false>, kTraceThreads, smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<3, false>, kTraceThreads, smem);
   if (e != cudaSuccess) return 0;
   return per * sms;
 }
 
 cudaError_t launch_render(Ctx &c, uint64_t seed, float sigma, const float *lbar, float *out) {
-  TraceArgs a;
-  fill_trace_args(c, a);
+  ObjTrace a;
+  fill_obj_trace(c, a);
   a.key = make_uint2((uint32_t)seed ^ c.obj, (uint32_t)(seed >> 32));
   const long long n = (long long)c.H * c.W * c.K;
   const int threads = 128;

@@ -32,7 +32,10 @@ EXPORTED = [
     "irtps_trace", "irtps_solve_normals", "irtps_integrate", "irtps_trace_pixels", "irtps_set_state",
     "irtps_set_indirect", "irtps_render", "irtps_get_normals", "irtps_get_albedo", "irtps_get_depth",
     "irtps_get_indirect", "irtps_get_valid", "irtps_get_stats", "irtps_probe_dirs", "irtps_probe_rays",
-    "irtps_last_error", "irtps_destroy", "irtps_integrate_noalloc",
+    "irtps_last_error", "irtps_destroy", "irtps_integrate_noalloc", "irtps_set_object", "irtps_set_tuning",
+    "irtps_get_tuning", "irtps_autotune", "irtps_batch_create", "irtps_batch_iterate", "irtps_batch_get_stats",
+    "irtps_batch_set_tuning", "irtps_batch_get_tuning", "irtps_batch_autotune", "irtps_batch_last_error",
+    "irtps_batch_destroy",
 ]
 
 
@@ -92,6 +95,18 @@ def _load():
         "irtps_last_error": (ctypes.c_char_p, [P]),
         "irtps_integrate_noalloc": (i32, [P, i32, i32, f32, dbl, i32, P, P]),
         "irtps_destroy": (None, [P]),
+        "irtps_set_object": (i32, [P, u32]),
+        "irtps_set_tuning": (i32, [P, i32, i32]),
+        "irtps_get_tuning": (i32, [P, P, P]),
+        "irtps_autotune": (i32, [P, i32, i32, u64, P]),
+        "irtps_batch_create": (i32, [P, P, i32, i32]),
+        "irtps_batch_iterate": (i32, [P, i32, P, P, u64, P]),
+        "irtps_batch_get_stats": (i32, [P, P]),
+        "irtps_batch_set_tuning": (i32, [P, i32, i32]),
+        "irtps_batch_get_tuning": (i32, [P, P, P]),
+        "irtps_batch_autotune": (i32, [P, P, P, u64, P]),
+        "irtps_batch_last_error": (ctypes.c_char_p, [P]),
+        "irtps_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -274,6 +289,83 @@ def irtps_last_error(h):
     return _lib.irtps_last_error(h).decode()
 
 
+def irtps_set_object(h, obj):
+    _check(h, _lib.irtps_set_object(h, obj))
+
+
+def irtps_set_tuning(h, blocks_per_sm, mip_cut):
+    _check(h, _lib.irtps_set_tuning(h, blocks_per_sm, mip_cut))
+
+
+def irtps_get_tuning(h):
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(h, _lib.irtps_get_tuning(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def irtps_autotune(h, spp_probe, bounces, seed):
+    ms = ctypes.c_double(0.0)
+    _check(h, _lib.irtps_autotune(h, spp_probe, bounces, seed, ctypes.byref(ms)))
+    return ms.value
+
+
+def _check_batch(b, rc):
+    if rc != IRTPS_OK:
+        msg = _lib.irtps_batch_last_error(b).decode() if b else ""
+        raise IrtpsError(rc, msg)
+
+
+def irtps_batch_create(handles, use_graph=False):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    b = ctypes.c_void_p()
+    rc = _lib.irtps_batch_create(ctypes.byref(b), arr, len(handles), 1 if use_graph else 0)
+    if rc != IRTPS_OK:
+        raise IrtpsError(rc, "batch_create")
+    return b
+
+
+def irtps_batch_iterate(b, n_iter, spp, bounces, seed):
+    n = len(spp)
+    s = _host(spp, np.int32)
+    r = _host(bounces, np.int32)
+    dh = np.zeros(n, np.float64)
+    _check_batch(b, _lib.irtps_batch_iterate(b, n_iter, _addr(s), _addr(r), seed, _addr(dh)))
+    return dh
+
+
+def irtps_batch_get_stats(b):
+    st = irtps_stats()
+    _check_batch(b, _lib.irtps_batch_get_stats(b, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def irtps_batch_set_tuning(b, blocks_per_sm, mip_cut):
+    _check_batch(b, _lib.irtps_batch_set_tuning(b, blocks_per_sm, mip_cut))
+
+
+def irtps_batch_get_tuning(b):
+    x, y = ctypes.c_int(0), ctypes.c_int(0)
+    _check_batch(b, _lib.irtps_batch_get_tuning(b, ctypes.byref(x), ctypes.byref(y)))
+    return x.value, y.value
+
+
+def irtps_batch_autotune(b, spp_probe, bounces, seed):
+    s = _host(spp_probe, np.int32)
+    r = _host(bounces, np.int32)
+    ms = ctypes.c_double(0.0)
+    _check_batch(b, _lib.irtps_batch_autotune(b, _addr(s), _addr(r), seed, ctypes.byref(ms)))
+    return ms.value
+
+
+def irtps_batch_last_error(b):
+    return _lib.irtps_batch_last_error(b).decode()
+
+
+def irtps_batch_destroy(b):
+    if b is not None and b.value:
+        _lib.irtps_batch_destroy(b)
+
+
 def irtps_destroy(h):
     if h is not None and h.value:
         _lib.irtps_destroy(h)
@@ -359,3 +451,56 @@ class Context:
 
     def probe_rays(self, rays):
         return irtps_probe_rays(self.h, rays)
+
+    def set_object(self, obj):
+        irtps_set_object(self.h, obj)
+
+    def set_tuning(self, blocks_per_sm, mip_cut):
+        irtps_set_tuning(self.h, blocks_per_sm, mip_cut)
+
+    def tuning(self):
+        return irtps_get_tuning(self.h)
+
+    def autotune(self, spp_probe, bounces, seed):
+        return irtps_autotune(self.h, spp_probe, bounces, seed)
+
+
+class Batch:
+    """Many contexts iterated together, one launch per IRT stage.  The contexts stay owned by the
+    caller and must outlive the batch; context i gets object index i."""
+
+    def __init__(self, contexts, use_graph=False):
+        self.contexts = list(contexts)
+        self.b = irtps_batch_create([c.h for c in self.contexts], use_graph)
+
+    def close(self):
+        irtps_batch_destroy(self.b)
+        self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if getattr(self, "b", None) is not None:
+                self.close()
+        except Exception:
+            pass
+
+    def iterate(self, n_iter, spp, bounces, seed):
+        return irtps_batch_iterate(self.b, n_iter, spp, bounces, seed)
+
+    def stats(self):
+        return irtps_batch_get_stats(self.b)
+
+    def set_tuning(self, blocks_per_sm, mip_cut):
+        irtps_batch_set_tuning(self.b, blocks_per_sm, mip_cut)
+
+    def tuning(self):
+        return irtps_batch_get_tuning(self.b)
+
+    def autotune(self, spp_probe, bounces, seed):
+        return irtps_batch_autotune(self.b, spp_probe, bounces, seed)

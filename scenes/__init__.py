@@ -28,6 +28,10 @@ which are not available):
                  degrees); images stored in FP16.
   * `mixed`:     any size: bumps, bowls and grooves mixed at random (for ragged
                  and odd-sized test cases).
+  * `batch_objects`: the batched pattern: 64 objects of side
+                 round(exp U(ln 96, ln 1024)) (square), K in {4, 8, 16, 32},
+                 spp in {64, 128, 256}, bounces in {1, 2}, each a random mix of
+                 bumps, bowls and a groove with RGB albedo U(0.3, 0.9).
 """
 from __future__ import annotations
 
@@ -276,3 +280,27 @@ def random_heightfield(seed, H, W, amp=0.2):
 def plain_state(scene):
     """The ground truth as an estimate (depth, normals, albedo) in float32."""
     return scene.depth, scene.normals, scene.albedo
+
+
+def batch_spec(seed=4, n=64, side_lo=96, side_hi=1024):
+    """Sizes and trace settings of a batch: list of (scene seed, side, K, spp, bounces)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        side = int(round(np.exp(rng.uniform(np.log(side_lo), np.log(side_hi)))))
+        K = int(rng.choice([4, 8, 16, 32]))
+        spp = int(rng.choice([64, 128, 256]))
+        bounces = int(rng.choice([1, 2]))
+        out.append((1000 * seed + i, side, K, spp, bounces))
+    return out
+
+
+def batch_objects(seed=4, n=64, side_lo=96, side_hi=1024):
+    """The scenes of batch_spec: list of (Scene, spp, bounces)."""
+    out = []
+    for s, side, K, spp, bounces in batch_spec(seed, n, side_lo, side_hi):
+        rng = np.random.default_rng(s)
+        sc = mixed(s, side, side, K=K, C=3, n_bumps=int(rng.integers(2, 9)), n_bowls=int(rng.integers(0, 3)),
+                   groove=bool(rng.integers(0, 2)))
+        out.append((sc, spp, bounces))
+    return out
