@@ -13,6 +13,13 @@ roofline   = the trace kernel (dominant): algorithmic lane operations per second
              against the lane-issue peak (bound "alu")
 cpu_baseline = the oracle (plain C++) on the host cores over a pixel sample
 
+Workload `batch_64`: 64 objects of scenes.batch_objects (sides log-uniform in
+96..1024, K in {4, 8, 16, 32}, spp in {64, 128, 256}, bounces in {1, 2}); one
+step = iteration 0 (batched set_images) and one IRT iteration of every object
+through one batch (one launch per stage; timed enqueued, for its stage events, and once more with
+the iteration replayed as a CUDA graph); the same job as 64 per-object contexts
+iterated one after another is timed beside it.
+
 `--impl reference` times the oracle itself on the same workload (pixel samples).
 """
 from __future__ import annotations
@@ -35,6 +42,9 @@ WORKLOADS = {
     "bowl_64": ("bowl_64", {}, 64, 1, 3, 256, 1),
     # a small case of the same kernels for profiler captures (one IRT iteration per job)
     "bumps_256_profile": ("bumps_512", {"H": 256, "W": 256}, 32, 2, 1, 32, 2),
+    # the batched pattern: 64 objects (sides 96..1024, K, spp, bounces per object), one IRT
+    # iteration of all of them per step, against per-object launches (run_batch)
+    "batch_64": ("batch_objects", {}, None, None, 1, 32, 1),
 }
 
 # Algorithmic lane operations per unit of trace work (counted from the formulas:
@@ -153,7 +163,10 @@ def run_reference(args):
         return 0
     import scenes
     name, kw, spp, bounces, n_iter, _, _ = WORKLOADS[args.workload]
-    sc = getattr(scenes, name)(**kw)
+    if args.workload == "batch_64":  # a sample of the first object (the oracle traces one object at a time)
+        sc, spp, bounces = scenes.batch_objects(n=1)[0]
+    else:
+        sc = getattr(scenes, name)(**kw)
     per_step_s = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         cpu_baseline(sc, spp, bounces, target_s=min(per_step_s, 3.0))
@@ -173,6 +186,173 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """The batched pattern: all objects in one batch against per-object contexts."""
+    import torch
+    import scenes
+    from paper_1811_02357_gb300 import build
+    build.build()
+    from paper_1811_02357_gb300 import irtps
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    _, _, _, _, n_iter, rspp, rb = WORKLOADS[args.workload]
+    objs = scenes.batch_objects(seed=4 + 100 * rank)
+    stream = torch.cuda.Stream(device=dev)
+    img_dtype = irtps.IRTPS_F16 if args.images == "f16" else irtps.IRTPS_F32
+    ctxs, imgs = [], []
+    for i, (sc, _, _) in enumerate(objs):
+        c = irtps.Context(sc.H, sc.W, sc.lights, sc.env)
+        c.set_stream(stream.cuda_stream)
+        c.set_state(sc.depth, sc.normals, sc.albedo)
+        A = torch.empty((sc.K, sc.C, sc.H, sc.W), dtype=torch.float32, device=dev)
+        c.render(rspp, rb, 1000 + i, 0.002, out=A)
+        ctxs.append(c)
+        imgs.append(A.half() if args.images == "f16" else A)
+    torch.cuda.synchronize()
+    spp = [o[1] for o in objs]
+    bnc = [o[2] for o in objs]
+    seed = 1 + rank
+    # stage events need the enqueued form; the captured (graph) form is timed once after it
+    batch = irtps.Batch(ctxs, use_graph=False)
+    batch.set_stream(stream.cuda_stream)
+    P = sum(sc.H * sc.W for sc, _, _ in objs)
+
+    def set_all(host=None):
+        src = host if host is not None else imgs
+        ptrs = (irtps.ctypes.c_void_p * len(src))(*[a.data_ptr() for a in src])
+        irtps._check_batch(batch.b, irtps._lib.irtps_batch_set_images(batch.b, ptrs, img_dtype,
+                                                                      0 if host is not None else 1))
+        return batch.stats()
+
+    def batched():
+        s0 = set_all()
+        batch.iterate(n_iter, spp, bnc, seed)
+        st = dict(batch.stats())
+        for k in ("ps_ms", "depth_ms"):
+            st[k] += s0[k]
+        return st
+
+    def per_object():
+        segs = 0
+        for c, s_, b_ in zip(ctxs, spp, bnc):
+            c.set_images(imgs[ctxs.index(c)], dtype=img_dtype, on_device=True)
+            c.iterate(n_iter, s_, b_, seed)
+            segs += c.stats()["segments"]
+        return segs
+
+    def timed(fn, steps):
+        out = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out.append((e0.elapsed_time(e1), r))
+        return out
+
+    for _ in range(args.warmup):
+        batched()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = batch.stats()["launches"] + sum(c.stats()["launches"] for c in ctxs)
+    with ClockSampler(local) as clk:
+        res = timed(batched, args.steps)
+    launches = batch.stats()["launches"] + sum(c.stats()["launches"] for c in ctxs) - launches0
+    ms = sum(r[0] for r in res)
+    segs = sum(r[1]["segments"] for r in res)
+    draws = sum(r[1]["draws"] for r in res)
+    nodes = sum(r[1]["node_visits"] for r in res)
+    tris = sum(r[1]["tri_tests"] for r in res)
+    trace_ms = sum(r[1]["trace_ms"] for r in res)
+    primary = sum(r[1]["primary_segments"] for r in res)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        sg = torch.tensor([float(segs)], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(sg)
+        ms_all, segs_all = float(t.item()), float(sg.item())
+    else:
+        ms_all, segs_all = ms, float(segs)
+    value = segs_all / (ms_all / 1e3) / 1e6
+    # the same step with the iteration replayed as a CUDA graph
+    batch.close()
+    batch = irtps.Batch(ctxs, use_graph=True)
+    batch.set_stream(stream.cuda_stream)
+    batched()
+    graph_ms = timed(batched, 1)[0][0]
+    # the same job as per-object launches of the plain form (one context after another)
+    per_object()
+    po = timed(per_object, max(1, min(2, args.steps)))
+    po_ms = sum(r[0] for r in po)
+    po_value = sum(r[1] for r in po) / (po_ms / 1e3) / 1e6
+
+    e2e = None
+    if not args.no_e2e:
+        host = []
+        for a in imgs:
+            h = torch.empty(a.shape, dtype=a.dtype, pin_memory=True)
+            h.copy_(a.cpu())
+            host.append(h)
+        outs = [torch.empty((sc.H, sc.W), pin_memory=True) for sc, _, _ in objs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        set_all(host)
+        batch.iterate(n_iter, spp, bnc, seed)
+        segs_e2e = batch.stats()["segments"]
+        for c, o in zip(ctxs, outs):
+            irtps._check(c.h, irtps._lib.irtps_get_depth(c.h, irtps._addr(o.data_ptr()), 0))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": segs_e2e / dt / 1e6, "unit": "Mrays/s",
+               "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in host),
+               "d2h_bytes_per_step": sum(o.numel() * 4 for o in outs), "steps": 1}
+    clocks = clk.summary()
+    mhz = clocks["sm_max_mhz"] or sm_max_mhz()
+    ops = OPS_PER_DRAW * draws + OPS_PER_NODE * nodes + OPS_PER_TRI * tris
+    achieved = ops / (trace_ms / 1e3) / 1e12
+    peak = SM_COUNT * LANES_PER_SM * mhz * 1e6 / 1e12
+    bps, cut = batch.tuning()
+    line = {"metric": "IRT-PS Mrays/s", "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "objects": len(objs), "pixels": P,
+                       "sides": [sc.H for sc, _, _ in objs], "K": [sc.K for sc, _, _ in objs], "spp": spp,
+                       "bounces": bnc, "images": args.images, "irt_iterations_per_step": n_iter,
+                       "trace_blocks_per_sm": bps, "mip_cut": cut, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (images of all objects)"},
+            "pixel_iters_per_s": P * n_iter * world * args.steps / (ms_all / 1e3),
+            "primary_mrays_per_s": primary * world / (ms_all / 1e3) / 1e6,
+            "per_object_launches": {"value": po_value, "unit": "Mrays/s", "ms_per_step": po_ms / len(po)},
+            "graph_ms_per_step": graph_ms,
+            "speedup_vs_per_object": value / po_value,
+            "stage_ms_per_step": {"trace": trace_ms / args.steps,
+                                  "ps": sum(r[1]["ps_ms"] for r in res) / args.steps,
+                                  "depth": sum(r[1]["depth_ms"] for r in res) / args.steps},
+            "gpu_launches": launches, "clocks": clocks,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_trace (batched)",
+                         "launch_ms": trace_ms / (args.steps * n_iter)},
+            "e2e": e2e}
+    if rank == 0 and not args.no_cpu_baseline:
+        sc0, s0, b0 = objs[0]
+        line["cpu_baseline"] = cpu_baseline(sc0, s0, b0)
+    batch.close()
+    for c in ctxs:
+        c.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -187,6 +367,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch_64":
+        return run_batch(args)
 
     import torch
     import scenes

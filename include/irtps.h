@@ -228,6 +228,16 @@ int irtps_autotune(irtps_ctx *ctx, int spp_probe, int bounces, uint64_t seed, do
  * object index of context i to i (irtps_set_object).  n_obj in 1..64. */
 typedef struct irtps_batch irtps_batch;
 int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int use_graph);
+/* Run the batch's work on `stream` (a cudaStream_t); NULL restores its own
+ * stream.  The batch orders itself after the work queued on every object's
+ * stream and every object's stream after the batch's work. */
+int irtps_batch_set_stream(irtps_batch *b, void *stream);
+/* Stage 0 / iteration 0 of every object, batched: copy images[i] (K_i x C x H_i
+ * x W_i, dtype IRTPS_F32 or IRTPS_F16, host pointers if on_device == 0, else
+ * device pointers readable on the batch stream) into object i, then classic PS
+ * (Eq. 4) and integration for all objects, as irtps_set_images does for one.
+ * Results equal irtps_set_images' up to the summation order of the solve. */
+int irtps_batch_set_images(irtps_batch *b, const void *const *images, int dtype, int on_device);
 /* n_iter IRT iterations of every object (each context must have images set):
  * spp[i], bounces[i] for object i (host arrays of n_obj; bounces in 1..3); seed
  * as in irtps_iterate.  Object i's iteration index advances by n_iter.

@@ -20,12 +20,14 @@ struct irtps_batch {
   std::vector<irtps_ctx *> objs;
   int n = 0, C = 0;
   int use_graph = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;      // where the batch's work runs
+  cudaStream_t own_stream = nullptr;
   std::string err;
   int sms = 0, trace_per_sm_max = 0, trace_per_sm = 0, mip_cut = 0;
   // device tables (owned)
   irtps::ObjTrace *d_trace = nullptr;
   void *d_ps = nullptr;    // PS descriptors (iterations: Lbar subtracted)
+  void *d_ps0 = nullptr;   // PS descriptors of iteration 0 (classic PS: Lbar taken as 0)
   void *d_jobs = nullptr;  // depth-solve jobs
   irtps::PyrObj *d_pyr = nullptr;
   irtps::DevStats *d_stats = nullptr;  // per object (solver, D_H); [n]: trace counters
@@ -72,14 +74,14 @@ int bcuda(irtps_batch &b, cudaError_t e, const char *what) {
   } while (0)
 
 void release(irtps_batch &b) {
-  void *bufs[] = {b.d_trace, b.d_ps, b.d_jobs, b.d_pyr, b.d_stats, b.next_item, b.iter_dev};
+  void *bufs[] = {b.d_trace, b.d_ps, b.d_ps0, b.d_jobs, b.d_pyr, b.d_stats, b.next_item, b.iter_dev};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (b.graph) cudaGraphExecDestroy(b.graph);
   if (b.fork) cudaEventDestroy(b.fork);
   for (cudaEvent_t e : b.tev)
     if (e) cudaEventDestroy(e);
-  if (b.stream) cudaStreamDestroy(b.stream);
+  if (b.own_stream) cudaStreamDestroy(b.own_stream);
 }
 
 int stage_mark(irtps_batch &b, int stage, bool start) {
@@ -341,9 +343,10 @@ int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int
   b.trace_per_sm_max = b.sms > 0 ? limit / b.sms : 0;
   if (b.trace_per_sm_max < 1) return bail(IRTPS_ECUDA);
   b.trace_per_sm = b.trace_per_sm_max;
-  if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess ||
+  if (cudaStreamCreateWithFlags(&b.own_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) != cudaSuccess)
     return bail(IRTPS_ECUDA);
+  b.stream = b.own_stream;
 
   // pyramid: per level, each object's block range (none beyond its levels)
   std::vector<irtps::PyrObj> pyr(n_obj);
@@ -360,10 +363,11 @@ int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int
     }
   // PS: ceil(P / 256) blocks per object
   const size_t ps_bytes = irtps::ps_args_bytes();
-  std::vector<unsigned char> ps(ps_bytes * n_obj);
+  std::vector<unsigned char> ps(ps_bytes * n_obj), ps0(ps_bytes * n_obj);
   for (int i = 0; i < n_obj; ++i) {
     const Ctx &c = objs[i]->c;
     irtps::ps_fill_args(c, false, b.ps_blocks, ps.data() + ps_bytes * i);
+    irtps::ps_fill_args(c, true, b.ps_blocks, ps0.data() + ps_bytes * i);
     b.ps_blocks += (c.H * c.W + 255) / 256;
   }
   // depth solves: every object gets a team, the co-resident grid shared in
@@ -383,7 +387,8 @@ int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int
   }
   if ((cudaMalloc((void **)&b.d_stats, sizeof(irtps::DevStats) * (n_obj + 1)) != cudaSuccess) ||
       (cudaMalloc((void **)&b.d_trace, sizeof(irtps::ObjTrace) * n_obj) != cudaSuccess) ||
-      (cudaMalloc(&b.d_ps, ps_bytes * n_obj) != cudaSuccess) || (cudaMalloc(&b.d_jobs, job_bytes * n_obj) != cudaSuccess) ||
+      (cudaMalloc(&b.d_ps, ps_bytes * n_obj) != cudaSuccess) ||
+      (cudaMalloc(&b.d_ps0, ps_bytes * n_obj) != cudaSuccess) || (cudaMalloc(&b.d_jobs, job_bytes * n_obj) != cudaSuccess) ||
       (cudaMalloc((void **)&b.d_pyr, sizeof(irtps::PyrObj) * n_obj) != cudaSuccess) ||
       (cudaMalloc((void **)&b.next_item, sizeof(unsigned)) != cudaSuccess) ||
       (cudaMalloc((void **)&b.iter_dev, sizeof(uint32_t)) != cudaSuccess)) {
@@ -396,11 +401,48 @@ int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int
   }
   if (cudaMemcpy(b.d_pyr, pyr.data(), sizeof(irtps::PyrObj) * n_obj, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b.d_ps, ps.data(), ps_bytes * n_obj, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b.d_ps0, ps0.data(), ps_bytes * n_obj, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b.d_jobs, jobs.data(), job_bytes * n_obj, cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(IRTPS_ECUDA);
   for (int i = 0; i < n_obj; ++i) irtps_set_object(objs[i], (uint32_t)i);
   *out = x;
   return IRTPS_OK;
+}
+
+int irtps_batch_set_images(irtps_batch *x, const void *const *images, int dtype, int on_device) {
+  if (!x) return IRTPS_EINVAL;
+  irtps_batch &b = *x;
+  if (!images || (dtype != IRTPS_F32 && dtype != IRTPS_F16))
+    return bfail(b, IRTPS_EINVAL, "set_images: need n_obj image pointers and dtype IRTPS_F32 or IRTPS_F16");
+  for (int i = 0; i < b.n; ++i)
+    if (!images[i]) return bfail(b, IRTPS_EINVAL, "set_images: image pointer " + std::to_string(i) + " is NULL");
+  int rc = begin_call(b);
+  if (rc) return rc;
+  for (int i = 0; i < b.n; ++i) {
+    Ctx &c = b.objs[i]->c;
+    const size_t bytes = (size_t)c.K * c.C * c.H * c.W * (dtype == IRTPS_F16 ? 2 : 4);
+    BCK(cudaMemcpyAsync(c.images, images[i], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        b.stream),
+        "set_images: copy");
+    c.images_dtype = dtype;
+    c.have_images = true;
+    c.t = 0;
+  }
+  // iteration 0 of every object: classic PS, then integration from a flat start
+  const bool timed = true;
+  BSTAGE(ST_PS, true);
+  BCK(irtps::launch_ps_batch(b.stream, b.C, dtype, b.d_ps0, b.n, b.ps_blocks), "ps launch");
+  BSTAGE(ST_PS, false);
+  BSTAGE(ST_DEPTH, true);
+  BCK(irtps::zero_depth_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks), "depth reset");
+  BCK(irtps::solve_depth_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks), "depth solve launch");
+  BSTAGE(ST_DEPTH, false);
+  b.primary_per_iter = 0;
+  rc = end_call(b, true, 0, nullptr);
+  b.stats.iterations_done = 0;
+  b.stats.launches += 1 + 1 + 7;
+  const int rj = join_out(b);
+  return rc ? rc : rj;
 }
 
 int irtps_batch_iterate(irtps_batch *x, int n_iter, const int *spp, const int *bounces, uint64_t seed,
@@ -417,15 +459,30 @@ int irtps_batch_iterate(irtps_batch *x, int n_iter, const int *spp, const int *b
   if (b.use_graph) {
     if ((rc = capture(b, spp, bounces, seed))) return rc;
     for (int it = 0; it < n_iter; ++it) BCK(cudaGraphLaunch(b.graph, b.stream), "graph launch");
-    b.stats.launches += (unsigned long long)n_iter;
   } else {
     for (int it = 0; it < n_iter; ++it)
       if ((rc = enqueue_iteration(b, (uint32_t)it, false))) return rc;
   }
   rc = end_call(b, true, n_iter, out_dH);
+  {  // kernels per iteration: pyramid levels, trace, PS, seven of the solve, two of D_H (+ counter)
+    int k = 1 + 1 + 7 + 2 + (b.use_graph ? 1 : 0);
+    for (int l = 0; l < b.pyr_levels; ++l) k += b.pyr_blocks[l] > 0 ? 1 : 0;
+    b.stats.launches += (unsigned long long)k * n_iter;
+  }
   for (irtps_ctx *o : b.objs) o->c.t += (uint32_t)n_iter;
   const int rj = join_out(b);
   return rc ? rc : rj;
+}
+
+int irtps_batch_set_stream(irtps_batch *b, void *stream) {
+  if (!b) return IRTPS_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bcuda(*b, cudaGetLastError(), "set_stream");
+  b->stream = stream ? (cudaStream_t)stream : b->own_stream;
+  if (b->graph) {  // captured on the old stream: capture again
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return IRTPS_OK;
 }
 
 int irtps_batch_get_stats(irtps_batch *b, irtps_stats *out) {
@@ -504,7 +561,7 @@ const char *irtps_batch_last_error(const irtps_batch *b) { return b ? b->err.c_s
 
 void irtps_batch_destroy(irtps_batch *b) {
   if (!b) return;
-  cudaStreamSynchronize(b->stream);
+  if (b->stream) cudaStreamSynchronize(b->stream);
   release(*b);
   delete b;
 }

@@ -191,6 +191,7 @@ void cg_fill_job(Ctx &c, int nblk, int blk_begin, DevStats *ds, void *dst);
 int cg_batch_grid_limit();
 cudaError_t solve_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks);
 cudaError_t depth_change_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks);
+cudaError_t zero_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks);
 void mg_layout(int H, int W, int *levels, int *h, int *w, int *off, int *total);
 void mg_weights(int levels, const int *h, const int *w, const int *off, float *wh, float *wv);
 

@@ -886,6 +886,11 @@ __global__ void __launch_bounds__(kThreads) k_depth_change_b(const CGJob *jobs, 
   for_team(jobs, n, [](const CGJob &j, Team t) { depth_change_body(j.g, j.old, t); });
 }
 __global__ void k_dh_final_b(const CGJob *jobs) { dh_final_body(jobs[blockIdx.x].g, jobs[blockIdx.x].ds); }
+__global__ void __launch_bounds__(kThreads) k_zero_depth_b(const CGJob *jobs, int n) {
+  for_team(jobs, n, [](const CGJob &j, Team t) {
+    for (int p = t.bid * blockDim.x + threadIdx.x; p < j.g.P; p += t.nblk * blockDim.x) j.g.depth[p] = 0.0f;
+  });
+}
 
 size_t cg_job_bytes() { return sizeof(CGJob); }
 
@@ -930,6 +935,11 @@ cudaError_t solve_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, i
   k_store_depth_b<<<blocks, kThreads, 0, s>>>(jobs, n);
   LAUNCH_CHECK();
   return cudaSuccess;
+}
+
+cudaError_t zero_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks) {
+  k_zero_depth_b<<<blocks, kThreads, 0, s>>>((const CGJob *)d_jobs, n);
+  return cudaGetLastError();
 }
 
 cudaError_t depth_change_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks) {

@@ -33,7 +33,7 @@ EXPORTED = [
     "irtps_set_indirect", "irtps_render", "irtps_get_normals", "irtps_get_albedo", "irtps_get_depth",
     "irtps_get_indirect", "irtps_get_valid", "irtps_get_stats", "irtps_probe_dirs", "irtps_probe_rays",
     "irtps_last_error", "irtps_destroy", "irtps_integrate_noalloc", "irtps_set_object", "irtps_set_tuning",
-    "irtps_get_tuning", "irtps_autotune", "irtps_batch_create", "irtps_batch_iterate", "irtps_batch_get_stats",
+    "irtps_get_tuning", "irtps_autotune", "irtps_batch_create", "irtps_batch_set_stream", "irtps_batch_set_images", "irtps_batch_iterate", "irtps_batch_get_stats",
     "irtps_batch_set_tuning", "irtps_batch_get_tuning", "irtps_batch_autotune", "irtps_batch_last_error",
     "irtps_batch_destroy",
 ]
@@ -101,6 +101,8 @@ def _load():
         "irtps_autotune": (i32, [P, i32, i32, u64, P]),
         "irtps_batch_create": (i32, [P, P, i32, i32]),
         "irtps_batch_iterate": (i32, [P, i32, P, P, u64, P]),
+        "irtps_batch_set_stream": (i32, [P, P]),
+        "irtps_batch_set_images": (i32, [P, P, i32, i32]),
         "irtps_batch_get_stats": (i32, [P, P]),
         "irtps_batch_set_tuning": (i32, [P, i32, i32]),
         "irtps_batch_get_tuning": (i32, [P, P, P]),
@@ -324,6 +326,18 @@ def irtps_batch_create(handles, use_graph=False):
     return b
 
 
+def irtps_batch_set_stream(b, stream):
+    _check_batch(b, _lib.irtps_batch_set_stream(b, ctypes.c_void_p(stream) if stream else None))
+
+
+def irtps_batch_set_images(b, images, dtype=IRTPS_F32, on_device=False):
+    """images: one array per object (numpy host arrays, or device tensors with on_device)."""
+    if not on_device:
+        images = [_host(a, np.float16 if dtype == IRTPS_F16 else np.float32) for a in images]
+    ptrs = (ctypes.c_void_p * len(images))(*[_addr(a).value for a in images])
+    _check_batch(b, _lib.irtps_batch_set_images(b, ptrs, dtype, 1 if on_device else 0))
+
+
 def irtps_batch_iterate(b, n_iter, spp, bounces, seed):
     n = len(spp)
     s = _host(spp, np.int32)
@@ -489,6 +503,12 @@ class Batch:
                 self.close()
         except Exception:
             pass
+
+    def set_stream(self, stream):
+        irtps_batch_set_stream(self.b, stream)
+
+    def set_images(self, images, dtype=IRTPS_F32, on_device=False):
+        irtps_batch_set_images(self.b, images, dtype, on_device)
 
     def iterate(self, n_iter, spp, bounces, seed):
         return irtps_batch_iterate(self.b, n_iter, spp, bounces, seed)

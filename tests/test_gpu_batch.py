@@ -174,3 +174,36 @@ def test_batch_autotune_and_errors(lib, oracle_mod):
     finally:
         for c in ctxs:
             c.close()
+
+
+def test_batch_set_images_matches_single(lib, oracle_mod):
+    """Batched iteration 0 (classic PS and integration of every object) against each
+    object's irtps_set_images: normals bit-identical, depth within the solver's tolerance;
+    then a batched iteration over it matches the oracle loop."""
+    scs = _scenes(SMALL)
+    A = _images(oracle_mod, scs, 19)
+    ctxs = [lib.Context(sc.H, sc.W, sc.lights, sc.env) for sc in scs]
+    try:
+        with lib.Batch(ctxs) as b:
+            b.set_images(A)
+            st = b.stats()
+            assert st["cg_rel_residual"] <= 1e-9
+            got = [(c.normals(), c.depth(), c.valid()) for c in ctxs]
+            spp = [s[4] for s in SMALL]
+            bounces = [s[5] for s in SMALL]
+            b.iterate(1, spp, bounces, 3)
+            after = [(c.normals(), c.depth()) for c in ctxs]
+        for i, (sc, a) in enumerate(zip(scs, A)):
+            with lib.Context(sc.H, sc.W, sc.lights, sc.env) as c:
+                c.set_images(a)
+                n, d, v = c.normals(), c.depth(), c.valid()
+            assert np.array_equal(got[i][0], n), i
+            assert np.array_equal(got[i][2], v), i
+            assert np.abs(got[i][1] - d).max() <= 1e-6 * np.ptp(d), i
+            hist = oracle_mod.irtps_run(a, sc.lights, sc.env, 1, spp[i], bounces[i], 3, obj=i)
+            err = oracle_mod.angular_error_deg(after[i][0][..., :3].reshape(-1, 3), hist[1]["normals"].reshape(-1, 3))
+            dabs = np.abs(after[i][1] - hist[1]["depth"]) / np.ptp(hist[1]["depth"])
+            assert err.mean() <= 0.05 and dabs.mean() <= 1e-4 and dabs.max() <= 1e-3, (i, err.mean(), dabs.max())
+    finally:
+        for c in ctxs:
+            c.close()
