@@ -57,6 +57,9 @@ OPS_PER_NODE = 16
 OPS_PER_TRI = 57
 SM_COUNT = 152
 LANES_PER_SM = 128
+# DRAM bytes (read + write) of one trace launch of a workload, from the ncu capture summarised in
+# profiles/k_trace_bumps512_dram.md (the kernel has not changed since)
+TRACE_DRAM_BYTES = {"bumps_512": 10.27e6 + 2.03e6}
 
 
 def sm_max_mhz():
@@ -476,7 +479,7 @@ def main():
     achieved = ops / (tot["trace_ms"] / 1e3) / 1e12
     peak = SM_COUNT * LANES_PER_SM * mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_trace",
+                "traffic": TRACE_DRAM_BYTES.get(args.workload), "kernel": "k_trace",
                 "launch_ms": tot["trace_ms"] / trace_launches,
                 "note": "lane-operation issue peak = 152 SMs x 128 lanes x max SM clock; ops counted per "
                         "sampled direction, pyramid node visit and triangle test"}
