@@ -87,6 +87,9 @@ def _load():
             lib.oracle_trace.argtypes = [i32, i32, i32, i32, P, P, P, P, P, i32, i32, P, i32, i32, i32,
                                          u64, u32, u32, u32, i32, i32, i32, P, P, P]
             lib.oracle_trace.restype = i32
+            lib.oracle_trace_shared.argtypes = [i32, i32, i32, i32, P, P, P, P, P, i32, i32, P, i32, i32, i32,
+                                         u64, u32, u32, u32, i32, i32, i32, P, P, P]
+            lib.oracle_trace_shared.restype = i32
             lib.oracle_pixel_visibility.argtypes = [i32, i32, i32, P, P, P, i32, P]
             lib.oracle_pixel_visibility.restype = i32
             lib.oracle_noise.argtypes = [i32, i32, i32, i32, u64, u32, P]
@@ -190,7 +193,7 @@ def pack_normals(normals, albedo):
 
 
 def trace(depth, normals, albedo, lights, env, spp, bounces, seed, iteration, *, pixels=None,
-          stream=0, obj=0, shadow_rays=True, fp32=True, threads=0, records=False):
+          stream=0, obj=0, shadow_rays=True, fp32=True, threads=0, records=False, shared=False):
     """Mean incident radiance Lbar (K, C, n_pix) of the reverted Monte-Carlo trace.
 
     depth (H, W), normals (H, W, 3), albedo (C, H, W) are the current estimate,
@@ -198,6 +201,10 @@ def trace(depth, normals, albedo, lights, env, spp, bounces, seed, iteration, *,
     precision (the kernel's); fp32=False in double.  Returns (lbar, records, counts):
     records (n_pix, K, spp, bounces, 2) int32 {hit pixel | -1 escape | -2 not reached,
     shadow visibility 1/0 | -1 not cast} when requested; counts = (primary, segments).
+
+    shared=True: light-shared sampling, one path per (pixel, sample) for all K lights
+    (directions drawn with light field 0); records then (n_pix, spp, bounces, 1 + K)
+    {hit pixel | -1 | -2, V_0 .. V_{K-1}}.
     """
     lib = _load()
     d = _c(depth, np.float32)
@@ -212,9 +219,13 @@ def trace(depth, normals, albedo, lights, env, spp, bounces, seed, iteration, *,
     pix = None if pixels is None else _c(pixels, np.int32)
     n_pix = H * W if pix is None else pix.size
     out = np.zeros((K, C, n_pix))
-    rec = np.zeros((n_pix, K, spp, bounces, 2), np.int32) if records else None
+    if shared:
+        rec = np.zeros((n_pix, spp, bounces, 1 + K), np.int32) if records else None
+    else:
+        rec = np.zeros((n_pix, K, spp, bounces, 2), np.int32) if records else None
     counts = np.zeros(2, np.uint64)
-    rc = lib.oracle_trace(H, W, C, K, _ptr(d), _ptr(n4), _ptr(a), _ptr(l), _ptr(e), EH, EW, _ptr(pix),
+    fn = lib.oracle_trace_shared if shared else lib.oracle_trace
+    rc = fn(H, W, C, K, _ptr(d), _ptr(n4), _ptr(a), _ptr(l), _ptr(e), EH, EW, _ptr(pix),
                           n_pix, spp, bounces, int(seed), obj, int(iteration) & 0xFFFFFFFF, stream,
                           int(shadow_rays), int(fp32), int(threads), _ptr(out), _ptr(rec), _ptr(counts))
     if rc != 0:
@@ -426,11 +437,12 @@ def ps_step(A0, rho_t, lbar, lights, tau_lo=TAU_LO, tau_hi=TAU_HI, cond_max=COND
 
 
 def irtps_run(A0, lights, env, n_iter, spp, bounces, seed, *, shadow_rays=True, fp32=True, threads=0,
-              tau_lo=TAU_LO, tau_hi=TAU_HI, obj=0):
+              tau_lo=TAU_LO, tau_hi=TAU_HI, obj=0, shared=False):
     """The IRT-PS loop: iteration 0 is classic PS + integration; each further
     iteration traces Lbar on the current estimate (iteration index t), subtracts
     rho_t * Lbar_t from the ORIGINAL images, re-solves PS and re-integrates.
-    `obj` is the object index in the Philox key {seed_lo ^ obj, seed_hi}.
+    `obj` is the object index in the Philox key {seed_lo ^ obj, seed_hi}; `shared`
+    selects light-shared sampling for the trace.
     Returns a list of per-iteration dicts (depth, normals, albedo, lbar, dH)."""
     A0 = np.asarray(A0, np.float32)
     K, C, H, W = A0.shape
@@ -444,7 +456,7 @@ def irtps_run(A0, lights, env, n_iter, spp, bounces, seed, *, shadow_rays=True, 
         st = hist[-1]
         lbar, _, counts = trace(st["depth"].astype(np.float32), st["normals"].astype(np.float32),
                                 st["albedo"].astype(np.float32), lights, env, spp, bounces, seed, t,
-                                obj=obj, shadow_rays=shadow_rays, fp32=fp32, threads=threads)
+                                obj=obj, shadow_rays=shadow_rays, fp32=fp32, threads=threads, shared=shared)
         n, rho, ok = ps_step(A0, st["albedo"].astype(np.float32).reshape(C, -1), lbar, lights, tau_lo,
                              tau_hi)
         depth = poisson_solve(n.reshape(H, W, 3), h)

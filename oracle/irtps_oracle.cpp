@@ -478,6 +478,104 @@ void trace_pixels(const Scene &sc, const int32_t *pixels, int n_pix, int spp, in
   }
 }
 
+// Light-shared sampling: one sample path per (pixel p, sample s) serves all K
+// lights.  The directions are drawn with light field 0 of the counter, so the
+// path of sample s is the one light 0 takes in the per-light trace.  On escape
+// T*Env(w) is added for every light; on a hit at q, every light k with
+// n_q . l_k > 0 gets T * rho_q * (n_q . l_k) * V_k(q) (one shadow ray per such
+// light); then T <- T * rho_q and the path continues.  acc is K x 3.
+// rec (nullable) holds B entries of 1 + K ints: {hit pixel | -1, V_0 .. V_{K-1}}.
+template <class T>
+void trace_path_shared(const Scene &sc, int p, int s, int B, uint32_t iter, uint32_t stream,
+                       const uint32_t key[2], double *acc, int32_t *rec, Counts &cnt) {
+  const int W = sc.W, H = sc.H, K = sc.K;
+  const T eps = eps_lift<T>(W);
+  const int pi = p / W, pj = p % W;
+  V3<T> o = {(T)pj, (T)pi, (T)sc.depth[p] + eps};
+  V3<T> n = {(T)sc.nrm[4 * (size_t)p + 0], (T)sc.nrm[4 * (size_t)p + 1], (T)sc.nrm[4 * (size_t)p + 2]};
+  double thr[3] = {1.0, 1.0, 1.0};
+  for (int b = 1; b <= B; ++b) {
+    int32_t *r = rec ? rec + (size_t)(b - 1) * (1 + K) : nullptr;
+    uint32_t x[4];
+    draw((uint32_t)p, (uint32_t)s, 0u, (uint32_t)b, stream, iter, key, x);
+    const V3<T> dw = cosine_dir<T>(n, x[0], x[1]);
+    const V3<T> dg = {dw.x * (T)W, dw.y * (T)W, dw.z};
+    cnt.segments++;
+    if (b == 1) cnt.primary++;
+    const Hit<T> h = march<T>(sc.field, o, dg);
+    if (!h.hit) {
+      for (int k = 0; k < K; ++k)
+        for (int c = 0; c < sc.C; ++c)
+          acc[3 * k + c] +=
+              thr[c] * env_lookup(sc.env, sc.EH, sc.EW, c, (double)dw.x, (double)dw.y, (double)dw.z);
+      if (r)
+        for (int k = 0; k <= K; ++k) r[k] = -1;
+      return;
+    }
+    const V3<T> q = {o.x + h.t * dg.x, o.y + h.t * dg.y, o.z + h.t * dg.z};
+    const int qi = nearest_index<T>(q.y, H), qj = nearest_index<T>(q.x, W);
+    const size_t qp = (size_t)qi * W + qj;
+    const V3<T> nq = {(T)sc.nrm[4 * qp + 0], (T)sc.nrm[4 * qp + 1], (T)sc.nrm[4 * qp + 2]};
+    const V3<T> o2 = {q.x, q.y, q.z + eps};
+    if (r) r[0] = (int32_t)qp;
+    for (int k = 0; k < K; ++k) {
+      const float *l = sc.lights + 3 * k;
+      const V3<T> lf = {(T)l[0], (T)l[1], (T)l[2]};
+      int vis = -1;
+      if (dot(nq, lf) > (T)0) {
+        vis = 1;
+        if (sc.shadow_rays) {
+          cnt.segments++;
+          vis = visible<T>(sc, o2, k) ? 1 : 0;
+        }
+        const double cosd = std::max(0.0, (double)sc.nrm[4 * qp + 0] * l[0] + (double)sc.nrm[4 * qp + 1] * l[1] +
+                                              (double)sc.nrm[4 * qp + 2] * l[2]);
+        for (int c = 0; c < sc.C; ++c)
+          acc[3 * k + c] += thr[c] * (double)sc.albedo[(size_t)c * H * W + qp] * cosd * (double)vis;
+      }
+      if (r) r[1 + k] = vis;
+    }
+    for (int c = 0; c < sc.C; ++c) thr[c] *= (double)sc.albedo[(size_t)c * H * W + qp];
+    o = o2;
+    n = nq;
+  }
+}
+
+template <class T>
+void trace_pixels_shared(const Scene &sc, const int32_t *pixels, int n_pix, int spp, int B, uint32_t iter,
+                         uint32_t stream, const uint32_t key[2], double *out_lbar, int32_t *out_rec,
+                         uint64_t *out_counts, int n_threads) {
+  const int K = sc.K, C = sc.C;
+  uint64_t prim = 0, segs = 0;
+#ifdef _OPENMP
+  if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads) reduction(+ : prim, segs)
+#endif
+  for (int ip = 0; ip < n_pix; ++ip) {
+    const int p = pixels ? pixels[ip] : ip;
+    Counts cnt;
+    std::vector<double> sum((size_t)3 * K, 0.0), acc((size_t)3 * K);
+    for (int s = 0; s < spp; ++s) {
+      std::fill(acc.begin(), acc.end(), 0.0);
+      int32_t *rec = nullptr;
+      if (out_rec) {
+        rec = out_rec + ((size_t)ip * spp + s) * B * (1 + K);
+        for (int i = 0; i < B * (1 + K); ++i) rec[i] = -2;
+      }
+      trace_path_shared<T>(sc, p, s, B, iter, stream, key, acc.data(), rec, cnt);
+      for (int i = 0; i < 3 * K; ++i) sum[i] += acc[i];
+    }
+    for (int k = 0; k < K; ++k)
+      for (int c = 0; c < C; ++c) out_lbar[((size_t)k * C + c) * n_pix + ip] = sum[3 * k + c] / (double)spp;
+    prim += cnt.primary;
+    segs += cnt.segments;
+  }
+  if (out_counts) {
+    out_counts[0] = prim;
+    out_counts[1] = segs;
+  }
+}
+
 Scene make_scene(int H, int W, int C, int K, const float *depth, const float *nrm, const float *albedo,
                  const float *lights, const float *env, int EH, int EW, int shadow_rays) {
   Scene sc{H, W, C, K, depth, nrm, albedo, lights, env, EH, EW, shadow_rays, {H, W, depth, 0.0f}};
@@ -616,6 +714,27 @@ int oracle_trace(int H, int W, int C, int K, const float *depth, const float *nr
   else
     trace_pixels<double>(sc, pixels, n_pix, spp, bounces, iter, stream, key, out_lbar, out_rec, out_counts,
                          n_threads);
+  return 0;
+}
+
+// The light-shared trace (same arguments as oracle_trace): out_lbar K x C x n_pix;
+// out_rec optional n_pix x spp x bounces x (1 + K): {hit pixel | -1 escape | -2 not
+// reached, then V_k: 1 visible, 0 blocked, -1 not cast, -2 not reached}.
+int oracle_trace_shared(int H, int W, int C, int K, const float *depth, const float *nrm, const float *albedo,
+                        const float *lights, const float *env, int EH, int EW, const int32_t *pixels, int n_pix,
+                        int spp, int bounces, uint64_t seed, uint32_t obj, uint32_t iter, uint32_t stream,
+                        int shadow_rays, int fp32, int n_threads, double *out_lbar, int32_t *out_rec,
+                        uint64_t *out_counts) {
+  if (H < 2 || W < 2 || C < 1 || C > 3 || K < 1 || spp < 1 || bounces < 1 || bounces > 3) return -1;
+  const Scene sc = make_scene(H, W, C, K, depth, nrm, albedo, lights, env, EH, EW, shadow_rays);
+  const uint32_t key[2] = {(uint32_t)seed ^ obj, (uint32_t)(seed >> 32)};
+  if (!pixels) n_pix = H * W;
+  if (fp32)
+    trace_pixels_shared<float>(sc, pixels, n_pix, spp, bounces, iter, stream, key, out_lbar, out_rec, out_counts,
+                               n_threads);
+  else
+    trace_pixels_shared<double>(sc, pixels, n_pix, spp, bounces, iter, stream, key, out_lbar, out_rec,
+                                out_counts, n_threads);
   return 0;
 }
 
