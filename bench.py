@@ -367,6 +367,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--images", default="f32", choices=["f32", "f16"],
                     help="storage type of the input images (f16: the mixed-precision pattern)")
+    ap.add_argument("--sampling", default="per_light", choices=["per_light", "shared"],
+                    help="trace sampling: spp paths per (pixel, light), or per pixel for all lights")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -390,7 +392,9 @@ def main():
     H, W, K, C = sc.H, sc.W, sc.K, sc.C
     seed = 1 + rank
     stream = torch.cuda.Stream(device=dev)
-    ctx = irtps.Context(H, W, sc.lights, sc.env)
+    opt = irtps.irtps_default_options()
+    opt.sampling = 1 if args.sampling == "shared" else 0
+    ctx = irtps.Context(H, W, sc.lights, sc.env, opt)
     ctx.set_stream(stream.cuda_stream)
     A0 = torch.empty((K, C, H, W), dtype=torch.float32, device=dev)
     ctx.set_state(sc.depth, sc.normals, sc.albedo)
@@ -479,7 +483,8 @@ def main():
     achieved = ops / (tot["trace_ms"] / 1e3) / 1e12
     peak = SM_COUNT * LANES_PER_SM * mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": TRACE_DRAM_BYTES.get(args.workload), "kernel": "k_trace",
+                "traffic": TRACE_DRAM_BYTES.get(args.workload) if args.sampling == "per_light" else None,
+                "kernel": "k_trace",
                 "launch_ms": tot["trace_ms"] / trace_launches,
                 "note": "lane-operation issue peak = 152 SMs x 128 lanes x max SM clock; ops counted per "
                         "sampled direction, pyramid node visit and triangle test"}
@@ -488,6 +493,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "H": H, "W": W, "K": K, "C": C, "spp": spp, "images": args.images,
+                       "sampling": args.sampling,
                        "bounces": bounces, "irt_iterations_per_step": n_iter, "parallelism": f"replicas{world}",
                        "l2": "512 MB buffer written between timed steps"},
             "pixel_iters_per_s": P * n_iter * world * args.steps / (ms_all / 1e3),

@@ -70,6 +70,11 @@ typedef struct irtps_options {
   int precond;        /* depth-solve preconditioner: 0 Jacobi (diagonal), 1 multigrid V-cycle (1) */
   int use_graph;      /* 1: irtps_iterate captures one iteration as a CUDA graph and replays it (0);
                          per-stage times are then not measured (reported as 0) */
+  int sampling;       /* trace sampling (0):
+                         0 per light: spp paths for every (pixel, light), counter light field k;
+                         1 light-shared: spp paths per pixel serve all K lights (counter light
+                           field 0; at each hit one shadow ray per light facing the hit normal);
+                           the same expectation with about K times fewer path segments */
 } irtps_options;
 
 /* Counters of the last irtps_iterate / irtps_trace / irtps_integrate call. */
@@ -134,7 +139,9 @@ int irtps_integrate(irtps_ctx *ctx);
 
 /* Trace a list of pixels only (host arrays): out_lbar K x C x n_pix;
  * out_rec (nullable) n_pix x K x spp x bounces x 2 int32 per segment:
- * {hit pixel | -1 escape | -2 not reached, shadow visibility 1 | 0 | -1 not cast}. */
+ * {hit pixel | -1 escape | -2 not reached, shadow visibility 1 | 0 | -1 not cast};
+ * with light-shared sampling n_pix x spp x bounces x (1 + K):
+ * {hit pixel | -1 | -2, then the visibility of each light 1 | 0 | -1 not cast | -2}. */
 int irtps_trace_pixels(irtps_ctx *ctx, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
                        uint32_t iteration, uint32_t stream_tag, float *out_lbar, int32_t *out_rec);
 
@@ -219,7 +226,7 @@ int irtps_autotune(irtps_ctx *ctx, int spp_probe, int bounces, uint64_t seed, do
  * per-item cost first), one PS launch, one cooperative depth-solve launch in
  * which each object's solve runs on its own team of blocks, and one D_H launch.
  * Objects may differ in H, W, K, spp, bounces and options; all must have the
- * same C and image dtype.  Every object's results are bit-identical to its own
+ * same C and image dtype and per-light sampling (sampling = 0).  Every object's results are bit-identical to its own
  * irtps_iterate in the trace and the normal solve; the depth solve differs from
  * it only by the summation order of its reductions (team size), within cg_tol.
  *

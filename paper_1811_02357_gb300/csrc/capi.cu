@@ -43,7 +43,7 @@ int dalloc(Ctx &c, T **p, size_t n, const char *what) {
 }
 
 void release(Ctx &c) {
-  void *bufs[] = {c.env, c.d_lights, c.images, c.lbar, c.depth, c.depth_prev, c.nrm, c.albedo, c.valid, c.pmin, c.pmax,
+  void *bufs[] = {c.env, c.d_lights, c.shared_part, c.images, c.lbar, c.depth, c.depth_prev, c.nrm, c.albedo, c.valid, c.pmin, c.pmax,
                   c.cg_x, c.cg_b, c.cg_r, c.cg_z, c.cg_p, c.cg_ap, c.part, c.dstats, c.next_item, c.cg_ctl,
                   c.mg_x0, c.mg_x1, c.mg_b, c.mg_wh, c.mg_wv, c.iter_dev};
   for (void *b : bufs)
@@ -147,7 +147,7 @@ int trace_into(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, u
   CK(irtps::launch_trace(c, pixels, n_pix, spp, bounces, seed, iter, stream_tag, out, rec, iter_from_device),
      "trace launch");
   if (!iter_from_device) STAGE(ST_TRACE, false);
-  c.stats.primary_segments += (unsigned long long)n_pix * c.K * spp;
+  c.stats.primary_segments += (unsigned long long)n_pix * (c.opt.sampling == 1 ? 1 : c.K) * spp;
   return IRTPS_OK;
 }
 
@@ -157,6 +157,25 @@ bool trace_args_ok(Ctx &c, int spp, int bounces) {
     return false;
   }
   return true;
+}
+
+// Light-shared traces keep per-chunk partial sums; size them before any capture.
+int prepare_trace(Ctx &c, int n_pix, int spp) {
+  if (c.opt.sampling != 1) return IRTPS_OK;
+  const size_t need = irtps::shared_scratch_floats(c, n_pix, spp);
+  if (need <= c.shared_cap) return IRTPS_OK;
+  CK(cudaStreamSynchronize(c.stream), "trace scratch");
+  if (c.graph) {  // a captured iteration holds the old buffer
+    cudaGraphExecDestroy(c.graph);
+    c.graph = nullptr;
+  }
+  if (c.shared_part) cudaFree(c.shared_part);
+  c.shared_part = nullptr;
+  c.shared_cap = 0;
+  int rc = dalloc(c, &c.shared_part, need, "light-shared partial sums");
+  if (rc) return rc;
+  c.shared_cap = need;
+  return IRTPS_OK;
 }
 
 int run_ps(Ctx &c, bool zero_indirect) {
@@ -248,6 +267,7 @@ void irtps_default_options(irtps_options *opt) {
   opt->stop_tol = 0.0;
   opt->precond = 1;
   opt->use_graph = 0;
+  opt->sampling = 0;
 }
 
 int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *lights, const float *env, int EH,
@@ -279,6 +299,8 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
     irtps_default_options(&c.opt);
   if (c.opt.precond != 0 && c.opt.precond != 1)
     return bail(fail(c, IRTPS_EINVAL, "create: precond must be 0 (Jacobi) or 1 (multigrid)"));
+  if (c.opt.sampling != 0 && c.opt.sampling != 1)
+    return bail(fail(c, IRTPS_EINVAL, "create: sampling must be 0 (per light) or 1 (light-shared)"));
   c.eps = (float)1e-3 / (float)W;  // same expression as the oracle's lift
   // lights and pinv(L) = (L^T L)^-1 L^T in FP64 (Eq. 4)
   c.h_lights.assign(lights, lights + 3 * K);
@@ -419,8 +441,8 @@ int irtps_iterate(irtps_ctx *ctx, int n_iter, int spp, int bounces, uint64_t see
   if (!c.have_images) return fail(c, IRTPS_ENOTREADY, "iterate: call irtps_set_images first");
   if (n_iter < 0 || !trace_args_ok(c, spp, bounces)) return fail(c, IRTPS_EINVAL, c.err.empty() ? "iterate" : c.err);
   c.stats.iterations_done = 0;
-  int rc = begin_call(c);
-  if (rc) return rc;
+  int rc = prepare_trace(c, c.H * c.W, spp);
+  if (rc || (rc = begin_call(c))) return rc;
   if (c.opt.use_graph && n_iter > 0) {
     if ((rc = capture_iteration(c, spp, bounces, seed))) return rc;
     CK(cudaMemcpyAsync(c.iter_dev, &c.t, sizeof(uint32_t), cudaMemcpyHostToDevice, c.stream), "iteration counter");
@@ -430,7 +452,7 @@ int irtps_iterate(irtps_ctx *ctx, int n_iter, int spp, int bounces, uint64_t see
   for (int it = 0; it < n_iter; ++it) {
     if (c.opt.use_graph) {
       CK(cudaGraphLaunch(c.graph, c.stream), "graph launch");
-      c.stats.primary_segments += (unsigned long long)c.H * c.W * c.K * spp;
+      c.stats.primary_segments += (unsigned long long)c.H * c.W * (c.opt.sampling == 1 ? 1 : c.K) * spp;
     } else if ((rc = enqueue_iteration(c, spp, bounces, seed, false))) {
       return rc;
     }
@@ -452,7 +474,9 @@ int irtps_trace(irtps_ctx *ctx, int spp, int bounces, uint64_t seed, uint32_t it
   if (!ctx) return IRTPS_EINVAL;
   Ctx &c = ctx->c;
   if (!trace_args_ok(c, spp, bounces) || stream_tag > 15) return fail(c, IRTPS_EINVAL, "trace: bad arguments");
-  int rc = begin_call(c);
+  int rc = prepare_trace(c, c.H * c.W, spp);
+  if (rc) return rc;
+  rc = begin_call(c);
   if (rc || (rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, iteration, stream_tag, c.lbar, nullptr)))
     return rc;
   return end_call(c, false);
@@ -484,10 +508,13 @@ int irtps_trace_pixels(irtps_ctx *ctx, const int32_t *pixels, int n_pix, int spp
   const int P = c.H * c.W;
   for (int i = 0; i < n_pix; ++i)
     if (pixels[i] < 0 || pixels[i] >= P) return fail(c, IRTPS_EINVAL, "trace_pixels: pixel index out of range");
-  const size_t nrec = out_rec ? (size_t)n_pix * c.K * spp * bounces * 2 : 0;
+  const size_t nrec = !out_rec ? 0
+                     : (c.opt.sampling == 1 ? (size_t)n_pix * spp * bounces * (1 + c.K)
+                                            : (size_t)n_pix * c.K * spp * bounces * 2);
   int32_t *d_pix = nullptr, *d_rec = nullptr;
   float *d_out = nullptr;
-  int rc;
+  int rc = prepare_trace(c, n_pix, spp);
+  if (rc) return rc;
   if ((rc = dalloc(c, &d_pix, n_pix, "pixel list")) || (rc = dalloc(c, &d_out, (size_t)c.K * c.C * n_pix, "out")) ||
       (out_rec && (rc = dalloc(c, &d_rec, nrec, "records")))) {
     cudaFree(d_pix);
@@ -557,10 +584,14 @@ int irtps_render(irtps_ctx *ctx, int spp, int bounces, uint64_t seed, float sigm
   if (!ctx) return IRTPS_EINVAL;
   Ctx &c = ctx->c;
   if (!out || !trace_args_ok(c, spp, bounces) || !(sigma >= 0.0f)) return fail(c, IRTPS_EINVAL, "render: bad arguments");
+  // the synthetic images take the per-light trace whatever the context's sampling
+  const int sampling = c.opt.sampling;
+  c.opt.sampling = 0;
   int rc = begin_call(c);
-  if (rc || (rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, 0xFFFFFFFFu, 1u, c.lbar, nullptr)) ||
-      (rc = end_call(c, false)))
-    return rc;
+  if (rc == IRTPS_OK) rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, 0xFFFFFFFFu, 1u, c.lbar, nullptr);
+  if (rc == IRTPS_OK) rc = end_call(c, false);
+  c.opt.sampling = sampling;
+  if (rc) return rc;
   const size_t n = (size_t)c.K * c.C * c.H * c.W;
   float *dst = out;
   float *tmp = nullptr;
@@ -713,6 +744,7 @@ int irtps_autotune(irtps_ctx *ctx, int spp_probe, int bounces, uint64_t seed, do
     for (int ps : per_sm) {
       c.trace_blocks = ps * c.sms;
       c.mip_cut = cut;
+      if ((rc = prepare_trace(c, c.H * c.W, spp_probe))) break;
       for (int rep = 0; rep < 2; ++rep) {  // the first run warms the caches; the second is timed
         c.tev_used = 0;
         if ((rc = trace_into(c, nullptr, c.H * c.W, spp_probe, bounces, seed, c.t, 0u, c.lbar, nullptr))) break;

@@ -79,6 +79,8 @@ struct Ctx {
   std::vector<float> h_lights;    // K*3
   std::vector<float> h_pinv;      // 3*K, (L^T L)^-1 L^T rounded to float
   float *d_lights = nullptr;      // K*3 on the device (read at trace hits)
+  float *shared_part = nullptr;   // light-shared trace: partial sums of its sample chunks
+  size_t shared_cap = 0;          // floats in shared_part
 
   // device buffers (owned)
   float *env = nullptr;           // C*EH*EW
@@ -168,7 +170,8 @@ cudaError_t launch_next_iter(Ctx &c);  // iter_dev += 1 (end of a captured itera
 cudaError_t launch_next_iter(cudaStream_t s, uint32_t *iter_dev);
 cudaError_t launch_render(Ctx &c, uint64_t seed, float sigma, const float *lbar, float *out);
 int trace_grid_limit(int C, int n_obj = 0);  // resident blocks of the (batched) trace kernel, 0 if unknown
-void fill_obj_trace(const Ctx &c, ObjTrace &o);  // descriptor of a context's object (no sampling fields)
+void fill_obj_trace(const Ctx &c, ObjTrace &o);
+size_t shared_scratch_floats(const Ctx &c, int n_pix, int spp);  // light-shared chunk partials needed  // descriptor of a context's object (no sampling fields)
 cudaError_t launch_trace_batch(cudaStream_t s, int C, const ObjTrace *d_objs, int n_obj, unsigned n_items,
                                unsigned long long *counts, unsigned *next_item, const uint32_t *iter_dev,
                                uint32_t iter, int grid_limit);

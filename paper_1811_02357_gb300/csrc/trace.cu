@@ -1,6 +1,7 @@
 // Reverted Monte-Carlo trace (Sec. IV, Eq. 5-7): min/max pyramid build, the
 // per-(pixel, light) trace kernel, the stage-0 forward render, and geometry
 // probes used by the parity tests.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <cuda_fp16.h>
@@ -188,11 +189,15 @@ struct TraceArgs {
   int n_obj;
   unsigned n_items;            // all work items of the launch
   const int32_t *pixels;       // optional pixel list (single object)
-  int32_t *rec;                // optional n_pix*K*spp*B*2 records (single object)
+  int32_t *rec;                // optional records (single object): per light n_pix*K*spp*B*2,
+                               // light-shared n_pix*spp*B*(1+K)
   unsigned long long *counts;  // {unused, segments, walk overflows, node visits, triangle tests, draws}
   unsigned *next_item;         // work-item counter, zero before the launch
   const uint32_t *iter_dev;    // when set, the iteration field is read here (graph replays)
   uint32_t iter, stream;
+  // light-shared sampling: partial sums n_chunks x K x C x n_pix (the output itself for one chunk)
+  float *part;
+  int n_chunks, chunk;
 };
 
 #ifndef IRTPS_TRACE_MINB
@@ -217,8 +222,9 @@ enum : int { PH_SETUP = 0, PH_MARCH = 1, PH_RESOLVE = 2, PH_DONE = 3 };
 // Dynamic shared memory of a trace launch over n objects: level tables and item ranges.
 static size_t trace_smem_bytes(int n) { return (size_t)n * sizeof(LevelTable) + (size_t)(n + 1) * sizeof(unsigned); }
 
-template <int C, bool BATCH>
-__global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH : IRTPS_TRACE_MINB) k_trace(const __grid_constant__ TraceArgs a) {
+template <int C, bool BATCH, bool SHARED>
+__global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH : IRTPS_TRACE_MINB)
+    k_trace(const __grid_constant__ TraceArgs a) {
   extern __shared__ __align__(16) unsigned char trace_smem[];
   LevelTable *lts = reinterpret_cast<LevelTable *>(trace_smem);
   const int n_obj = BATCH ? a.n_obj : 1;
@@ -237,17 +243,19 @@ __global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH 
   } else {
     load_levels(a.one.f, lts);
   }
-  // Work items are (object, light, pixel) triples, within an object
-  // item = k * n_pix + ip.  Each lane starts with the item of its global index
-  // and, when done, takes the next unclaimed item from a counter (claimed a warp
-  // at a time), so that no lane idles while items remain.  An item is always
-  // traced by one lane, samples in order.
+  // Work items.  Per-light sampling: (object, light k, pixel), within an object
+  // item = k * n_pix + ip, all spp samples of (p, k).  Light-shared sampling:
+  // (chunk j, pixel), item = j * n_pix + ip, samples [j * chunk, (j + 1) * chunk)
+  // of pixel p for all lights.  Each lane starts with the item of its global
+  // index and, when done, takes the next unclaimed item from a counter (claimed a
+  // warp at a time), so that no lane idles while items remain.  An item is
+  // always traced by one lane, samples in order.
   const unsigned n_items = a.n_items;
   unsigned item = blockIdx.x * blockDim.x + threadIdx.x;
   const ObjTrace *ob = &a.one;
   const LevelTable *lt = lts;
-  int k = 0, ip = 0, p = 0;
-  auto take = [&](unsigned it) {
+  int k = 0, ip = 0, p = 0, j = 0, s_end = 0;
+  auto take = [&](unsigned it) -> int {  // returns the item's first sample
     item = it;
     if constexpr (BATCH) {
       int lo = 0, hi = n_obj - 1;  // last object whose range starts at or before it
@@ -259,27 +267,35 @@ __global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH 
       lt = lts + lo;
       it -= s_begin[lo];
     }
-    k = (int)(it / (unsigned)ob->n_pix);
-    ip = (int)it - k * ob->n_pix;
+    const int q = (int)(it / (unsigned)ob->n_pix);
+    ip = (int)it - q * ob->n_pix;
     p = a.pixels ? a.pixels[ip] : ip;
+    if constexpr (SHARED) {
+      j = q;
+      s_end = min(ob->spp, (j + 1) * a.chunk);
+      return j * a.chunk;
+    } else {
+      k = q;
+      return 0;
+    }
   };
   const bool alive = item < n_items;
-  if (alive) take(item);
+  int s = alive ? take(item) : 0;
   // the pixel's own vertex, lifted: origin of every primary ray of this lane
   auto pixel_origin = [&]() -> F3 {
     const int W = ob->f.W;
     const int pi = p / W, pj = p - pi * W;
     return F3{(float)pj, (float)pi, radd(__ldg(ob->f.depth + p), ob->eps)};
   };
-  auto light = [&]() -> F3 {
-    const float *l = ob->lights + 3 * k;
+  auto light_k = [&](int kk) -> F3 {
+    const float *l = ob->lights + 3 * kk;
     return F3{__ldg(l), __ldg(l + 1), __ldg(l + 2)};
   };
   auto budget0 = [&]() -> int { return 8 * (ob->f.Wc + ob->f.Hc + 8) * (ob->f.levels + 1); };
   const uint32_t iter_base = a.iter_dev ? *a.iter_dev : a.iter;
 
   int phase = alive ? PH_SETUP : PH_DONE;
-  int s = 0, b = 1, qp = 0, budget = alive ? budget0() : 0;
+  int b = 1, qp = 0, ks = 0, budget = alive ? budget0() : 0;
   bool shadow = false;
   float cosv = 0.0f;
   float thr[C], acc[C], sum[C], comp[C];
@@ -294,11 +310,22 @@ __global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH 
   uint32_t segs = 0;
   int overflow = 0;
 
+  // records: per light {hit, visibility} per bounce; light-shared {hit, V_0 .. V_{K-1}} per bounce
   auto rec_slot = [&](int bb) -> int32_t * {
-    return a.rec + ((((size_t)ip * ob->K + k) * ob->spp + s) * ob->bounces + (bb - 1)) * 2;
+    if constexpr (SHARED)
+      return a.rec + (((size_t)ip * ob->spp + s) * ob->bounces + (bb - 1)) * (1 + ob->K);
+    else
+      return a.rec + ((((size_t)ip * ob->K + k) * ob->spp + s) * ob->bounces + (bb - 1)) * 2;
   };
+  auto rec_width = [&]() -> int { return SHARED ? 1 + ob->K : 2; };
   auto albedo_at = [&](int c, int q) -> float {
     return __ldg(ob->albedo + (size_t)c * ob->f.H * ob->f.W + q);
+  };
+  // light-shared: the direct term of light kk at the current hit, into the chunk's partial sums
+  auto add_direct = [&](int kk) {
+    float *d = a.part + ((size_t)j * ob->K + kk) * C * ob->n_pix + ip;
+#pragma unroll
+    for (int c = 0; c < C; ++c) d[(size_t)c * ob->n_pix] += thr[c] * albedo_at(c, qp) * cosv;
   };
   auto end_sample = [&]() {
 #pragma unroll
@@ -327,19 +354,55 @@ __global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH 
       end_sample();
     }
   };
+  // light-shared: the next light from ks on that faces the hit normal gets its
+  // shadow ray (or, without shadow rays, its direct term); then the path goes on
+  auto next_light = [&]() {
+    const float4 m4 = __ldg(ob->nrm + qp);
+    const F3 nq = {m4.x, m4.y, m4.z};
+    while (ks < ob->K) {
+      const F3 l = light_k(ks);
+      if (f3dot(nq, l) > 0.0f) {
+        cosv = fmaxf(0.0f, nq.x * l.x + nq.y * l.y + nq.z * l.z);
+        if (ob->shadow) {
+          walker_init(m, m.o, F3{rmul(l.x, ob->Wf), rmul(l.y, ob->Wf), l.z}, true);
+          shadow = true;
+          ++segs;
+          budget = budget0();
+          phase = PH_MARCH;
+          return;
+        }
+        if (a.rec) rec_slot(b)[1 + ks] = 1;
+        add_direct(ks);
+      }
+      ++ks;
+    }
+    shadow = false;
+    continue_path(qp);
+  };
 
   while (true) {
-    // ---- finished items: store the mean and claim the next item ----
-    const bool item_done = phase == PH_SETUP && s >= ob->spp;
+    // ---- finished items: store the result and claim the next item ----
+    const bool item_done = phase == PH_SETUP && s >= (SHARED ? s_end : ob->spp);
     const unsigned need = __ballot_sync(0xffffffffu, item_done);
     if (need) {
       if (item_done) {
-        const float inv = 1.0f / (float)ob->spp;
+        if constexpr (SHARED) {
+          // the environment part is common to every light; one chunk: also the mean
+          float *d = a.part + (size_t)j * ob->K * C * ob->n_pix + ip;
+          const float scale = a.n_chunks == 1 ? 1.0f / (float)ob->spp : 1.0f;
+          for (int kk = 0; kk < ob->K; ++kk)
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          ob->out[((size_t)k * C + c) * ob->n_pix + ip] = sum[c] * inv;
-          sum[c] = comp[c] = 0.0f;
+            for (int c = 0; c < C; ++c) {
+              float *v = d + ((size_t)kk * C + c) * ob->n_pix;
+              *v = (*v + sum[c]) * scale;
+            }
+        } else {
+          const float inv = 1.0f / (float)ob->spp;
+#pragma unroll
+          for (int c = 0; c < C; ++c) ob->out[((size_t)k * C + c) * ob->n_pix + ip] = sum[c] * inv;
         }
+#pragma unroll
+        for (int c = 0; c < C; ++c) sum[c] = comp[c] = 0.0f;
       }
       const int lane = threadIdx.x & 31;
       const int leader = __ffs(need) - 1;
@@ -350,8 +413,7 @@ __global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH 
       if (item_done) {
         const unsigned mine = base + (unsigned)__popc(need & ((1u << lane) - 1u));
         if (mine < n_items) {
-          take(mine);
-          s = 0;
+          s = take(mine);
           b = 1;
           budget = budget0();
         } else {
@@ -363,11 +425,12 @@ __global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH 
     if (phase == PH_SETUP) {
       if (a.rec && b == 1) {
         int32_t *r = rec_slot(1);
-        for (int j = 0; j < 2 * ob->bounces; ++j) r[j] = -2;
+        const int n = rec_width() * ob->bounces;
+        for (int i = 0; i < n; ++i) r[i] = -2;
       }
+      const uint32_t lf = SHARED ? 0u : (uint32_t)k;
       const uint4 x = philox4x32_10(
-          make_uint4((uint32_t)p, (uint32_t)s, ((uint32_t)k << 8) | ((uint32_t)b << 4) | a.stream,
-                     ob->iter0 + iter_base),
+          make_uint4((uint32_t)p, (uint32_t)s, (lf << 8) | ((uint32_t)b << 4) | a.stream, ob->iter0 + iter_base),
           ob->key);
       // bounce 1 leaves the pixel's own vertex about its normal; later bounces the
       // previous hit point (m.o) about the hit pixel's normal
@@ -408,12 +471,19 @@ __global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH 
     if (phase == PH_RESOLVE) {
       if (shadow) {
         const int vis = m.btri >= 0 ? 0 : 1;
-        if (a.rec) rec_slot(b)[1] = vis;
-        if (vis) {
+        if constexpr (SHARED) {
+          if (a.rec) rec_slot(b)[1 + ks] = vis;
+          if (vis) add_direct(ks);
+          ++ks;
+          next_light();
+        } else {
+          if (a.rec) rec_slot(b)[1] = vis;
+          if (vis) {
 #pragma unroll
-          for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * albedo_at(c, qp), cosv, acc[c]);
+            for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * albedo_at(c, qp), cosv, acc[c]);
+          }
+          continue_path(qp);
         }
-        continue_path(qp);
       } else if (m.btri < 0) {
         // escaped: environment radiance along the (world) direction
         const F3 dw = {m.d.x / ob->Wf, m.d.y / ob->Wf, m.d.z};
@@ -423,8 +493,8 @@ __global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH 
         for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c], e[c], acc[c]);
         if (a.rec) {
           int32_t *r = rec_slot(b);
-          r[0] = -1;
-          r[1] = -1;
+          const int n = rec_width();
+          for (int i = 0; i < n; ++i) r[i] = -1;
         }
         end_sample();
       } else {
@@ -432,32 +502,39 @@ __global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH 
         const float t = m.bt;
         const F3 q = {radd(m.o.x, rmul(t, m.d.x)), radd(m.o.y, rmul(t, m.d.y)), radd(m.o.z, rmul(t, m.d.z))};
         qp = nearest_index(q.y, H) * W + nearest_index(q.x, W);
-        const float4 m4 = __ldg(ob->nrm + qp);
-        const F3 nq = {m4.x, m4.y, m4.z};
         const F3 o2 = {q.x, q.y, radd(q.z, ob->eps)};
         if (a.rec) {
           int32_t *r = rec_slot(b);
           r[0] = qp;
-          r[1] = -1;
+          const int n = rec_width();
+          for (int i = 1; i < n; ++i) r[i] = -1;
         }
-        const F3 l = light();
-        if (f3dot(nq, l) > 0.0f) {
-          cosv = fmaxf(0.0f, nq.x * l.x + nq.y * l.y + nq.z * l.z);
-          if (ob->shadow) {
-            walker_init(m, o2, F3{rmul(l.x, ob->Wf), rmul(l.y, ob->Wf), l.z}, true);
-            shadow = true;
-            ++segs;
-            phase = PH_MARCH;
-          } else {
-            if (a.rec) rec_slot(b)[1] = 1;
+        if constexpr (SHARED) {
+          m.o = o2;  // origin of the shadow rays and of the next bounce
+          ks = 0;
+          next_light();
+        } else {
+          const float4 m4 = __ldg(ob->nrm + qp);
+          const F3 nq = {m4.x, m4.y, m4.z};
+          const F3 l = light_k(k);
+          if (f3dot(nq, l) > 0.0f) {
+            cosv = fmaxf(0.0f, nq.x * l.x + nq.y * l.y + nq.z * l.z);
+            if (ob->shadow) {
+              walker_init(m, o2, F3{rmul(l.x, ob->Wf), rmul(l.y, ob->Wf), l.z}, true);
+              shadow = true;
+              ++segs;
+              phase = PH_MARCH;
+            } else {
+              if (a.rec) rec_slot(b)[1] = 1;
 #pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * albedo_at(c, qp), cosv, acc[c]);
+              for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * albedo_at(c, qp), cosv, acc[c]);
+              m.o = o2;
+              continue_path(qp);
+            }
+          } else {
             m.o = o2;
             continue_path(qp);
           }
-        } else {
-          m.o = o2;
-          continue_path(qp);
         }
       }
     }
@@ -477,6 +554,16 @@ __global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH 
     if (nv) atomicAdd(a.counts + 3, nv);
     if (tt) atomicAdd(a.counts + 4, tt);
     if (dr) atomicAdd(a.counts + 5, dr);
+  }
+}
+
+// Light-shared traces in several sample chunks: Lbar = (sum of the chunks' partial sums) / spp.
+__global__ void k_reduce_chunks(const float *__restrict__ part, int n_chunks, size_t n, double inv_spp,
+                                float *__restrict__ out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int jj = 0; jj < n_chunks; ++jj) v += (double)part[(size_t)jj * n + i];
+    out[i] = (float)(v * inv_spp);
   }
 }
 
@@ -514,8 +601,26 @@ cudaError_t launch_next_iter(cudaStream_t s, uint32_t *iter_dev) {
   return cudaGetLastError();
 }
 
+// Light-shared sampling splits each pixel's samples into chunks so that there
+// are about 2^20 work items (several per lane of a full persistent grid).  The
+// split depends on the sizes only, never on the grid, so that the summation
+// order - and every result bit - is the same for any tuning.
+constexpr long long kSharedItems = 1ll << 20;
+int shared_chunks(const Ctx &, int n_pix, int spp) {
+  long long n = (kSharedItems + n_pix - 1) / n_pix;
+  n = n < 1 ? 1 : (n > spp ? spp : n);
+  const int chunk = (int)((spp + n - 1) / n);
+  return (spp + chunk - 1) / chunk;
+}
+
+size_t shared_scratch_floats(const Ctx &c, int n_pix, int spp) {
+  const int n = shared_chunks(c, n_pix, spp);
+  return n > 1 ? (size_t)n * c.K * c.C * n_pix : 0;
+}
+
 cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
                          uint32_t iter, uint32_t stream, float *out, int32_t *rec, bool iter_from_device) {
+  const bool shared = c.opt.sampling == 1;
   TraceArgs a;
   fill_obj_trace(c, a.one);
   a.one.n_pix = n_pix;
@@ -525,7 +630,6 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
   a.one.out = out;
   a.objs = nullptr;
   a.n_obj = 1;
-  a.n_items = (unsigned)n_pix * (unsigned)c.K;
   a.pixels = pixels;
   a.rec = rec;
   a.counts = c.dstats->counts;
@@ -533,7 +637,20 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
   a.iter_dev = iter_from_device ? c.iter_dev : nullptr;
   a.iter = iter;
   a.stream = stream;
-  const long long n = (long long)n_pix * c.K;
+  a.part = nullptr;
+  a.n_chunks = 1;
+  a.chunk = spp;
+  long long n = (long long)n_pix * c.K;
+  if (shared) {
+    a.n_chunks = shared_chunks(c, n_pix, spp);
+    a.chunk = (spp + a.n_chunks - 1) / a.n_chunks;
+    const size_t need = (size_t)a.n_chunks * c.K * c.C * n_pix;
+    if (a.n_chunks > 1 && need > c.shared_cap) return cudaErrorInvalidValue;  // scratch not prepared
+    a.part = a.n_chunks > 1 ? c.shared_part : out;
+    if (cudaMemsetAsync(a.part, 0, sizeof(float) * need, c.stream) != cudaSuccess) return cudaGetLastError();
+    n = (long long)n_pix * a.n_chunks;
+  }
+  a.n_items = (unsigned)n;
   const int threads = kTraceThreads;
   // a persistent grid: as many blocks as stay resident, each lane claiming items until none remain
   long long blocks = (n + threads - 1) / threads;
@@ -541,10 +658,23 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
   if (cudaMemsetAsync(a.next_item, 0, sizeof(unsigned), c.stream) != cudaSuccess) return cudaGetLastError();
   ++c.stats.launches;
   const size_t smem = trace_smem_bytes(1);
-  if (c.C == 1)
-    k_trace<1, false><<<(unsigned)blocks, threads, smem, c.stream>>>(a);
-  else
-    k_trace<3, false><<<(unsigned)blocks, threads, smem, c.stream>>>(a);
+  if (shared) {
+    if (c.C == 1)
+      k_trace<1, false, true><<<(unsigned)blocks, threads, smem, c.stream>>>(a);
+    else
+      k_trace<3, false, true><<<(unsigned)blocks, threads, smem, c.stream>>>(a);
+    if (a.n_chunks > 1) {
+      const size_t m = (size_t)c.K * c.C * n_pix;
+      const unsigned rb = (unsigned)std::min<size_t>((m + 255) / 256, 4096);
+      k_reduce_chunks<<<rb, 256, 0, c.stream>>>(a.part, a.n_chunks, m, 1.0 / (double)spp, out);
+      ++c.stats.launches;
+    }
+  } else {
+    if (c.C == 1)
+      k_trace<1, false, false><<<(unsigned)blocks, threads, smem, c.stream>>>(a);
+    else
+      k_trace<3, false, false><<<(unsigned)blocks, threads, smem, c.stream>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -554,7 +684,7 @@ cudaError_t launch_trace_batch(cudaStream_t s, int C, const ObjTrace *d_objs, in
                                unsigned long long *counts, unsigned *next_item, const uint32_t *iter_dev,
                                uint32_t iter, int grid_limit) {
   TraceArgs a;
-  std::memset(&a.one, 0, sizeof(a.one));
+  std::memset(&a, 0, sizeof(a));
   a.objs = d_objs;
   a.n_obj = n_obj;
   a.n_items = n_items;
@@ -572,9 +702,9 @@ cudaError_t launch_trace_batch(cudaStream_t s, int C, const ObjTrace *d_objs, in
   if (cudaMemsetAsync(next_item, 0, sizeof(unsigned), s) != cudaSuccess) return cudaGetLastError();
   const size_t smem = trace_smem_bytes(n_obj);
   if (C == 1)
-    k_trace<1, true><<<(unsigned)blocks, threads, smem, s>>>(a);
+    k_trace<1, true, false><<<(unsigned)blocks, threads, smem, s>>>(a);
   else
-    k_trace<3, true><<<(unsigned)blocks, threads, smem, s>>>(a);
+    k_trace<3, true, false><<<(unsigned)blocks, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -632,11 +762,11 @@ int trace_grid_limit(int C, int n_obj) {
   const size_t smem = trace_smem_bytes(n_obj > 0 ? n_obj : 1);
   cudaError_t e;
   if (n_obj > 0)
-    e = C == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<1, true>, kTraceThreads, smem)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<3, true>, kTraceThreads, smem);
+    e = C == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<1, true, false>, kTraceThreads, smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<3, true, false>, kTraceThreads, smem);
   else
-    e = C == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<1, false>, kTraceThreads, smem)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<3, false>, kTraceThreads, smem);
+    e = C == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<1, false, false>, kTraceThreads, smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<3, false, false>, kTraceThreads, smem);
   if (e != cudaSuccess) return 0;
   return per * sms;
 }

@@ -43,7 +43,7 @@ class irtps_options(ctypes.Structure):
     _fields_ = [("shadow_rays", ctypes.c_int), ("tau_lo", ctypes.c_float), ("tau_hi", ctypes.c_float),
                 ("cond_max", ctypes.c_double), ("nz_min", ctypes.c_float), ("cg_tol", ctypes.c_double),
                 ("cg_max_iter", ctypes.c_int), ("cg_check_every", ctypes.c_int), ("stop_tol", ctypes.c_double),
-                ("precond", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("use_graph", ctypes.c_int), ("sampling", ctypes.c_int)]
 
 
 class irtps_stats(ctypes.Structure):
@@ -194,10 +194,13 @@ def irtps_integrate(h):
     _check(h, _lib.irtps_integrate(h))
 
 
-def irtps_trace_pixels(h, pixels, K, C, spp, bounces, seed, iteration, stream_tag=0, records=False):
+def irtps_trace_pixels(h, pixels, K, C, spp, bounces, seed, iteration, stream_tag=0, records=False,
+                       shared=False):
+    """`shared`: the context uses light-shared sampling (records (n_pix, spp, bounces, 1 + K))."""
     pix = _host(pixels, np.int32)
     out = np.zeros((K, C, pix.size), np.float32)
-    rec = np.zeros((pix.size, K, spp, bounces, 2), np.int32) if records else None
+    shape = (pix.size, spp, bounces, 1 + K) if shared else (pix.size, K, spp, bounces, 2)
+    rec = np.zeros(shape, np.int32) if records else None
     _check(h, _lib.irtps_trace_pixels(h, _addr(pix), pix.size, spp, bounces, seed, iteration & 0xFFFFFFFF,
                                       stream_tag, _addr(out), _addr(rec)))
     return out, rec
@@ -395,6 +398,7 @@ class Context:
         lights = np.asarray(lights, np.float32).reshape(-1, 3)
         env = np.asarray(env, np.float32)
         self.H, self.W, self.K, self.C = H, W, lights.shape[0], env.shape[0]
+        self.shared = bool(opt is not None and opt.sampling == 1)
         self.h = irtps_create(H, W, self.K, self.C, lights, env, opt)
 
     def close(self):
@@ -434,7 +438,7 @@ class Context:
 
     def trace_pixels(self, pixels, spp, bounces, seed, iteration, stream_tag=0, records=False):
         return irtps_trace_pixels(self.h, pixels, self.K, self.C, spp, bounces, seed, iteration, stream_tag,
-                                  records)
+                                  records, self.shared)
 
     def set_state(self, depth=None, normals=None, albedo=None):
         irtps_set_state(self.h, depth, normals, albedo)

@@ -39,13 +39,30 @@ def test_default_options(binding):
     o = binding.irtps_default_options()
     assert o.shadow_rays == 1 and abs(o.tau_lo - 0.02) < 1e-8 and abs(o.tau_hi - 0.98) < 1e-7
     assert o.cond_max == 1e8 and abs(o.nz_min - 0.05) < 1e-8 and o.cg_tol == 1e-9
-    assert o.stop_tol == 0.0 and o.precond == 1
+    assert o.stop_tol == 0.0 and o.precond == 1 and o.use_graph == 0 and o.sampling == 0
 
 
-def test_struct_layouts_match_header(binding):
-    # sizes of the option / stats structs as the C compiler lays them out
-    assert ctypes.sizeof(binding.irtps_options) == 64
-    assert ctypes.sizeof(binding.irtps_stats) == 8 * 3 + 8 + 8 * 3 + 8 + 8 * 2 + 8 * 3 + 8 + 8
+def test_struct_layouts_match_header(binding, tmp_path):
+    """Field offsets and sizes of the binding's structs equal those the C compiler gives the header's."""
+    import subprocess
+    structs = {"irtps_options": binding.irtps_options, "irtps_stats": binding.irtps_stats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "irtps.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
 
 
 @pytest.mark.parametrize("args,needle", [
