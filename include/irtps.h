@@ -99,7 +99,7 @@ typedef struct irtps_stats {
 /* Defaults listed beside each field of irtps_options. */
 void irtps_default_options(irtps_options *opt);
 
-/* Create a context for an H x W object (H, W >= 2; H*W*K*C < 2^31), K lights
+/* Create a context for an H x W object (H, W >= 2; H*W*K < 2^31), K lights
  * (3 <= K <= 64, at least three non-coplanar: Eq. 4 needs (L^T L)^-1), C in {1, 3},
  * environment EH x EW (>= 1).  lights, env: host pointers, copied.  opt may be
  * NULL (defaults).  (L^T L)^-1 L^T is formed on the host in FP64 (Eq. 4). */

@@ -122,7 +122,7 @@ int upload_trace(irtps_batch &b, const int *spp, const int *bounces, uint64_t se
   });
   std::vector<irtps::ObjTrace> h(b.n);
   unsigned begin = 0;
-  unsigned long long primary = 0;
+  unsigned long long primary = 0, items = 0;
   for (int r = 0; r < b.n; ++r) {
     const int i = order[r];
     Ctx &c = b.objs[i]->c;
@@ -136,8 +136,12 @@ int upload_trace(irtps_batch &b, const int *spp, const int *bounces, uint64_t se
     o.item_begin = begin;
     o.iter0 = c.t;
     begin += (unsigned)(c.H * c.W) * (unsigned)c.K;
+    items += (unsigned long long)c.H * c.W * c.K;
     primary += (unsigned long long)c.H * c.W * c.K * spp[i];
   }
+  // claims run past the last item by at most one per lane: keep the counter far from wrapping
+  if (items > (1ull << 32) - (1ull << 24))
+    return bfail(b, IRTPS_EINVAL, "batch: too many work items (objects x lights x pixels >= 2^32 - 2^24)");
   b.n_items = begin;
   b.primary_per_iter = primary;
   BCK(cudaMemcpyAsync(b.d_trace, h.data(), sizeof(irtps::ObjTrace) * b.n, cudaMemcpyHostToDevice, b.stream),

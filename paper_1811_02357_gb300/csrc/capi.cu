@@ -285,8 +285,8 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
   if (H < 2 || W < 2 || K < 3 || K > irtps::kMaxLights || (C != 1 && C != 3) || EH < 1 || EW < 1 || !lights ||
       !env)
     return bail(fail(c, IRTPS_EINVAL, "create: need H, W >= 2, 3 <= K <= 64, C in {1,3}, EH, EW >= 1, lights, env"));
-  if ((long long)H * W * K * C >= (1LL << 31) || (long long)(W - 1) * (H - 1) * 2 >= (1LL << 31))
-    return bail(fail(c, IRTPS_EINVAL, "create: H*W*K*C must stay below 2^31"));
+  if ((long long)H * W * K >= (1LL << 31) || (long long)(W - 1) * (H - 1) * 2 >= (1LL << 31))
+    return bail(fail(c, IRTPS_EINVAL, "create: H*W*K must stay below 2^31"));
   c.H = H;
   c.W = W;
   c.K = K;

@@ -28,6 +28,11 @@ which are not available):
                  degrees); images stored in FP16.
   * `mixed`:     any size: bumps, bowls and grooves mixed at random (for ragged
                  and odd-sized test cases).
+  * `bumps_4096`: 4096x4096 RGB, 1000 Gaussian bumps/dents (amplitude
+                 U(-0.05, 0.05), sigma U(0.005, 0.03)) and 16 deep bowls (opening
+                 radius U(0.03, 0.1), depth half the radius), 16-cell RGB Voronoi
+                 albedo U(0.4, 0.9), 128x256 RGB cosine environment, K = 64 lights
+                 on the jittered ring of `bumps_2048`.
   * `batch_objects`: the batched pattern: 64 objects of side
                  round(exp U(ln 96, ln 1024)) (square), K in {4, 8, 16, 32},
                  spp in {64, 128, 256}, bounces in {1, 2}, each a random mix of
@@ -237,6 +242,47 @@ def bumps_2048(seed=3, H=2048, W=2048, K=32, n_bumps=200, n_bowls=4):
     el = np.radians(45.0 + rng.uniform(-10.0, 10.0, K))
     lights = np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], axis=1)
     return _finish(Hf, Hx, Hy, albedo, lights, env, f"bumps_{H}x{W}")
+
+
+def _add_windowed_bowl(Hf, Hx, Hy, h, cx, cy, radius, depth):
+    """Add a bowl evaluated on its bounding box only (it is zero outside its opening)."""
+    H, W = Hf.shape
+    j0, j1 = max(0, int((cx - radius) / h - 1)), min(W, int((cx + radius) / h + 2))
+    i0, i1 = max(0, int((cy - radius) / h - 1)), min(H, int((cy + radius) / h + 2))
+    if j0 >= j1 or i0 >= i1:
+        return
+    X, Y = np.meshgrid((np.arange(j0, j1) + 0.5) * h, (np.arange(i0, i1) + 0.5) * h)
+    e, ex, ey = bowl_field(X, Y, cx, cy, radius, depth)
+    Hf[i0:i1, j0:j1] += e
+    Hx[i0:i1, j0:j1] += ex
+    Hy[i0:i1, j0:j1] += ey
+
+
+def _jittered_ring(rng, K):
+    az = 2.0 * np.pi * (np.arange(K) + rng.uniform(-0.25, 0.25, K)) / K
+    el = np.radians(45.0 + rng.uniform(-10.0, 10.0, K))
+    return np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], axis=1)
+
+
+def bumps_4096(seed=5, H=4096, W=4096, K=64, n_bumps=1000, n_bowls=16):
+    """Many small bumps and deep bowls at 4096x4096, 128x256 environment, K = 64 lights."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / W
+    ymax = H / W
+    Hf = np.zeros((H, W))
+    Hx = np.zeros((H, W))
+    Hy = np.zeros((H, W))
+    for _ in range(n_bumps):
+        _add_windowed_gauss(Hf, Hx, Hy, h, rng.uniform(0, 1), rng.uniform(0, ymax), rng.uniform(-0.05, 0.05),
+                            rng.uniform(0.005, 0.03))
+    for _ in range(n_bowls):
+        r = rng.uniform(0.03, 0.1)
+        _add_windowed_bowl(Hf, Hx, Hy, h, rng.uniform(0.1, 0.9), rng.uniform(0.1, 0.9) * ymax, r, 0.5 * r)
+    X, Y = grid(H, W)
+    albedo = _voronoi_lowmem(X, Y, rng, 16, 3, 0.4, 0.9)
+    del X, Y
+    env = cosine_env(rng, 3, 128, 256)
+    return _finish(Hf, Hx, Hy, albedo, _jittered_ring(rng, K), env, f"bumps_{H}x{W}")
 
 
 def mixed(seed, H, W, K=6, C=3, n_bumps=6, n_bowls=2, groove=True, EH=16, EW=32):
