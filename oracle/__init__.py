@@ -415,6 +415,64 @@ def poisson_solve(normals, h, nz_min=NZ_MIN):
     return idctn(X, type=2, norm="ortho")
 
 
+def edge_slope_residuals(depth, normals, h, nz_min=NZ_MIN):
+    """Slope residual of every grid edge: u = (H_b - H_a) / h - (s_a + s_b) / 2 with s the
+    slope p along rows (edges (i, j)-(i, j+1), shape (H, W-1)) and q along columns (shape (H-1, W))."""
+    d = np.asarray(depth, np.float64)
+    p, q = gradients(normals, nz_min)
+    uh = (d[:, 1:] - d[:, :-1]) / h - (p[:, :-1] + p[:, 1:]) / 2.0
+    uv = (d[1:, :] - d[:-1, :]) / h - (q[:-1, :] + q[1:, :]) / 2.0
+    return uh, uv
+
+
+def huber_weights(u, delta):
+    """IRLS weight of the Huber M-estimator: 1 where |u| <= delta, delta / |u| beyond."""
+    a = np.abs(np.asarray(u, np.float64))
+    return np.where(a <= delta, 1.0, delta / np.maximum(a, 1e-300))
+
+
+def weighted_poisson_solve(normals, h, wh, wv, nz_min=NZ_MIN):
+    """Depth minimising sum wh (H_{i,j+1} - H_ij - gh)^2 + sum wv (H_{i+1,j} - H_ij - gv)^2,
+    mean(H) = 0, with the trapezoidal targets of poisson_rhs; wh (H, W-1), wv (H-1, W) > 0.
+    Sparse normal equations, solved directly with node 0 held at 0, then centred."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.linalg import spsolve
+    p, q = gradients(normals, nz_min)
+    H, W = p.shape
+    idx = np.arange(H * W).reshape(H, W)
+    wh = np.asarray(wh, np.float64)
+    wv = np.asarray(wv, np.float64)
+    gh = h * (p[:, :-1] + p[:, 1:]) / 2.0
+    gv = h * (q[:-1, :] + q[1:, :]) / 2.0
+    a = np.concatenate([idx[:, :-1].ravel(), idx[:-1, :].ravel()])  # edge tails
+    b = np.concatenate([idx[:, 1:].ravel(), idx[1:, :].ravel()])    # edge heads
+    w = np.concatenate([wh.ravel(), wv.ravel()])
+    g = np.concatenate([gh.ravel(), gv.ravel()])
+    rows = np.concatenate([a, b, a, b])
+    cols = np.concatenate([a, b, b, a])
+    vals = np.concatenate([w, w, -w, -w])
+    L = coo_matrix((vals, (rows, cols)), shape=(H * W, H * W)).tocsr()
+    rhs = np.zeros(H * W)
+    np.add.at(rhs, b, w * g)
+    np.add.at(rhs, a, -w * g)
+    x = np.zeros(H * W)
+    x[1:] = spsolve(L[1:, 1:].tocsc(), rhs[1:])
+    x -= x.mean()
+    return x.reshape(H, W)
+
+
+def irls_solve(normals, h, delta, iters, nz_min=NZ_MIN):
+    """Integration by the Huber M-estimator (the robust estimator the paper names for this
+    step), by iteratively reweighted least squares: H^0 is the least-squares surface;
+    H^i solves the weighted problem with the Huber weights of the slope residuals of
+    H^(i-1) (threshold `delta` in slope units)."""
+    d = poisson_solve(normals, h, nz_min)
+    for _ in range(iters):
+        uh, uv = edge_slope_residuals(d, normals, h, nz_min)
+        d = weighted_poisson_solve(normals, h, huber_weights(uh, delta), huber_weights(uv, delta), nz_min)
+    return d
+
+
 def diff_norm(h_new, h_old):
     """D_H: max |H_{t+1} - H_t| over the depth range of H_{t+1}, and the RMS difference."""
     a = np.asarray(h_new, np.float64)
