@@ -75,6 +75,9 @@ typedef struct irtps_options {
                          1 light-shared: spp paths per pixel serve all K lights (counter light
                            field 0; at each hit one shadow ray per light facing the hit normal);
                            the same expectation with about K times fewer path segments */
+  int irls_iters;     /* integration by the Huber M-estimator: reweighting steps after the
+                         least-squares solve (0 = least squares only) (0) */
+  float irls_delta;   /* Huber threshold on the edge slope residual (H_b - H_a)/h - mean slope (0.05) */
 } irtps_options;
 
 /* Counters of the last irtps_iterate / irtps_trace / irtps_integrate call. */
@@ -226,7 +229,8 @@ int irtps_autotune(irtps_ctx *ctx, int spp_probe, int bounces, uint64_t seed, do
  * per-item cost first), one PS launch, one cooperative depth-solve launch in
  * which each object's solve runs on its own team of blocks, and one D_H launch.
  * Objects may differ in H, W, K, spp, bounces and options; all must have the
- * same C and image dtype and per-light sampling (sampling = 0).  Every object's results are bit-identical to its own
+ * same C and image dtype, per-light sampling (sampling = 0) and least-squares
+ * integration (irls_iters = 0).  Every object's results are bit-identical to its own
  * irtps_iterate in the trace and the normal solve; the depth solve differs from
  * it only by the summation order of its reductions (team size), within cg_tol.
  *

@@ -495,19 +495,25 @@ def ps_step(A0, rho_t, lbar, lights, tau_lo=TAU_LO, tau_hi=TAU_HI, cond_max=COND
 
 
 def irtps_run(A0, lights, env, n_iter, spp, bounces, seed, *, shadow_rays=True, fp32=True, threads=0,
-              tau_lo=TAU_LO, tau_hi=TAU_HI, obj=0, shared=False):
+              tau_lo=TAU_LO, tau_hi=TAU_HI, obj=0, shared=False, irls_iters=0, irls_delta=0.05):
     """The IRT-PS loop: iteration 0 is classic PS + integration; each further
     iteration traces Lbar on the current estimate (iteration index t), subtracts
     rho_t * Lbar_t from the ORIGINAL images, re-solves PS and re-integrates.
     `obj` is the object index in the Philox key {seed_lo ^ obj, seed_hi}; `shared`
-    selects light-shared sampling for the trace.
+    selects light-shared sampling for the trace; irls_iters > 0 integrates with the
+    Huber M-estimator (irls_solve) instead of plain least squares.
     Returns a list of per-iteration dicts (depth, normals, albedo, lbar, dH)."""
     A0 = np.asarray(A0, np.float32)
     K, C, H, W = A0.shape
     h = 1.0 / W
     zero = np.zeros((K, C, H * W))
+    def integrate(nn):
+        if irls_iters > 0:
+            return irls_solve(nn.reshape(H, W, 3), h, irls_delta, irls_iters)
+        return poisson_solve(nn.reshape(H, W, 3), h)
+
     n, rho, ok = ps_step(A0, np.zeros((C, H * W)), zero, lights, tau_lo, tau_hi)
-    depth = poisson_solve(n.reshape(H, W, 3), h)
+    depth = integrate(n)
     hist = [dict(depth=depth, normals=n.reshape(H, W, 3), albedo=rho.reshape(C, H, W), ok=ok,
                  lbar=None, dH=None, counts=(0, 0))]
     for t in range(n_iter):
@@ -517,7 +523,7 @@ def irtps_run(A0, lights, env, n_iter, spp, bounces, seed, *, shadow_rays=True, 
                                 obj=obj, shadow_rays=shadow_rays, fp32=fp32, threads=threads, shared=shared)
         n, rho, ok = ps_step(A0, st["albedo"].astype(np.float32).reshape(C, -1), lbar, lights, tau_lo,
                              tau_hi)
-        depth = poisson_solve(n.reshape(H, W, 3), h)
+        depth = integrate(n)
         hist.append(dict(depth=depth, normals=n.reshape(H, W, 3), albedo=rho.reshape(C, H, W), ok=ok,
                          lbar=lbar.reshape(K, C, H, W), dH=diff_norm(depth, st["depth"]), counts=counts))
     return hist

@@ -338,7 +338,8 @@ int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int
   b.C = objs[0]->c.C;
   b.use_graph = use_graph ? 1 : 0;
   for (int i = 0; i < n_obj; ++i)
-    if (objs[i]->c.C != b.C || objs[i]->c.opt.sampling != 0) return bail(IRTPS_EINVAL);
+    if (objs[i]->c.C != b.C || objs[i]->c.opt.sampling != 0 || objs[i]->c.opt.irls_iters != 0)
+      return bail(IRTPS_EINVAL);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&b.sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                cudaSuccess)

@@ -45,7 +45,7 @@ int dalloc(Ctx &c, T **p, size_t n, const char *what) {
 void release(Ctx &c) {
   void *bufs[] = {c.env, c.d_lights, c.shared_part, c.images, c.lbar, c.depth, c.depth_prev, c.nrm, c.albedo, c.valid, c.pmin, c.pmax,
                   c.cg_x, c.cg_b, c.cg_r, c.cg_z, c.cg_p, c.cg_ap, c.part, c.dstats, c.next_item, c.cg_ctl,
-                  c.mg_x0, c.mg_x1, c.mg_b, c.mg_wh, c.mg_wv, c.iter_dev};
+                  c.mg_x0, c.mg_x1, c.mg_b, c.mg_wh, c.mg_wv, c.mg_wh_unit, c.mg_wv_unit, c.iter_dev};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (c.h_part) cudaFreeHost(c.h_part);
@@ -268,6 +268,8 @@ void irtps_default_options(irtps_options *opt) {
   opt->precond = 1;
   opt->use_graph = 0;
   opt->sampling = 0;
+  opt->irls_iters = 0;
+  opt->irls_delta = 0.05f;
 }
 
 int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *lights, const float *env, int EH,
@@ -301,6 +303,8 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
     return bail(fail(c, IRTPS_EINVAL, "create: precond must be 0 (Jacobi) or 1 (multigrid)"));
   if (c.opt.sampling != 0 && c.opt.sampling != 1)
     return bail(fail(c, IRTPS_EINVAL, "create: sampling must be 0 (per light) or 1 (light-shared)"));
+  if (c.opt.irls_iters < 0 || c.opt.irls_iters > 100 || !(c.opt.irls_delta > 0.0f))
+    return bail(fail(c, IRTPS_EINVAL, "create: irls_iters in 0..100 and irls_delta > 0"));
   c.eps = (float)1e-3 / (float)W;  // same expression as the oracle's lift
   // lights and pinv(L) = (L^T L)^-1 L^T in FP64 (Eq. 4)
   c.h_lights.assign(lights, lights + 3 * K);
@@ -381,12 +385,20 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
     irtps::mg_layout(H, W, &c.mg_levels, c.mg_h, c.mg_w, c.mg_off, &total);
     std::vector<float> wh((size_t)total), wv((size_t)total);
     irtps::mg_weights(c.mg_levels, c.mg_h, c.mg_w, c.mg_off, wh.data(), wv.data());
+    c.mg_total = total;
     if ((rc = dalloc(c, &c.mg_x0, (size_t)total, "multigrid")) || (rc = dalloc(c, &c.mg_x1, (size_t)total, "multigrid")) ||
         (rc = dalloc(c, &c.mg_b, (size_t)total, "multigrid")) || (rc = dalloc(c, &c.mg_wh, (size_t)total, "multigrid")) ||
         (rc = dalloc(c, &c.mg_wv, (size_t)total, "multigrid")))
       return bail(rc);
     e = cudaMemcpy(c.mg_wh, wh.data(), sizeof(float) * total, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c.mg_wv, wv.data(), sizeof(float) * total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && c.opt.irls_iters > 0) {  // a pristine copy to restore after the weighted solves
+      if ((rc = dalloc(c, &c.mg_wh_unit, (size_t)total, "multigrid")) ||
+          (rc = dalloc(c, &c.mg_wv_unit, (size_t)total, "multigrid")))
+        return bail(rc);
+      e = cudaMemcpy(c.mg_wh_unit, wh.data(), sizeof(float) * total, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(c.mg_wv_unit, wv.data(), sizeof(float) * total, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "create: multigrid weights"));
   }
   e = cudaMallocHost((void **)&c.h_part, sizeof(double) * c.part_stride);

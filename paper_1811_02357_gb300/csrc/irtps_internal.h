@@ -109,6 +109,8 @@ struct Ctx {
   int mg_levels = 0;
   int mg_h[kMaxLevels] = {0}, mg_w[kMaxLevels] = {0}, mg_off[kMaxLevels] = {0};
   float *mg_x0 = nullptr, *mg_x1 = nullptr, *mg_b = nullptr, *mg_wh = nullptr, *mg_wv = nullptr;
+  float *mg_wh_unit = nullptr, *mg_wv_unit = nullptr;  // unit-weight hierarchy (restored after IRLS)
+  int mg_total = 0;               // points of all levels
   DevStats *dstats = nullptr;     // device counters of the current call
   unsigned *next_item = nullptr;  // work-item counter of the trace launch
   uint32_t *iter_dev = nullptr;   // IRT iteration index read by replayed graphs

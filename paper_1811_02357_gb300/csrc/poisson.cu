@@ -89,6 +89,29 @@ __device__ __forceinline__ int degree(int i, int j, int H, int W) {
   return (j > 0) + (j < W - 1) + (i > 0) + (i < H - 1);
 }
 
+// The weighted graph Laplacian (IRLS solves): sum over the edges of p of
+// w_e (v_p - v_neighbour); wh[p] weighs edge p - p+1, wv[p] edge p - p+W.
+template <typename T>
+__device__ __forceinline__ T lap_weighted(const T *v, const float *wh, const float *wv, int i, int j, int H, int W) {
+  const size_t p = (size_t)i * W + j;
+  const T c = v[p];
+  T s = 0, d = 0;
+  if (j > 0) { const T w = (T)wh[p - 1]; s = fma(w, v[p - 1], s); d += w; }
+  if (j < W - 1) { const T w = (T)wh[p]; s = fma(w, v[p + 1], s); d += w; }
+  if (i > 0) { const T w = (T)wv[p - W]; s = fma(w, v[p - W], s); d += w; }
+  if (i < H - 1) { const T w = (T)wv[p]; s = fma(w, v[p + W], s); d += w; }
+  return d * c - s;
+}
+
+__device__ __forceinline__ float weighted_degree(const float *wh, const float *wv, int p, int i, int j, int H, int W) {
+  float d = 0.0f;
+  if (j > 0) d += wh[p - 1];
+  if (j < W - 1) d += wh[p];
+  if (i > 0) d += wv[p - W];
+  if (i < H - 1) d += wv[p];
+  return d;
+}
+
 // The blocks that work on one solve: all of a plain launch, or the range of a
 // batched launch that belongs to one object (bid = block index within it).
 struct Team {
@@ -106,6 +129,7 @@ struct CG {
   float *r, *z, *p, *ap;  // p: two buffers of P; ap: A p, then the FP32 correction
   double *part;
   int stride, nblk;
+  const float *wh, *wv;   // edge weights of the weighted (IRLS) solves, level 0 of the multigrid pool
 };
 
 __device__ __forceinline__ void slopes(const float4 *nrm, size_t p, float nz_min, double &sp, double &sq) {
@@ -115,19 +139,21 @@ __device__ __forceinline__ void slopes(const float4 *nrm, size_t p, float nz_min
   sq = -(double)n.y / nz;
 }
 
-// b = D^T g (FP64) and |b|^2 partials.
+// b = D^T g (FP64; weighted: D^T W g) and |b|^2 partials.
+template <bool WEIGHTED>
 __device__ __forceinline__ void rhs_body(const CG &g, Team t) {
   __shared__ double sh[33];
   double bb = 0.0;
+  auto wt = [&](const float *w, int e, double x) -> double { return WEIGHTED ? (double)w[e] * x : x; };
   for (int p = t.bid * blockDim.x + threadIdx.x; p < g.P; p += t.nblk * blockDim.x) {
     const int i = p / g.W, j = p - i * g.W;
     double pc, qc, pn, qn;
     slopes(g.nrm, p, g.nz_min, pc, qc);
     double v = 0.0;
-    if (j > 0) { slopes(g.nrm, p - 1, g.nz_min, pn, qn); v += g.h * (pn + pc) * 0.5; }
-    if (j < g.W - 1) { slopes(g.nrm, p + 1, g.nz_min, pn, qn); v -= g.h * (pc + pn) * 0.5; }
-    if (i > 0) { slopes(g.nrm, p - g.W, g.nz_min, pn, qn); v += g.h * (qn + qc) * 0.5; }
-    if (i < g.H - 1) { slopes(g.nrm, p + g.W, g.nz_min, pn, qn); v -= g.h * (qc + qn) * 0.5; }
+    if (j > 0) { slopes(g.nrm, p - 1, g.nz_min, pn, qn); v += wt(g.wh, p - 1, g.h * (pn + pc) * 0.5); }
+    if (j < g.W - 1) { slopes(g.nrm, p + 1, g.nz_min, pn, qn); v -= wt(g.wh, p, g.h * (pc + pn) * 0.5); }
+    if (i > 0) { slopes(g.nrm, p - g.W, g.nz_min, pn, qn); v += wt(g.wv, p - g.W, g.h * (qn + qc) * 0.5); }
+    if (i < g.H - 1) { slopes(g.nrm, p + g.W, g.nz_min, pn, qn); v -= wt(g.wv, p, g.h * (qc + qn) * 0.5); }
     g.b[p] = v;
     bb += v * v;
   }
@@ -140,14 +166,17 @@ __device__ __forceinline__ void load_x_body(const CG &g, Team t) {
 }
 
 // True residual r = b - A x in FP64 (stored FP32), z = r / deg, partials of r.z and |r|^2 (FP64).
+template <bool WEIGHTED>
 __device__ __forceinline__ void residual_body(const CG &g, int rz_slot, Team t) {
   __shared__ double sh[33];
   double rz = 0.0, rr = 0.0;
   for (int p = t.bid * blockDim.x + threadIdx.x; p < g.P; p += t.nblk * blockDim.x) {
     const int i = p / g.W, j = p - i * g.W;
-    const double res = g.b[p] - lap_at<double>(g.x, i, j, g.H, g.W);
+    const double ax = WEIGHTED ? lap_weighted<double>(g.x, g.wh, g.wv, i, j, g.H, g.W)
+                               : lap_at<double>(g.x, i, j, g.H, g.W);
+    const double res = g.b[p] - ax;
     const float rf = (float)res;
-    const float zf = rf / (float)degree(i, j, g.H, g.W);
+    const float zf = rf / (WEIGHTED ? weighted_degree(g.wh, g.wv, p, i, j, g.H, g.W) : (float)degree(i, j, g.H, g.W));
     g.r[p] = rf;
     g.z[p] = zf;
     rz += (double)rf * (double)zf;
@@ -436,7 +465,7 @@ __device__ void mg_vcycle(const MG &m, const float *r, CGCtl *ctl, Team t) {
 // against tol (iterative refinement).  Dot products are FP32 within a block and
 // FP64 across blocks; every block sums the same partials in the same order and
 // so takes the same decisions.
-template <int PRE>
+template <int PRE, bool WEIGHTED>
 __device__ __forceinline__ void cg_loop_body(const CG &g, CGCtl *ctl, CGAcc *acc, double tol, int max_iter, int check,
                                              const MG &mg, Team t) {
   __shared__ double sh[33];
@@ -464,7 +493,8 @@ __device__ __forceinline__ void cg_loop_body(const CG &g, CGCtl *ctl, CGAcc *acc
       if (PRE == 1) {
         zf = z[q.p];
       } else {
-        zf = rf * inv_degree(q.i, q.j, g.H, g.W);
+        zf = WEIGHTED ? rf / weighted_degree(g.wh, g.wv, q.p, q.i, q.j, g.H, g.W)
+                      : rf * inv_degree(q.i, q.j, g.H, g.W);
         z[q.p] = zf;
       }
       rz = fmaf(rf, zf, rz);
@@ -502,10 +532,17 @@ __device__ __forceinline__ void cg_loop_body(const CG &g, CGCtl *ctl, CGAcc *acc
       const int p = q.p;
       const float pc = dir(p);
       float s = 0.0f, deg = 0.0f;
-      if (q.j > 0) { s += dir(p - 1); deg += 1.0f; }
-      if (q.j < g.W - 1) { s += dir(p + 1); deg += 1.0f; }
-      if (q.i > 0) { s += dir(p - g.W); deg += 1.0f; }
-      if (q.i < g.H - 1) { s += dir(p + g.W); deg += 1.0f; }
+      if (WEIGHTED) {
+        if (q.j > 0) { const float w = g.wh[p - 1]; s = fmaf(w, dir(p - 1), s); deg += w; }
+        if (q.j < g.W - 1) { const float w = g.wh[p]; s = fmaf(w, dir(p + 1), s); deg += w; }
+        if (q.i > 0) { const float w = g.wv[p - g.W]; s = fmaf(w, dir(p - g.W), s); deg += w; }
+        if (q.i < g.H - 1) { const float w = g.wv[p]; s = fmaf(w, dir(p + g.W), s); deg += w; }
+      } else {
+        if (q.j > 0) { s += dir(p - 1); deg += 1.0f; }
+        if (q.j < g.W - 1) { s += dir(p + 1); deg += 1.0f; }
+        if (q.i > 0) { s += dir(p - g.W); deg += 1.0f; }
+        if (q.i < g.H - 1) { s += dir(p + g.W); deg += 1.0f; }
+      }
       const float apv = fmaf(deg, pc, -s);
       pnew[p] = pc;
       g.ap[p] = apv;
@@ -538,7 +575,9 @@ __device__ __forceinline__ void cg_loop_body(const CG &g, CGCtl *ctl, CGAcc *acc
       if (*(volatile int *)&ctl->err) break;
       double rr = 0.0;
       for (Stride q(g.W, t); q.p < g.P; q.next(g.W)) {
-        const double res = g.b[q.p] - lap_at<double>(g.x, q.i, q.j, g.H, g.W);
+        const double ax = WEIGHTED ? lap_weighted<double>(g.x, g.wh, g.wv, q.i, q.j, g.H, g.W)
+                                   : lap_at<double>(g.x, q.i, q.j, g.H, g.W);
+        const double res = g.b[q.p] - ax;
         g.r[q.p] = (float)res;
         rr += res * res;
       }
@@ -572,10 +611,10 @@ __device__ __forceinline__ void cg_loop_body(const CG &g, CGCtl *ctl, CGAcc *acc
   }
 }
 
-template <int PRE>
+template <int PRE, bool WEIGHTED = false>
 __global__ void __launch_bounds__(kThreads) k_cg_loop(const CG g, CGCtl *ctl, CGAcc *acc, double tol, int max_iter,
                                                       int check, const MG mg) {
-  cg_loop_body<PRE>(g, ctl, acc, tol, max_iter, check, mg, whole_grid());
+  cg_loop_body<PRE, WEIGHTED>(g, ctl, acc, tol, max_iter, check, mg, whole_grid());
 }
 
 // Start of a solve: |b| and the warm start's relative residual from the partials,
@@ -640,10 +679,12 @@ __device__ __forceinline__ void depth_change_body(const CG &g, const float *old,
 }
 
 // Plain (one solve per launch) forms of the solver's kernels.
-__global__ void __launch_bounds__(kThreads) k_rhs(const CG g) { rhs_body(g, whole_grid()); }
+template <bool WEIGHTED = false>
+__global__ void __launch_bounds__(kThreads) k_rhs(const CG g) { rhs_body<WEIGHTED>(g, whole_grid()); }
 __global__ void __launch_bounds__(kThreads) k_load_x(const CG g) { load_x_body(g, whole_grid()); }
+template <bool WEIGHTED = false>
 __global__ void __launch_bounds__(kThreads) k_residual(const CG g, int rz_slot) {
-  residual_body(g, rz_slot, whole_grid());
+  residual_body<WEIGHTED>(g, rz_slot, whole_grid());
 }
 __global__ void k_cg_start(const CG g, CGCtl *ctl) { cg_start_body(g, ctl); }
 __global__ void __launch_bounds__(kThreads) k_sum_x(const CG g) { sum_x_body(g, whole_grid()); }
@@ -660,10 +701,14 @@ int cg_grid_limit() {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
-  int per1 = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_loop<0>, kThreads, 0) != cudaSuccess) return 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_cg_loop<1>, kThreads, 0) != cudaSuccess) return 1;
-  per = per < per1 ? per : per1;
+  const void *fns[] = {(const void *)k_cg_loop<0, false>, (const void *)k_cg_loop<1, false>,
+                       (const void *)k_cg_loop<0, true>, (const void *)k_cg_loop<1, true>};
+  per = 1 << 30;
+  for (const void *fn : fns) {
+    int q = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, fn, kThreads, 0) != cudaSuccess) return 1;
+    per = per < q ? per : q;
+  }
   per = per < IRTPS_CG_BLOCKS_PER_SM ? per : IRTPS_CG_BLOCKS_PER_SM;
   return per * sms > 0 ? per * sms : 1;
 }
@@ -746,6 +791,8 @@ static CG make_cg(Ctx &c) {
   g.part = c.part;
   g.stride = c.part_stride;
   g.nblk = c.cg_blocks;
+  g.wh = c.mg_wh;
+  g.wv = c.mg_wv;
   return g;
 }
 
@@ -776,16 +823,60 @@ __device__ __forceinline__ void dh_final_body(const CG &g, DevStats *ds) {
 }
 __global__ void k_dh_final(const CG g, DevStats *ds) { dh_final_body(g, ds); }
 
+// IRLS weights of the Huber M-estimator from the current iterate x: for every
+// edge the slope residual u = (x_b - x_a) / h - (s_a + s_b) / 2 (FP64) gives
+// w = 1 if |u| <= delta, else delta / |u|; written as the level-0 edge weights of
+// the multigrid pool (zero on the last column / row, as the unit weights).
+__global__ void __launch_bounds__(kThreads) k_irls_weights(const CG g, float *wh, float *wv, double delta) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
+    const int i = p / g.W, j = p - i * g.W;
+    double pc, qc, pn, qn;
+    slopes(g.nrm, p, g.nz_min, pc, qc);
+    float a = 0.0f, b = 0.0f;
+    if (j < g.W - 1) {
+      slopes(g.nrm, p + 1, g.nz_min, pn, qn);
+      const double u = fabs((g.x[p + 1] - g.x[p]) / g.h - (pc + pn) * 0.5);
+      a = u <= delta ? 1.0f : (float)(delta / u);
+    }
+    if (i < g.H - 1) {
+      slopes(g.nrm, p + g.W, g.nz_min, pn, qn);
+      const double u = fabs((g.x[p + g.W] - g.x[p]) / g.h - (qc + qn) * 0.5);
+      b = u <= delta ? 1.0f : (float)(delta / u);
+    }
+    wh[p] = a;
+    wv[p] = b;
+  }
+}
+
+// Galerkin weights of level l+1 from level l (2x2 aggregates): the sum of the fine
+// edge weights crossing between two aggregates (the host's construction, on the device).
+__global__ void __launch_bounds__(kThreads) k_mg_coarsen(const MG m, int l, float *wh, float *wv) {
+  const int Hf = m.H[l], Wf = m.W[l], Hc = m.H[l + 1], Wc = m.W[l + 1];
+  const float *fh = wh + m.off[l], *fv = wv + m.off[l];
+  float *ch = wh + m.off[l + 1], *cv = wv + m.off[l + 1];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Hc * Wc; q += gridDim.x * blockDim.x) {
+    const int I = q / Wc, J = q - I * Wc;
+    float sh = 0.0f, sv = 0.0f;
+    if (2 * J + 2 < Wf)
+      for (int i = 2 * I; i < 2 * I + 2 && i < Hf; ++i) sh += fh[i * Wf + 2 * J + 1];
+    if (2 * I + 2 < Hf)
+      for (int j = 2 * J; j < 2 * J + 2 && j < Wf; ++j) sv += fv[(2 * I + 1) * Wf + j];
+    ch[q] = sh;
+    cv[q] = sv;
+  }
+}
+
 // One depth solve, enqueued without host round trips: right-hand side, warm
 // start, residual, |b| on the device, the cooperative PCG loop, mean removal.
-cudaError_t solve_depth_async(Ctx &c) {
+template <bool WEIGHTED>
+static cudaError_t solve_once(Ctx &c) {
   const CG g = make_cg(c);
   const int nb = c.cg_blocks;
   CGCtl *ctl = (CGCtl *)c.cg_ctl;
   CGAcc *acc = &c.dstats->cg;
-  k_rhs<<<nb, kThreads, 0, c.stream>>>(g);
+  k_rhs<WEIGHTED><<<nb, kThreads, 0, c.stream>>>(g);
   k_load_x<<<nb, kThreads, 0, c.stream>>>(g);
-  k_residual<<<nb, kThreads, 0, c.stream>>>(g, S_RZ0);
+  k_residual<WEIGHTED><<<nb, kThreads, 0, c.stream>>>(g, S_RZ0);
   k_cg_start<<<1, 32, 0, c.stream>>>(g, ctl);
   LAUNCH_CHECK();
   int m = c.opt.cg_check_every > 0 ? c.opt.cg_check_every : 10;
@@ -793,7 +884,7 @@ cudaError_t solve_depth_async(Ctx &c) {
   int max_iter = c.opt.cg_max_iter;
   const MG mg = make_mg(c);
   void *args[] = {(void *)&g, (void *)&ctl, (void *)&acc, (void *)&tol, (void *)&max_iter, (void *)&m, (void *)&mg};
-  const void *fn = c.opt.precond == 1 ? (const void *)k_cg_loop<1> : (const void *)k_cg_loop<0>;
+  const void *fn = c.opt.precond == 1 ? (const void *)k_cg_loop<1, WEIGHTED> : (const void *)k_cg_loop<0, WEIGHTED>;
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(kThreads), args, 0, c.stream);
   if (e != cudaSuccess) return e;
   k_sum_x<<<nb, kThreads, 0, c.stream>>>(g);
@@ -801,6 +892,31 @@ cudaError_t solve_depth_async(Ctx &c) {
   c.stats.launches += 7;
   LAUNCH_CHECK();
   return cudaSuccess;
+}
+
+// The least-squares solve, then (option irls_iters) the Huber M-estimator by
+// IRLS: weights from the last surface, Galerkin hierarchy rebuilt, weighted solve
+// warm-started from it; the unit weights are put back at the end.
+cudaError_t solve_depth_async(Ctx &c) {
+  cudaError_t e = solve_once<false>(c);
+  if (e != cudaSuccess || c.opt.irls_iters <= 0) return e;
+  const CG g = make_cg(c);
+  const MG mg = make_mg(c);
+  const int nb = c.cg_blocks;
+  for (int it = 0; it < c.opt.irls_iters; ++it) {
+    k_irls_weights<<<nb, kThreads, 0, c.stream>>>(g, c.mg_wh, c.mg_wv, (double)c.opt.irls_delta);
+    for (int l = 0; l + 1 < mg.levels; ++l) {
+      const int n = mg.H[l + 1] * mg.W[l + 1];
+      k_mg_coarsen<<<(n + kThreads - 1) / kThreads, kThreads, 0, c.stream>>>(mg, l, c.mg_wh, c.mg_wv);
+    }
+    c.stats.launches += mg.levels;
+    LAUNCH_CHECK();
+    if ((e = solve_once<true>(c)) != cudaSuccess) return e;
+  }
+  const size_t bytes = sizeof(float) * (size_t)c.mg_total;
+  e = cudaMemcpyAsync(c.mg_wh, c.mg_wh_unit, bytes, cudaMemcpyDeviceToDevice, c.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c.mg_wv, c.mg_wv_unit, bytes, cudaMemcpyDeviceToDevice, c.stream);
+  return e;
 }
 
 int solve_depth(Ctx &c) {
@@ -858,22 +974,22 @@ __device__ __forceinline__ void for_team(const CGJob *__restrict__ jobs, int n, 
 }
 
 __global__ void __launch_bounds__(kThreads) k_rhs_b(const CGJob *jobs, int n) {
-  for_team(jobs, n, [](const CGJob &j, Team t) { rhs_body(j.g, t); });
+  for_team(jobs, n, [](const CGJob &j, Team t) { rhs_body<false>(j.g, t); });
 }
 __global__ void __launch_bounds__(kThreads) k_load_x_b(const CGJob *jobs, int n) {
   for_team(jobs, n, [](const CGJob &j, Team t) { load_x_body(j.g, t); });
 }
 __global__ void __launch_bounds__(kThreads) k_residual_b(const CGJob *jobs, int n) {
-  for_team(jobs, n, [](const CGJob &j, Team t) { residual_body(j.g, S_RZ0, t); });
+  for_team(jobs, n, [](const CGJob &j, Team t) { residual_body<false>(j.g, S_RZ0, t); });
 }
 // one warp per job
 __global__ void k_cg_start_b(const CGJob *jobs) { cg_start_body(jobs[blockIdx.x].g, jobs[blockIdx.x].ctl); }
 __global__ void __launch_bounds__(kThreads) k_cg_loop_b(const CGJob *jobs, int n) {
   for_team(jobs, n, [](const CGJob &j, Team t) {
     if (j.pre == 1)
-      cg_loop_body<1>(j.g, j.ctl, &j.ds->cg, j.tol, j.max_iter, j.check, j.mg, t);
+      cg_loop_body<1, false>(j.g, j.ctl, &j.ds->cg, j.tol, j.max_iter, j.check, j.mg, t);
     else
-      cg_loop_body<0>(j.g, j.ctl, &j.ds->cg, j.tol, j.max_iter, j.check, j.mg, t);
+      cg_loop_body<0, false>(j.g, j.ctl, &j.ds->cg, j.tol, j.max_iter, j.check, j.mg, t);
   });
 }
 __global__ void __launch_bounds__(kThreads) k_sum_x_b(const CGJob *jobs, int n) {
@@ -1020,18 +1136,20 @@ extern "C" int irtps_integrate_noalloc(const float *normals, int H, int W, float
   g.part = reinterpret_cast<double *>(base + kNaPart);
   g.stride = kNoAllocMaxBlocks;
   g.nblk = nb;
+  g.wh = g.wv = nullptr;
   CGCtl *ctl = reinterpret_cast<CGCtl *>(base + kNaCtl);
 
-  k_rhs<<<nb, kThreads, 0, s>>>(g);
+  k_rhs<false><<<nb, kThreads, 0, s>>>(g);
   k_load_x<<<nb, kThreads, 0, s>>>(g);
-  k_residual<<<nb, kThreads, 0, s>>>(g, S_RZ0);
+  k_residual<false><<<nb, kThreads, 0, s>>>(g, S_RZ0);
   k_cg_start<<<1, 32, 0, s>>>(g, ctl);  // also clears the barrier state left by the previous call
   if (cudaGetLastError() != cudaSuccess) return IRTPS_ECUDA;
   int m = 10;
   const MG none{};
   CGAcc *acc = nullptr;
   void *args[] = {(void *)&g, (void *)&ctl, (void *)&acc, (void *)&tol, (void *)&max_iter, (void *)&m, (void *)&none};
-  if (cudaLaunchCooperativeKernel((const void *)k_cg_loop<0>, dim3(nb), dim3(kThreads), args, 0, s) != cudaSuccess)
+  if (cudaLaunchCooperativeKernel((const void *)k_cg_loop<0, false>, dim3(nb), dim3(kThreads), args, 0, s) !=
+      cudaSuccess)
     return IRTPS_ECUDA;
   k_sum_x<<<nb, kThreads, 0, s>>>(g);
   k_store_depth<<<nb, kThreads, 0, s>>>(g, ctl);
