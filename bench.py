@@ -125,6 +125,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def combine_ranks(ms, units, world, device):
+    """Whole-job figures of N replica ranks: the slowest rank's time (max) and the units all ranks
+    processed (sum).  Any process group works (nccl on GPUs; gloo in the CPU tests)."""
+    if world <= 1:
+        return float(ms), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -277,14 +291,7 @@ def run_batch(args):
     tris = sum(r[1]["tri_tests"] for r in res)
     trace_ms = sum(r[1]["trace_ms"] for r in res)
     primary = sum(r[1]["primary_segments"] for r in res)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        sg = torch.tensor([float(segs)], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(sg)
-        ms_all, segs_all = float(t.item()), float(sg.item())
-    else:
-        ms_all, segs_all = ms, float(segs)
+    ms_all, segs_all = combine_ranks(ms, segs, world, dev)
     value = segs_all / (ms_all / 1e3) / 1e6
     # the same step with the iteration replayed as a CUDA graph
     batch.close()
@@ -441,14 +448,7 @@ def main():
         torch.cuda.synchronize()
     launches = ctx.stats()["launches"] - launches0
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        s = torch.tensor([float(tot["segments"])], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(s)
-        ms_all, segs_all = float(t.item()), float(s.item())
-    else:
-        ms_all, segs_all = ms, float(tot["segments"])
+    ms_all, segs_all = combine_ranks(ms, tot["segments"], world, dev)
     value = segs_all / (ms_all / 1e3) / 1e6
     P = H * W
 

@@ -195,7 +195,7 @@ struct TraceArgs {
   unsigned *next_item;         // work-item counter, zero before the launch
   const uint32_t *iter_dev;    // when set, the iteration field is read here (graph replays)
   uint32_t iter, stream;
-  // light-shared sampling: partial sums n_chunks x K x C x n_pix (the output itself for one chunk)
+  // light-shared sampling: partial sums, n_chunks x n_pix x K x C
   float *part;
   int n_chunks, chunk;
 };
@@ -205,6 +205,9 @@ struct TraceArgs {
 #endif
 #ifndef IRTPS_TRACE_MINB_BATCH
 #define IRTPS_TRACE_MINB_BATCH 6
+#endif
+#ifndef IRTPS_TRACE_MINB_SHARED
+#define IRTPS_TRACE_MINB_SHARED 8
 #endif
 #ifndef IRTPS_MARCH_KEEP
 #define IRTPS_MARCH_KEEP 2
@@ -223,7 +226,8 @@ enum : int { PH_SETUP = 0, PH_MARCH = 1, PH_RESOLVE = 2, PH_DONE = 3 };
 static size_t trace_smem_bytes(int n) { return (size_t)n * sizeof(LevelTable) + (size_t)(n + 1) * sizeof(unsigned); }
 
 template <int C, bool BATCH, bool SHARED>
-__global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH : IRTPS_TRACE_MINB)
+__global__ void __launch_bounds__(kTraceThreads,
+                                  BATCH ? IRTPS_TRACE_MINB_BATCH : (SHARED ? IRTPS_TRACE_MINB_SHARED : IRTPS_TRACE_MINB))
     k_trace(const __grid_constant__ TraceArgs a) {
   extern __shared__ __align__(16) unsigned char trace_smem[];
   LevelTable *lts = reinterpret_cast<LevelTable *>(trace_smem);
@@ -321,11 +325,12 @@ __global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH 
   auto albedo_at = [&](int c, int q) -> float {
     return __ldg(ob->albedo + (size_t)c * ob->f.H * ob->f.W + q);
   };
-  // light-shared: the direct term of light kk at the current hit, into the chunk's partial sums
+  // light-shared: the direct term of light kk at the current hit, into the item's
+  // partial sums (K x C contiguous per item, so a lane's updates stay in one or two lines)
   auto add_direct = [&](int kk) {
-    float *d = a.part + ((size_t)j * ob->K + kk) * C * ob->n_pix + ip;
+    float *d = a.part + ((size_t)j * ob->n_pix + ip) * ob->K * C + kk * C;
 #pragma unroll
-    for (int c = 0; c < C; ++c) d[(size_t)c * ob->n_pix] += thr[c] * albedo_at(c, qp) * cosv;
+    for (int c = 0; c < C; ++c) d[c] += thr[c] * albedo_at(c, qp) * cosv;
   };
   auto end_sample = [&]() {
 #pragma unroll
@@ -387,15 +392,11 @@ __global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH 
     if (need) {
       if (item_done) {
         if constexpr (SHARED) {
-          // the environment part is common to every light; one chunk: also the mean
-          float *d = a.part + (size_t)j * ob->K * C * ob->n_pix + ip;
-          const float scale = a.n_chunks == 1 ? 1.0f / (float)ob->spp : 1.0f;
+          // the environment part is common to every light
+          float *d = a.part + ((size_t)j * ob->n_pix + ip) * ob->K * C;
           for (int kk = 0; kk < ob->K; ++kk)
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-              float *v = d + ((size_t)kk * C + c) * ob->n_pix;
-              *v = (*v + sum[c]) * scale;
-            }
+            for (int c = 0; c < C; ++c) d[kk * C + c] += sum[c];
         } else {
           const float inv = 1.0f / (float)ob->spp;
 #pragma unroll
@@ -557,13 +558,16 @@ __global__ void __launch_bounds__(kTraceThreads, BATCH ? IRTPS_TRACE_MINB_BATCH 
   }
 }
 
-// Light-shared traces in several sample chunks: Lbar = (sum of the chunks' partial sums) / spp.
-__global__ void k_reduce_chunks(const float *__restrict__ part, int n_chunks, size_t n, double inv_spp,
+// Light-shared traces: Lbar(k, c, p) = (sum over the sample chunks of the partial
+// sums, n_chunks x n_pix x KC with KC = K C, in chunk order, FP64) / spp.
+__global__ void k_reduce_chunks(const float *__restrict__ part, int n_chunks, int n_pix, int kc, double inv_spp,
                                 float *__restrict__ out) {
+  const size_t n = (size_t)n_pix * kc;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     double v = 0.0;
     for (int jj = 0; jj < n_chunks; ++jj) v += (double)part[(size_t)jj * n + i];
-    out[i] = (float)(v * inv_spp);
+    const size_t ip = i / kc, e = i - ip * kc;
+    out[e * n_pix + ip] = (float)(v * inv_spp);
   }
 }
 
@@ -614,8 +618,7 @@ int shared_chunks(const Ctx &, int n_pix, int spp) {
 }
 
 size_t shared_scratch_floats(const Ctx &c, int n_pix, int spp) {
-  const int n = shared_chunks(c, n_pix, spp);
-  return n > 1 ? (size_t)n * c.K * c.C * n_pix : 0;
+  return (size_t)shared_chunks(c, n_pix, spp) * c.K * c.C * n_pix;
 }
 
 cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
@@ -645,8 +648,8 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
     a.n_chunks = shared_chunks(c, n_pix, spp);
     a.chunk = (spp + a.n_chunks - 1) / a.n_chunks;
     const size_t need = (size_t)a.n_chunks * c.K * c.C * n_pix;
-    if (a.n_chunks > 1 && need > c.shared_cap) return cudaErrorInvalidValue;  // scratch not prepared
-    a.part = a.n_chunks > 1 ? c.shared_part : out;
+    if (need > c.shared_cap) return cudaErrorInvalidValue;  // scratch not prepared
+    a.part = c.shared_part;
     if (cudaMemsetAsync(a.part, 0, sizeof(float) * need, c.stream) != cudaSuccess) return cudaGetLastError();
     n = (long long)n_pix * a.n_chunks;
   }
@@ -663,12 +666,10 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
       k_trace<1, false, true><<<(unsigned)blocks, threads, smem, c.stream>>>(a);
     else
       k_trace<3, false, true><<<(unsigned)blocks, threads, smem, c.stream>>>(a);
-    if (a.n_chunks > 1) {
-      const size_t m = (size_t)c.K * c.C * n_pix;
-      const unsigned rb = (unsigned)std::min<size_t>((m + 255) / 256, 4096);
-      k_reduce_chunks<<<rb, 256, 0, c.stream>>>(a.part, a.n_chunks, m, 1.0 / (double)spp, out);
-      ++c.stats.launches;
-    }
+    const size_t m = (size_t)c.K * c.C * n_pix;
+    const unsigned rb = (unsigned)std::min<size_t>((m + 255) / 256, 8192);
+    k_reduce_chunks<<<rb, 256, 0, c.stream>>>(a.part, a.n_chunks, n_pix, c.K * c.C, 1.0 / (double)spp, out);
+    ++c.stats.launches;
   } else {
     if (c.C == 1)
       k_trace<1, false, false><<<(unsigned)blocks, threads, smem, c.stream>>>(a);
