@@ -224,8 +224,10 @@ def run_batch(args):
     stream = torch.cuda.Stream(device=dev)
     img_dtype = irtps.IRTPS_F16 if args.images == "f16" else irtps.IRTPS_F32
     ctxs, imgs = [], []
+    opt = irtps.irtps_default_options()
+    opt.sampling = 1 if args.sampling == "shared" else 0
     for i, (sc, _, _) in enumerate(objs):
-        c = irtps.Context(sc.H, sc.W, sc.lights, sc.env)
+        c = irtps.Context(sc.H, sc.W, sc.lights, sc.env, opt)
         c.set_stream(stream.cuda_stream)
         c.set_state(sc.depth, sc.normals, sc.albedo)
         A = torch.empty((sc.K, sc.C, sc.H, sc.W), dtype=torch.float32, device=dev)
@@ -336,7 +338,8 @@ def run_batch(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "objects": len(objs), "pixels": P,
                        "sides": [sc.H for sc, _, _ in objs], "K": [sc.K for sc, _, _ in objs], "spp": spp,
-                       "bounces": bnc, "images": args.images, "irt_iterations_per_step": n_iter,
+                       "bounces": bnc, "images": args.images, "sampling": args.sampling,
+                       "irt_iterations_per_step": n_iter,
                        "trace_blocks_per_sm": bps, "mip_cut": cut, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (images of all objects)"},
             "pixel_iters_per_s": P * n_iter * world * args.steps / (ms_all / 1e3),

@@ -19,6 +19,7 @@ constexpr int kMaxBatch = 64;
 struct irtps_batch {
   std::vector<irtps_ctx *> objs;
   int n = 0, C = 0;
+  bool shared = false;  // light-shared sampling (every object's option)
   int use_graph = 0;
   cudaStream_t stream = nullptr;      // where the batch's work runs
   cudaStream_t own_stream = nullptr;
@@ -30,6 +31,8 @@ struct irtps_batch {
   void *d_ps0 = nullptr;   // PS descriptors of iteration 0 (classic PS: Lbar taken as 0)
   void *d_jobs = nullptr;  // depth-solve jobs
   irtps::PyrObj *d_pyr = nullptr;
+  irtps::ReduceObj *d_reduce = nullptr;  // light-shared: partial-sum buffers of the objects
+  int reduce_blocks = 0;
   irtps::DevStats *d_stats = nullptr;  // per object (solver, D_H); [n]: trace counters
   unsigned *next_item = nullptr;
   uint32_t *iter_dev = nullptr;
@@ -74,7 +77,7 @@ int bcuda(irtps_batch &b, cudaError_t e, const char *what) {
   } while (0)
 
 void release(irtps_batch &b) {
-  void *bufs[] = {b.d_trace, b.d_ps, b.d_ps0, b.d_jobs, b.d_pyr, b.d_stats, b.next_item, b.iter_dev};
+  void *bufs[] = {b.d_trace, b.d_ps, b.d_ps0, b.d_jobs, b.d_pyr, b.d_reduce, b.d_stats, b.next_item, b.iter_dev};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (b.graph) cudaGraphExecDestroy(b.graph);
@@ -117,15 +120,23 @@ int trace_grid(const irtps_batch &b) { return b.trace_per_sm * b.sms; }
 int upload_trace(irtps_batch &b, const int *spp, const int *bounces, uint64_t seed) {
   std::vector<int> order(b.n);
   for (int i = 0; i < b.n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    return (long long)spp[x] * bounces[x] > (long long)spp[y] * bounces[y];
-  });
+  auto cost = [&](int i) -> long long {  // samples x bounces of one work item (x K when shared)
+    const Ctx &c = b.objs[i]->c;
+    if (!b.shared) return (long long)spp[i] * bounces[i];
+    const int nc = irtps::shared_chunks(c.H * c.W, spp[i]);
+    return (long long)((spp[i] + nc - 1) / nc) * bounces[i] * c.K;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
   std::vector<irtps::ObjTrace> h(b.n);
+  std::vector<irtps::ReduceObj> red(b.shared ? b.n : 0);
   unsigned begin = 0;
   unsigned long long primary = 0, items = 0;
+  int rblk = 0;
+  bool grown = false;
   for (int r = 0; r < b.n; ++r) {
     const int i = order[r];
     Ctx &c = b.objs[i]->c;
+    const int P = c.H * c.W;
     irtps::ObjTrace &o = h[r];
     irtps::fill_obj_trace(c, o);
     o.f.levels = irtps::march_levels(c.levels, b.mip_cut);
@@ -135,9 +146,33 @@ int upload_trace(irtps_batch &b, const int *spp, const int *bounces, uint64_t se
     o.out = c.lbar;
     o.item_begin = begin;
     o.iter0 = c.t;
-    begin += (unsigned)(c.H * c.W) * (unsigned)c.K;
-    items += (unsigned long long)c.H * c.W * c.K;
-    primary += (unsigned long long)c.H * c.W * c.K * spp[i];
+    unsigned long long n_it = (unsigned long long)P * c.K;
+    if (b.shared) {  // (chunk, pixel) items; partial sums in the object's scratch
+      o.n_chunks = irtps::shared_chunks(P, spp[i]);
+      o.chunk = (spp[i] + o.n_chunks - 1) / o.n_chunks;
+      bool g = false;
+      BCK(irtps::ensure_shared_scratch(c, (size_t)o.n_chunks * c.K * c.C * P, g), "light-shared partial sums");
+      grown = grown || g;
+      o.part = c.shared_part;
+      n_it = (unsigned long long)P * o.n_chunks;
+      irtps::ReduceObj &q = red[r];
+      q.part = c.shared_part;
+      q.out = c.lbar;
+      q.n_chunks = o.n_chunks;
+      q.n_pix = P;
+      q.kc = c.K * c.C;
+      q.inv_spp = 1.0 / (double)spp[i];
+      q.blk_begin = rblk;
+      q.nblk = (int)std::min<long long>(4096, std::max<long long>(1, ((long long)P * q.kc + 2047) / 2048));
+      rblk += q.nblk;
+    }
+    begin += (unsigned)n_it;
+    items += n_it;
+    primary += (unsigned long long)P * (b.shared ? 1 : c.K) * spp[i];
+  }
+  if (grown && b.graph) {  // a captured iteration holds the old buffers
+    cudaGraphExecDestroy(b.graph);
+    b.graph = nullptr;
   }
   // claims run past the last item by at most one per lane: keep the counter far from wrapping
   if (items > (1ull << 32) - (1ull << 24))
@@ -146,15 +181,26 @@ int upload_trace(irtps_batch &b, const int *spp, const int *bounces, uint64_t se
   b.primary_per_iter = primary;
   BCK(cudaMemcpyAsync(b.d_trace, h.data(), sizeof(irtps::ObjTrace) * b.n, cudaMemcpyHostToDevice, b.stream),
       "trace descriptors");
+  if (b.shared) {
+    BCK(cudaMemcpyAsync(b.d_reduce, red.data(), sizeof(irtps::ReduceObj) * b.n, cudaMemcpyHostToDevice, b.stream),
+        "partial-sum descriptors");
+    if (rblk != b.reduce_blocks && b.graph) {
+      cudaGraphExecDestroy(b.graph);
+      b.graph = nullptr;
+    }
+    b.reduce_blocks = rblk;
+  }
   return IRTPS_OK;
 }
 
 int enqueue_trace(irtps_batch &b, uint32_t iter, bool captured, bool timed) {
   BSTAGE(ST_TRACE, true);
   BCK(irtps::build_pyramid_batch(b.stream, b.d_pyr, b.n, b.pyr_levels, b.pyr_blocks.data()), "pyramid launch");
-  BCK(irtps::launch_trace_batch(b.stream, b.C, b.d_trace, b.n, b.n_items, b.d_stats[b.n].counts, b.next_item,
-                                captured ? b.iter_dev : nullptr, iter, trace_grid(b)),
+  if (b.shared) BCK(irtps::launch_parts_batch(b.stream, true, b.d_reduce, b.n, b.reduce_blocks), "partial sums");
+  BCK(irtps::launch_trace_batch(b.stream, b.C, b.shared, b.d_trace, b.n, b.n_items, b.d_stats[b.n].counts,
+                                b.next_item, captured ? b.iter_dev : nullptr, iter, trace_grid(b)),
       "trace launch");
+  if (b.shared) BCK(irtps::launch_parts_batch(b.stream, false, b.d_reduce, b.n, b.reduce_blocks), "partial sums");
   BSTAGE(ST_TRACE, false);
   return IRTPS_OK;
 }
@@ -337,8 +383,9 @@ int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int
   b.n = n_obj;
   b.C = objs[0]->c.C;
   b.use_graph = use_graph ? 1 : 0;
+  b.shared = objs[0]->c.opt.sampling == 1;
   for (int i = 0; i < n_obj; ++i)
-    if (objs[i]->c.C != b.C || objs[i]->c.opt.sampling != 0 || objs[i]->c.opt.irls_iters != 0)
+    if (objs[i]->c.C != b.C || (objs[i]->c.opt.sampling == 1) != b.shared || objs[i]->c.opt.irls_iters != 0)
       return bail(IRTPS_EINVAL);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&b.sms, cudaDevAttrMultiProcessorCount, dev) !=
@@ -395,6 +442,7 @@ int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int
       (cudaMalloc(&b.d_ps, ps_bytes * n_obj) != cudaSuccess) ||
       (cudaMalloc(&b.d_ps0, ps_bytes * n_obj) != cudaSuccess) || (cudaMalloc(&b.d_jobs, job_bytes * n_obj) != cudaSuccess) ||
       (cudaMalloc((void **)&b.d_pyr, sizeof(irtps::PyrObj) * n_obj) != cudaSuccess) ||
+      (cudaMalloc((void **)&b.d_reduce, sizeof(irtps::ReduceObj) * n_obj) != cudaSuccess) ||
       (cudaMalloc((void **)&b.next_item, sizeof(unsigned)) != cudaSuccess) ||
       (cudaMalloc((void **)&b.iter_dev, sizeof(uint32_t)) != cudaSuccess)) {
     cudaGetLastError();
@@ -470,7 +518,7 @@ int irtps_batch_iterate(irtps_batch *x, int n_iter, const int *spp, const int *b
   }
   rc = end_call(b, true, n_iter, out_dH);
   {  // kernels per iteration: pyramid levels, trace, PS, seven of the solve, two of D_H (+ counter)
-    int k = 1 + 1 + 7 + 2 + (b.use_graph ? 1 : 0);
+    int k = 1 + 1 + 7 + 2 + (b.use_graph ? 1 : 0) + (b.shared ? 2 : 0);
     for (int l = 0; l < b.pyr_levels; ++l) k += b.pyr_blocks[l] > 0 ? 1 : 0;
     b.stats.launches += (unsigned long long)k * n_iter;
   }

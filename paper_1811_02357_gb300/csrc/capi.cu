@@ -162,19 +162,11 @@ bool trace_args_ok(Ctx &c, int spp, int bounces) {
 // Light-shared traces keep per-chunk partial sums; size them before any capture.
 int prepare_trace(Ctx &c, int n_pix, int spp) {
   if (c.opt.sampling != 1) return IRTPS_OK;
-  const size_t need = irtps::shared_scratch_floats(c, n_pix, spp);
-  if (need <= c.shared_cap) return IRTPS_OK;
-  CK(cudaStreamSynchronize(c.stream), "trace scratch");
-  if (c.graph) {  // a captured iteration holds the old buffer
-    cudaGraphExecDestroy(c.graph);
-    c.graph = nullptr;
-  }
-  if (c.shared_part) cudaFree(c.shared_part);
-  c.shared_part = nullptr;
-  c.shared_cap = 0;
-  int rc = dalloc(c, &c.shared_part, need, "light-shared partial sums");
-  if (rc) return rc;
-  c.shared_cap = need;
+  bool grown = false;
+  const cudaError_t e = irtps::ensure_shared_scratch(c, irtps::shared_scratch_floats(c, n_pix, spp), grown);
+  if (e != cudaSuccess)
+    return fail(c, e == cudaErrorMemoryAllocation ? IRTPS_ENOMEM : IRTPS_ECUDA,
+                std::string("light-shared partial sums: ") + cudaGetErrorString(e));
   return IRTPS_OK;
 }
 

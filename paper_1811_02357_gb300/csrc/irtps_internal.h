@@ -55,6 +55,8 @@ struct ObjTrace {
   float eps, Wf;          // ray-origin lift; W (grid units per world unit in x and y)
   unsigned item_begin;    // first work item of the object (batched launches)
   uint32_t iter0;         // added to the launch's iteration field
+  float *part;            // light-shared sampling: partial sums, n_chunks x n_pix x K x C
+  int n_chunks, chunk;    // light-shared sampling: sample chunks per pixel and samples per chunk
 };
 
 
@@ -174,9 +176,20 @@ cudaError_t launch_render(Ctx &c, uint64_t seed, float sigma, const float *lbar,
 int trace_grid_limit(int C, int n_obj = 0);  // resident blocks of the (batched) trace kernel, 0 if unknown
 void fill_obj_trace(const Ctx &c, ObjTrace &o);
 size_t shared_scratch_floats(const Ctx &c, int n_pix, int spp);  // light-shared chunk partials needed  // descriptor of a context's object (no sampling fields)
-cudaError_t launch_trace_batch(cudaStream_t s, int C, const ObjTrace *d_objs, int n_obj, unsigned n_items,
-                               unsigned long long *counts, unsigned *next_item, const uint32_t *iter_dev,
-                               uint32_t iter, int grid_limit);
+cudaError_t launch_trace_batch(cudaStream_t s, int C, bool shared, const ObjTrace *d_objs, int n_obj,
+                               unsigned n_items, unsigned long long *counts, unsigned *next_item,
+                               const uint32_t *iter_dev, uint32_t iter, int grid_limit);
+// light-shared sampling: sample chunks per pixel (fixed by the sizes), scratch, batched zero / reduce
+int shared_chunks(int n_pix, int spp);
+cudaError_t ensure_shared_scratch(Ctx &c, size_t need, bool &grown);
+struct ReduceObj {
+  float *part;     // n_chunks x n_pix x kc partial sums
+  float *out;      // kc x n_pix (Lbar)
+  int n_chunks, n_pix, kc;
+  double inv_spp;
+  int blk_begin, nblk;
+};
+cudaError_t launch_parts_batch(cudaStream_t s, bool zero, const ReduceObj *d_objs, int n, int blocks);
 cudaError_t launch_probe_dirs(cudaStream_t s, int n, const float *normals, const uint32_t *x0, const uint32_t *x1,
                               float *out);
 cudaError_t launch_probe_rays(Ctx &c, int n, const float *rays, float *t_out, int32_t *tri_out, int *overflow);

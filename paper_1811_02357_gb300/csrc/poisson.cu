@@ -32,7 +32,18 @@ static_assert(S_RZREF < kPartSlots, "partial slots");
 #ifndef IRTPS_CG_BLOCKS_PER_SM
 #define IRTPS_CG_BLOCKS_PER_SM 2
 #endif
+// batched solves: smaller teams (a share of the grid per object) gain from more co-resident blocks
+#ifndef IRTPS_CG_BATCH_BLOCKS_PER_SM
+#define IRTPS_CG_BATCH_BLOCKS_PER_SM 4
+#endif
+#ifndef IRTPS_CG_BATCH_MINB
+#define IRTPS_CG_BATCH_MINB 4
+#endif
 constexpr int kThreads = IRTPS_CG_THREADS;
+#ifndef IRTPS_BARRIER_SLEEP_NS
+#define IRTPS_BARRIER_SLEEP_NS 64
+#endif
+constexpr unsigned kBarrierSleepNs = IRTPS_BARRIER_SLEEP_NS;  // back-off between barrier polls
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -211,7 +222,7 @@ __device__ __forceinline__ void grid_barrier(unsigned *count, volatile unsigned 
           atomicExch(err, 1);
           break;
         }
-        __nanosleep(64);
+        if (kBarrierSleepNs > 0) __nanosleep(kBarrierSleepNs);
       }
     }
     __threadfence();
@@ -984,7 +995,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_b(const CGJob *jobs, int 
 }
 // one warp per job
 __global__ void k_cg_start_b(const CGJob *jobs) { cg_start_body(jobs[blockIdx.x].g, jobs[blockIdx.x].ctl); }
-__global__ void __launch_bounds__(kThreads) k_cg_loop_b(const CGJob *jobs, int n) {
+__global__ void __launch_bounds__(kThreads, IRTPS_CG_BATCH_MINB) k_cg_loop_b(const CGJob *jobs, int n) {
   for_team(jobs, n, [](const CGJob &j, Team t) {
     if (j.pre == 1)
       cg_loop_body<1, false>(j.g, j.ctl, &j.ds->cg, j.tol, j.max_iter, j.check, j.mg, t);
@@ -1010,13 +1021,13 @@ __global__ void __launch_bounds__(kThreads) k_zero_depth_b(const CGJob *jobs, in
 
 size_t cg_job_bytes() { return sizeof(CGJob); }
 
-// Co-resident blocks of the batched solve loop (at most IRTPS_CG_BLOCKS_PER_SM per SM).
+// Co-resident blocks of the batched solve loop (at most IRTPS_CG_BATCH_BLOCKS_PER_SM per SM).
 int cg_batch_grid_limit() {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_loop_b, kThreads, 0) != cudaSuccess) return 0;
-  per = per < IRTPS_CG_BLOCKS_PER_SM ? per : IRTPS_CG_BLOCKS_PER_SM;
+  per = per < IRTPS_CG_BATCH_BLOCKS_PER_SM ? per : IRTPS_CG_BATCH_BLOCKS_PER_SM;
   return per * sms;
 }
 

@@ -195,9 +195,6 @@ struct TraceArgs {
   unsigned *next_item;         // work-item counter, zero before the launch
   const uint32_t *iter_dev;    // when set, the iteration field is read here (graph replays)
   uint32_t iter, stream;
-  // light-shared sampling: partial sums, n_chunks x n_pix x K x C
-  float *part;
-  int n_chunks, chunk;
 };
 
 #ifndef IRTPS_TRACE_MINB
@@ -276,8 +273,8 @@ __global__ void __launch_bounds__(kTraceThreads,
     p = a.pixels ? a.pixels[ip] : ip;
     if constexpr (SHARED) {
       j = q;
-      s_end = min(ob->spp, (j + 1) * a.chunk);
-      return j * a.chunk;
+      s_end = min(ob->spp, (j + 1) * ob->chunk);
+      return j * ob->chunk;
     } else {
       k = q;
       return 0;
@@ -328,7 +325,7 @@ __global__ void __launch_bounds__(kTraceThreads,
   // light-shared: the direct term of light kk at the current hit, into the item's
   // partial sums (K x C contiguous per item, so a lane's updates stay in one or two lines)
   auto add_direct = [&](int kk) {
-    float *d = a.part + ((size_t)j * ob->n_pix + ip) * ob->K * C + kk * C;
+    float *d = ob->part + ((size_t)j * ob->n_pix + ip) * ob->K * C + kk * C;
 #pragma unroll
     for (int c = 0; c < C; ++c) d[c] += thr[c] * albedo_at(c, qp) * cosv;
   };
@@ -393,7 +390,7 @@ __global__ void __launch_bounds__(kTraceThreads,
       if (item_done) {
         if constexpr (SHARED) {
           // the environment part is common to every light
-          float *d = a.part + ((size_t)j * ob->n_pix + ip) * ob->K * C;
+          float *d = ob->part + ((size_t)j * ob->n_pix + ip) * ob->K * C;
           for (int kk = 0; kk < ob->K; ++kk)
 #pragma unroll
             for (int c = 0; c < C; ++c) d[kk * C + c] += sum[c];
@@ -591,6 +588,9 @@ void fill_obj_trace(const Ctx &c, ObjTrace &o) {
   o.Wf = (float)c.W;
   o.item_begin = 0;
   o.iter0 = 0;
+  o.part = nullptr;
+  o.n_chunks = 1;
+  o.chunk = 0;
 }
 
 __global__ void k_next_iter(uint32_t *iter) { *iter += 1u; }
@@ -610,7 +610,7 @@ cudaError_t launch_next_iter(cudaStream_t s, uint32_t *iter_dev) {
 // split depends on the sizes only, never on the grid, so that the summation
 // order - and every result bit - is the same for any tuning.
 constexpr long long kSharedItems = 1ll << 20;
-int shared_chunks(const Ctx &, int n_pix, int spp) {
+int shared_chunks(int n_pix, int spp) {
   long long n = (kSharedItems + n_pix - 1) / n_pix;
   n = n < 1 ? 1 : (n > spp ? spp : n);
   const int chunk = (int)((spp + n - 1) / n);
@@ -618,7 +618,7 @@ int shared_chunks(const Ctx &, int n_pix, int spp) {
 }
 
 size_t shared_scratch_floats(const Ctx &c, int n_pix, int spp) {
-  return (size_t)shared_chunks(c, n_pix, spp) * c.K * c.C * n_pix;
+  return (size_t)shared_chunks(n_pix, spp) * c.K * c.C * n_pix;
 }
 
 cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
@@ -640,18 +640,15 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
   a.iter_dev = iter_from_device ? c.iter_dev : nullptr;
   a.iter = iter;
   a.stream = stream;
-  a.part = nullptr;
-  a.n_chunks = 1;
-  a.chunk = spp;
   long long n = (long long)n_pix * c.K;
   if (shared) {
-    a.n_chunks = shared_chunks(c, n_pix, spp);
-    a.chunk = (spp + a.n_chunks - 1) / a.n_chunks;
-    const size_t need = (size_t)a.n_chunks * c.K * c.C * n_pix;
+    a.one.n_chunks = shared_chunks(n_pix, spp);
+    a.one.chunk = (spp + a.one.n_chunks - 1) / a.one.n_chunks;
+    const size_t need = (size_t)a.one.n_chunks * c.K * c.C * n_pix;
     if (need > c.shared_cap) return cudaErrorInvalidValue;  // scratch not prepared
-    a.part = c.shared_part;
-    if (cudaMemsetAsync(a.part, 0, sizeof(float) * need, c.stream) != cudaSuccess) return cudaGetLastError();
-    n = (long long)n_pix * a.n_chunks;
+    a.one.part = c.shared_part;
+    if (cudaMemsetAsync(a.one.part, 0, sizeof(float) * need, c.stream) != cudaSuccess) return cudaGetLastError();
+    n = (long long)n_pix * a.one.n_chunks;
   }
   a.n_items = (unsigned)n;
   const int threads = kTraceThreads;
@@ -668,7 +665,7 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
       k_trace<3, false, true><<<(unsigned)blocks, threads, smem, c.stream>>>(a);
     const size_t m = (size_t)c.K * c.C * n_pix;
     const unsigned rb = (unsigned)std::min<size_t>((m + 255) / 256, 8192);
-    k_reduce_chunks<<<rb, 256, 0, c.stream>>>(a.part, a.n_chunks, n_pix, c.K * c.C, 1.0 / (double)spp, out);
+    k_reduce_chunks<<<rb, 256, 0, c.stream>>>(a.one.part, a.one.n_chunks, n_pix, c.K * c.C, 1.0 / (double)spp, out);
     ++c.stats.launches;
   } else {
     if (c.C == 1)
@@ -680,10 +677,11 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
 }
 
 // Batched trace: one persistent launch over the work items of n objects (all of
-// C channels); descriptors in device memory, items in descriptor order.
-cudaError_t launch_trace_batch(cudaStream_t s, int C, const ObjTrace *d_objs, int n_obj, unsigned n_items,
-                               unsigned long long *counts, unsigned *next_item, const uint32_t *iter_dev,
-                               uint32_t iter, int grid_limit) {
+// C channels, all with the same sampling); descriptors in device memory, items in
+// descriptor order.
+cudaError_t launch_trace_batch(cudaStream_t s, int C, bool shared, const ObjTrace *d_objs, int n_obj,
+                               unsigned n_items, unsigned long long *counts, unsigned *next_item,
+                               const uint32_t *iter_dev, uint32_t iter, int grid_limit) {
   TraceArgs a;
   std::memset(&a, 0, sizeof(a));
   a.objs = d_objs;
@@ -702,11 +700,80 @@ cudaError_t launch_trace_batch(cudaStream_t s, int C, const ObjTrace *d_objs, in
   if (blocks < 1) blocks = 1;
   if (cudaMemsetAsync(next_item, 0, sizeof(unsigned), s) != cudaSuccess) return cudaGetLastError();
   const size_t smem = trace_smem_bytes(n_obj);
-  if (C == 1)
-    k_trace<1, true, false><<<(unsigned)blocks, threads, smem, s>>>(a);
-  else
-    k_trace<3, true, false><<<(unsigned)blocks, threads, smem, s>>>(a);
+  if (shared) {
+    if (C == 1)
+      k_trace<1, true, true><<<(unsigned)blocks, threads, smem, s>>>(a);
+    else
+      k_trace<3, true, true><<<(unsigned)blocks, threads, smem, s>>>(a);
+  } else {
+    if (C == 1)
+      k_trace<1, true, false><<<(unsigned)blocks, threads, smem, s>>>(a);
+    else
+      k_trace<3, true, false><<<(unsigned)blocks, threads, smem, s>>>(a);
+  }
   return cudaGetLastError();
+}
+
+// Light-shared partial sums of a batch: ZERO clears every object's buffer before
+// the trace; otherwise each object's chunks are reduced into its Lbar (as
+// k_reduce_chunks).  Object o owns blocks [blk_begin, blk_begin + nblk).
+template <bool ZERO>
+__global__ void k_parts_b(const ReduceObj *__restrict__ objs, int n) {
+  __shared__ int s_o;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (objs[mid].blk_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    s_o = lo;
+  }
+  __syncthreads();
+  const ReduceObj &o = objs[s_o];
+  const size_t m = (size_t)o.n_pix * o.kc;
+  const size_t start = (size_t)((int)blockIdx.x - o.blk_begin) * blockDim.x + threadIdx.x;
+  const size_t step = (size_t)o.nblk * blockDim.x;
+  if (ZERO) {
+    const size_t all = m * o.n_chunks;
+    for (size_t i = start; i < all; i += step) o.part[i] = 0.0f;
+  } else {
+    for (size_t i = start; i < m; i += step) {
+      double v = 0.0;
+      for (int jj = 0; jj < o.n_chunks; ++jj) v += (double)o.part[(size_t)jj * m + i];
+      const size_t ip = i / o.kc, e = i - ip * o.kc;
+      o.out[e * o.n_pix + ip] = (float)(v * o.inv_spp);
+    }
+  }
+}
+
+cudaError_t launch_parts_batch(cudaStream_t s, bool zero, const ReduceObj *d_objs, int n, int blocks) {
+  if (zero)
+    k_parts_b<true><<<blocks, 256, 0, s>>>(d_objs, n);
+  else
+    k_parts_b<false><<<blocks, 256, 0, s>>>(d_objs, n);
+  return cudaGetLastError();
+}
+
+cudaError_t ensure_shared_scratch(Ctx &c, size_t need, bool &grown) {
+  grown = false;
+  if (need <= c.shared_cap) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return e;
+  if (c.graph) {  // a captured iteration holds the old buffer
+    cudaGraphExecDestroy(c.graph);
+    c.graph = nullptr;
+  }
+  if (c.shared_part) cudaFree(c.shared_part);
+  c.shared_part = nullptr;
+  c.shared_cap = 0;
+  e = cudaMalloc((void **)&c.shared_part, sizeof(float) * need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  c.shared_cap = need;
+  grown = true;
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------

@@ -82,9 +82,47 @@ def test_shared_graph_and_tuning_keep_bits(lib, oracle_mod):
             assert np.array_equal(x, y)
 
 
-def test_shared_rejected_in_batches(lib):
+def test_shared_batch_matches_single_contexts(lib, oracle_mod):
+    """A batch of light-shared objects (one persistent launch, per-object chunking and partial
+    sums, batched zero and reduce) traces and solves the normals bit for bit as each object's
+    own context, and a batched loop matches the oracle's light-shared loop per object."""
+    spec = [(91, 24, 20, 4, 16, 1), (92, 17, 33, 8, 8, 2), (93, 30, 30, 6, 12, 2), (94, 9, 41, 5, 4, 1)]
+    scs = [scenes.mixed(sd, H, W, K=K, C=3) for sd, H, W, K, _, _ in spec]
+    A = [oracle_mod.render(sc.depth, sc.normals, sc.albedo, sc.lights, sc.env, 32, 2, 3 + i, 0.002)
+         for i, sc in enumerate(scs)]
+    spp = [x[4] for x in spec]
+    bounces = [x[5] for x in spec]
+    ctxs = [_ctx(lib, sc) for sc in scs]
+    try:
+        for c, a in zip(ctxs, A):
+            c.set_images(a)
+        with lib.Batch(ctxs, use_graph=True) as b:
+            b.iterate(1, spp, bounces, 41)
+            st = b.stats()
+            got = [(c.indirect(), c.normals()) for c in ctxs]
+            b.iterate(1, spp, bounces, 41)
+            got2 = [(c.normals(), c.depth()) for c in ctxs]
+        assert st["walk_overflows"] == 0
+        assert st["primary_segments"] == sum(sc.H * sc.W * s for sc, s in zip(scs, spp))
+        for i, sc in enumerate(scs):
+            with _ctx(lib, sc) as c:
+                c.set_object(i)
+                c.set_images(A[i])
+                c.iterate(1, spp[i], bounces[i], 41)
+                assert np.array_equal(got[i][0], c.indirect()), i
+                assert np.array_equal(got[i][1], c.normals()), i
+            hist = oracle_mod.irtps_run(A[i], sc.lights, sc.env, 2, spp[i], bounces[i], 41, obj=i, shared=True)
+            err = oracle_mod.angular_error_deg(got2[i][0][..., :3].reshape(-1, 3), hist[2]["normals"].reshape(-1, 3))
+            dabs = np.abs(got2[i][1] - hist[2]["depth"]) / np.ptp(hist[2]["depth"])
+            assert err.mean() <= 0.05 and dabs.mean() <= 1e-4 and dabs.max() <= 1e-3, (i, err.mean(), dabs.max())
+    finally:
+        for c in ctxs:
+            c.close()
+
+
+def test_batch_rejects_mixed_sampling(lib):
     sc = scenes.mixed(87, 20, 20, K=4, C=3)
-    with _ctx(lib, sc) as a:
+    with _ctx(lib, sc) as a, lib.Context(sc.H, sc.W, sc.lights, sc.env) as b:
         with pytest.raises(lib.IrtpsError) as e:
-            lib.Batch([a])
+            lib.Batch([a, b])
         assert e.value.code == lib.IRTPS_EINVAL
