@@ -285,8 +285,13 @@ __device__ __forceinline__ float inv_degree(int i, int j, int H, int W) {
 // ---------------------------------------------------------------------------
 constexpr int kMgMaxLevels = 16;
 constexpr int kMgBlockPoints = 4096;
+// Scale of the coarse-grid correction.  Piecewise-constant aggregation
+// under-corrects the smooth error components; scaling the correction by 1.5
+// (a scalar, so the V-cycle stays symmetric) cut the warm 512x512 solve from 90
+// to 30 iterations.  Above about 1.7 the preconditioner lost definiteness on some
+// grids.  The weighted (IRLS) solves keep the plain correction.
 #ifndef IRTPS_MG_CSCALE
-#define IRTPS_MG_CSCALE 1.0f
+#define IRTPS_MG_CSCALE 1.5f
 #endif
 
 struct MG {
@@ -893,7 +898,8 @@ static cudaError_t solve_once(Ctx &c) {
   int m = c.opt.cg_check_every > 0 ? c.opt.cg_check_every : 10;
   double tol = c.opt.cg_tol;
   int max_iter = c.opt.cg_max_iter;
-  const MG mg = make_mg(c);
+  MG mg = make_mg(c);
+  if (WEIGHTED) mg.cscale = 1.0f;
   void *args[] = {(void *)&g, (void *)&ctl, (void *)&acc, (void *)&tol, (void *)&max_iter, (void *)&m, (void *)&mg};
   const void *fn = c.opt.precond == 1 ? (const void *)k_cg_loop<1, WEIGHTED> : (const void *)k_cg_loop<0, WEIGHTED>;
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(kThreads), args, 0, c.stream);
