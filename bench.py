@@ -47,6 +47,8 @@ WORKLOADS = {
     # the batched pattern: 64 objects (sides 96..1024, K, spp, bounces per object), one IRT
     # iteration of all of them per step, against per-object launches (run_batch)
     "batch_64": ("batch_objects", {}, None, None, 1, 32, 1),
+    # a small batch of the same kernels for profiler captures (16 objects, sides 96..384)
+    "batch_16_profile": ("batch_objects", {"n": 16, "side_hi": 384}, None, None, 1, 8, 1),
 }
 
 # Algorithmic lane operations per unit of trace work (counted from the formulas:
@@ -182,7 +184,7 @@ def run_reference(args):
         return 0
     import scenes
     name, kw, spp, bounces, n_iter, _, _ = WORKLOADS[args.workload]
-    if args.workload == "batch_64":  # a sample of the first object (the oracle traces one object at a time)
+    if name == "batch_objects":  # a sample of the first object (the oracle traces one object at a time)
         sc, spp, bounces = scenes.batch_objects(n=1)[0]
     else:
         sc = getattr(scenes, name)(**kw)
@@ -220,7 +222,8 @@ def run_batch(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     _, _, _, _, n_iter, rspp, rb = WORKLOADS[args.workload]
-    objs = scenes.batch_objects(seed=4 + 100 * rank)
+    _, kw, _, _, _, _, _ = WORKLOADS[args.workload]
+    objs = scenes.batch_objects(seed=4 + 100 * rank, **kw)
     stream = torch.cuda.Stream(device=dev)
     img_dtype = irtps.IRTPS_F16 if args.images == "f16" else irtps.IRTPS_F32
     ctxs, imgs = [], []
@@ -384,7 +387,7 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batch_64":
+    if WORKLOADS[args.workload][0] == "batch_objects":
         return run_batch(args)
 
     import torch

@@ -606,13 +606,17 @@ cudaError_t launch_next_iter(cudaStream_t s, uint32_t *iter_dev) {
 }
 
 // Light-shared sampling splits each pixel's samples into chunks so that there
-// are about 2^20 work items (several per lane of a full persistent grid).  The
-// split depends on the sizes only, never on the grid, so that the summation
-// order - and every result bit - is the same for any tuning.
+// are about 2^20 work items (several per lane of a full persistent grid), with at
+// least 16 samples per chunk: every chunk costs a K x C block of partial sums
+// (cleared, updated, reduced), which few samples would not pay for.  The split
+// depends on the sizes only, never on the grid, so that the summation order -
+// and every result bit - is the same for any tuning.
 constexpr long long kSharedItems = 1ll << 20;
+constexpr int kSharedMinChunk = 16;
 int shared_chunks(int n_pix, int spp) {
   long long n = (kSharedItems + n_pix - 1) / n_pix;
-  n = n < 1 ? 1 : (n > spp ? spp : n);
+  const long long most = spp / kSharedMinChunk > 1 ? spp / kSharedMinChunk : 1;
+  n = n < 1 ? 1 : (n > most ? most : n);
   const int chunk = (int)((spp + n - 1) / n);
   return (spp + chunk - 1) / chunk;
 }
