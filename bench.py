@@ -64,6 +64,7 @@ LANES_PER_SM = 128
 # DRAM bytes (read + write) of one trace launch of a workload, from the ncu capture summarised in
 # profiles/k_trace_bumps512_dram.md (the kernel has not changed since)
 TRACE_DRAM_BYTES = {"bumps_512": 10.27e6 + 2.03e6}
+TRACE_DRAM_TUNING = (8, 0)  # trace blocks per SM and pyramid levels left out when it was taken
 
 
 def sm_max_mhz():
@@ -148,8 +149,9 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(sc, spp, bounces, target_s=12.0, seed=1):
-    """The oracle as it stands, on all host cores, over a pixel sample of the workload."""
+def cpu_baseline(sc, spp, bounces, target_s=12.0, seed=1, shared=False):
+    """The oracle as it stands, on all host cores, over a pixel sample of the workload
+    (`shared`: its light-shared trace)."""
     import oracle
     threads = os.cpu_count() or 1
     rng = np.random.default_rng(123)
@@ -159,7 +161,7 @@ def cpu_baseline(sc, spp, bounces, target_s=12.0, seed=1):
         pix = np.sort(rng.choice(P, n, replace=False)).astype(np.int32)
         t0 = time.perf_counter()
         _, _, (prim, segs) = oracle.trace(sc.depth, sc.normals, sc.albedo, sc.lights, sc.env, spp, bounces, seed,
-                                          0, pixels=pix, fp32=True, threads=threads)
+                                          0, pixels=pix, fp32=True, threads=threads, shared=shared)
         return time.perf_counter() - t0, segs
 
     n = max(threads, 16)
@@ -173,7 +175,8 @@ def cpu_baseline(sc, spp, bounces, target_s=12.0, seed=1):
     else:
         n2 = n
     return {"value": segs / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n2} random pixels of the workload x {sc.K} lights x {spp} spp x {bounces} bounces "
+            "sample": f"{n2} random pixels of the workload x {'one path for all ' if shared else ''}{sc.K} lights "
+                      f"x {spp} spp x {bounces} bounces "
                       f"(ground-truth state, one trace pass, {segs} segments, {dt:.1f} s)"}
 
 
@@ -189,18 +192,19 @@ def run_reference(args):
     else:
         sc = getattr(scenes, name)(**kw)
     per_step_s = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    shared = args.sampling == "shared"
     for _ in range(args.warmup):
-        cpu_baseline(sc, spp, bounces, target_s=min(per_step_s, 3.0))
+        cpu_baseline(sc, spp, bounces, target_s=min(per_step_s, 3.0), shared=shared)
     vals = []
     last = None
     for _ in range(args.steps):
-        last = cpu_baseline(sc, spp, bounces, target_s=per_step_s)
+        last = cpu_baseline(sc, spp, bounces, target_s=per_step_s, shared=shared)
         vals.append(last["value"])
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": "IRT-PS Mrays/s", "value": v, "unit": "Mrays/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "spp": spp, "bounces": bounces},
+            "config": {"workload": args.workload, "spp": spp, "bounces": bounces, "sampling": args.sampling},
             "cpu_baseline": dict(last, value=v),
             "e2e": {"value": v, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -280,6 +284,9 @@ def run_batch(args):
             out.append((e0.elapsed_time(e1), r))
         return out
 
+    # the tuner picks the trace grid and pyramid depth (no result bit depends on them)
+    set_all()
+    batch.autotune([max(1, s_ // 16) for s_ in spp], bnc, seed)
     for _ in range(args.warmup):
         batched()
     torch.cuda.synchronize()
@@ -299,9 +306,11 @@ def run_batch(args):
     ms_all, segs_all = combine_ranks(ms, segs, world, dev)
     value = segs_all / (ms_all / 1e3) / 1e6
     # the same step with the iteration replayed as a CUDA graph
+    tuning = batch.tuning()
     batch.close()
     batch = irtps.Batch(ctxs, use_graph=True)
     batch.set_stream(stream.cuda_stream)
+    batch.set_tuning(*tuning)
     batched()
     graph_ms = timed(batched, 1)[0][0]
     # the same job as per-object launches of the plain form (one context after another)
@@ -335,7 +344,7 @@ def run_batch(args):
     ops = OPS_PER_DRAW * draws + OPS_PER_NODE * nodes + OPS_PER_TRI * tris
     achieved = ops / (trace_ms / 1e3) / 1e12
     peak = SM_COUNT * LANES_PER_SM * mhz * 1e6 / 1e12
-    bps, cut = batch.tuning()
+    bps, cut = tuning
     line = {"metric": "IRT-PS Mrays/s", "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -360,7 +369,7 @@ def run_batch(args):
             "e2e": e2e}
     if rank == 0 and not args.no_cpu_baseline:
         sc0, s0, b0 = objs[0]
-        line["cpu_baseline"] = cpu_baseline(sc0, s0, b0)
+        line["cpu_baseline"] = cpu_baseline(sc0, s0, b0, shared=args.sampling == "shared")
     batch.close()
     for c in ctxs:
         c.close()
@@ -424,6 +433,11 @@ def main():
         ctx.set_images(A0_in, dtype=img_dtype, on_device=True)
         ctx.iterate(n_iter, spp, bounces, seed)
         return ctx.stats()
+
+    # the tuner picks the trace grid and pyramid depth (no result bit depends on them)
+    ctx.set_images(A0_in, dtype=img_dtype, on_device=True)
+    ctx.autotune(max(1, spp // 16), bounces, seed)
+    tuning = ctx.tuning()
 
     for _ in range(args.warmup):
         job()
@@ -491,7 +505,8 @@ def main():
     achieved = ops / (tot["trace_ms"] / 1e3) / 1e12
     peak = SM_COUNT * LANES_PER_SM * mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": TRACE_DRAM_BYTES.get(args.workload) if args.sampling == "per_light" else None,
+                "traffic": (TRACE_DRAM_BYTES.get(args.workload)
+                            if args.sampling == "per_light" and tuning == TRACE_DRAM_TUNING else None),
                 "kernel": "k_trace",
                 "launch_ms": tot["trace_ms"] / trace_launches,
                 "note": "lane-operation issue peak = 152 SMs x 128 lanes x max SM clock; ops counted per "
@@ -501,7 +516,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "H": H, "W": W, "K": K, "C": C, "spp": spp, "images": args.images,
-                       "sampling": args.sampling,
+                       "sampling": args.sampling, "trace_blocks_per_sm": tuning[0], "mip_cut": tuning[1],
                        "bounces": bounces, "irt_iterations_per_step": n_iter, "parallelism": f"replicas{world}",
                        "l2": "512 MB buffer written between timed steps"},
             "pixel_iters_per_s": P * n_iter * world * args.steps / (ms_all / 1e3),
@@ -514,7 +529,7 @@ def main():
                                  "draws": tot["draws"] / max(1, tot["segments"])},
             "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e}
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sc, spp, bounces)
+        line["cpu_baseline"] = cpu_baseline(sc, spp, bounces, shared=args.sampling == "shared")
     ctx.close()
     if rank == 0:
         print(json.dumps(line))
