@@ -12,6 +12,8 @@ e2e        = the same through the C ABI from pinned host images, results copied 
 roofline   = the trace kernel (dominant): algorithmic lane operations per second
              against the lane-issue peak (bound "alu")
 cpu_baseline = the oracle (plain C++) on the host cores over a pixel sample
+evaluation (--evaluate) = errors against the ground truth (height, albedo, normal; the paper's
+             evaluation measures) of classic PS and of IRT-PS with 1, 2 and 3 traced reflections
 
 Workload `batch_64`: 64 objects of scenes.batch_objects (sides log-uniform in
 96..1024, K in {4, 8, 16, 32}, spp in {64, 128, 256}, bounces in {1, 2}); one
@@ -126,6 +128,44 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def gt_errors(sc, depth, normals, albedo):
+    """Errors of an estimate against the synthetic ground truth, as the paper's evaluation reports
+    them: mean |H_gt - H| with each surface's mean removed, mean absolute albedo error (over channels),
+    mean absolute normal-component error (over x, y, z); plus the mean angle between normals (deg)."""
+    a = sc.depth.astype(np.float64)
+    b = depth.astype(np.float64)
+    e_h = float(np.abs((a - a.mean()) - (b - b.mean())).mean())
+    e_rho = float(np.abs(sc.albedo.astype(np.float64) - albedo.astype(np.float64)).mean(axis=(1, 2)).mean())
+    ng = sc.normals.reshape(-1, 3).astype(np.float64)
+    ne = normals[..., :3].reshape(-1, 3).astype(np.float64)
+    e_n = float(np.abs(ng - ne).mean(axis=0).mean())
+    cross = np.linalg.norm(np.cross(ng, ne), axis=1)
+    ang = float(np.degrees(np.arctan2(cross, (ng * ne).sum(axis=1))).mean())
+    return {"height": e_h, "albedo": e_rho, "normal": e_n, "normal_deg": ang}
+
+
+def evaluate(irtps, sc, spp, n_iter, seed, opt, stream, dev):
+    """Classic PS and IRT-PS with r = 1, 2, 3 traced reflections on images rendered with three."""
+    import torch
+    K, C, H, W = sc.K, sc.C, sc.H, sc.W
+    A = torch.empty((K, C, H, W), dtype=torch.float32, device=dev)
+    with irtps.Context(H, W, sc.lights, sc.env) as gt:
+        gt.set_stream(stream.cuda_stream)
+        gt.set_state(sc.depth, sc.normals, sc.albedo)
+        gt.render(spp, 3, 2000, 0.002, out=A)
+    torch.cuda.synchronize()
+    out = {"images": f"rendered with 3 reflections, {spp} spp, sigma 0.002", "irt_iterations": n_iter}
+    for r in (1, 2, 3):
+        with irtps.Context(H, W, sc.lights, sc.env, opt) as ctx:
+            ctx.set_stream(stream.cuda_stream)
+            ctx.set_images(A, on_device=True)
+            if r == 1:
+                out["classic_ps"] = gt_errors(sc, ctx.depth(), ctx.normals(), ctx.albedo())
+            ctx.iterate(n_iter, spp, r, seed)
+            out[f"irtps_r{r}"] = gt_errors(sc, ctx.depth(), ctx.normals(), ctx.albedo())
+    return out
 
 
 def combine_ranks(ms, units, world, device):
@@ -285,8 +325,9 @@ def run_batch(args):
         return out
 
     # the tuner picks the trace grid and pyramid depth (no result bit depends on them)
-    set_all()
-    batch.autotune([max(1, s_ // 16) for s_ in spp], bnc, seed)
+    if not args.no_autotune and not args.workload.endswith("_profile"):  # profile cases keep the defaults
+        set_all()
+        batch.autotune([max(1, s_ // 16) for s_ in spp], bnc, seed)
     for _ in range(args.warmup):
         batched()
     torch.cuda.synchronize()
@@ -391,6 +432,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--images", default="f32", choices=["f32", "f16"],
                     help="storage type of the input images (f16: the mixed-precision pattern)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default trace grid and pyramid depth (profiler captures)")
+    ap.add_argument("--evaluate", action="store_true",
+                    help="also report Table-1-style errors against the ground truth: classic PS and IRT-PS "
+                         "with 1, 2 and 3 traced reflections (outside the timed region)")
     ap.add_argument("--sampling", default="per_light", choices=["per_light", "shared"],
                     help="trace sampling: spp paths per (pixel, light), or per pixel for all lights")
     args = ap.parse_args()
@@ -435,8 +481,9 @@ def main():
         return ctx.stats()
 
     # the tuner picks the trace grid and pyramid depth (no result bit depends on them)
-    ctx.set_images(A0_in, dtype=img_dtype, on_device=True)
-    ctx.autotune(max(1, spp // 16), bounces, seed)
+    if not args.no_autotune and not args.workload.endswith("_profile"):  # profile cases keep the defaults
+        ctx.set_images(A0_in, dtype=img_dtype, on_device=True)
+        ctx.autotune(max(1, spp // 16), bounces, seed)
     tuning = ctx.tuning()
 
     for _ in range(args.warmup):
@@ -528,6 +575,8 @@ def main():
                                  "tri_tests": tot["tris"] / max(1, tot["segments"]),
                                  "draws": tot["draws"] / max(1, tot["segments"])},
             "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e}
+    if args.evaluate:
+        line["evaluation"] = evaluate(irtps, sc, spp, n_iter, seed, opt, stream, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, spp, bounces, shared=args.sampling == "shared")
     ctx.close()
