@@ -65,8 +65,7 @@ SM_COUNT = 152
 LANES_PER_SM = 128
 # DRAM bytes (read + write) of one trace launch of a workload, from the ncu capture summarised in
 # profiles/k_trace_bumps512_dram.md (the kernel has not changed since)
-TRACE_DRAM_BYTES = {"bumps_512": 10.27e6 + 2.03e6}
-TRACE_DRAM_TUNING = (8, 0)  # trace blocks per SM and pyramid levels left out when it was taken
+TRACE_DRAM_BYTES = {"bumps_512": 10.50e6 + 1.65e6}
 
 
 def sm_max_mhz():
@@ -327,7 +326,7 @@ def run_batch(args):
     # the tuner picks the trace grid and pyramid depth (no result bit depends on them)
     if not args.no_autotune and not args.workload.endswith("_profile"):  # profile cases keep the defaults
         set_all()
-        batch.autotune([max(1, s_ // 16) for s_ in spp], bnc, seed)
+        batch.autotune([max(1, s_ // (4 if args.sampling == "shared" else 16)) for s_ in spp], bnc, seed)
     for _ in range(args.warmup):
         batched()
     torch.cuda.synchronize()
@@ -483,7 +482,9 @@ def main():
     # the tuner picks the trace grid and pyramid depth (no result bit depends on them)
     if not args.no_autotune and not args.workload.endswith("_profile"):  # profile cases keep the defaults
         ctx.set_images(A0_in, dtype=img_dtype, on_device=True)
-        ctx.autotune(max(1, spp // 16), bounces, seed)
+        # probes with a sixteenth of the samples (a quarter when light-shared, whose work items are
+        # sample chunks of at least 16: fewer samples would change the items the grid shares)
+        ctx.autotune(max(1, spp // (4 if args.sampling == "shared" else 16)), bounces, seed)
     tuning = ctx.tuning()
 
     for _ in range(args.warmup):
@@ -552,8 +553,7 @@ def main():
     achieved = ops / (tot["trace_ms"] / 1e3) / 1e12
     peak = SM_COUNT * LANES_PER_SM * mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": (TRACE_DRAM_BYTES.get(args.workload)
-                            if args.sampling == "per_light" and tuning == TRACE_DRAM_TUNING else None),
+                "traffic": TRACE_DRAM_BYTES.get(args.workload) if args.sampling == "per_light" else None,
                 "kernel": "k_trace",
                 "launch_ms": tot["trace_ms"] / trace_launches,
                 "note": "lane-operation issue peak = 152 SMs x 128 lanes x max SM clock; ops counted per "
