@@ -188,9 +188,9 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(sc, spp, bounces, target_s=12.0, seed=1, shared=False):
+def cpu_baseline(sc, spp, bounces, target_s=12.0, seed=1, shared=False, single_thread=False):
     """The oracle as it stands, on all host cores, over a pixel sample of the workload
-    (`shared`: its light-shared trace)."""
+    (`shared`: its light-shared trace; `single_thread`: also its rate on one core)."""
     import oracle
     threads = os.cpu_count() or 1
     rng = np.random.default_rng(123)
@@ -213,10 +213,20 @@ def cpu_baseline(sc, spp, bounces, target_s=12.0, seed=1, shared=False):
         dt, segs = run(n2)
     else:
         n2 = n
-    return {"value": segs / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
-            "sample": f"{n2} random pixels of the workload x {'one path for all ' if shared else ''}{sc.K} lights "
-                      f"x {spp} spp x {bounces} bounces "
-                      f"(ground-truth state, one trace pass, {segs} segments, {dt:.1f} s)"}
+    out = {"value": segs / dt / 1e6, "unit": "Mrays/s", "cores": threads, "kind": "oracle",
+           "sample": f"{n2} random pixels of the workload x {'one path for all ' if shared else ''}{sc.K} lights "
+                     f"x {spp} spp x {bounces} bounces "
+                     f"(ground-truth state, one trace pass, {segs} segments, {dt:.1f} s)"}
+    if single_thread and threads > 1:  # the oracle's other mode: one core, about 3 s of work
+        n1 = int(max(1, min(P, n2 * 3.0 / max(dt * threads, 1e-3))))
+        pix = np.sort(rng.choice(P, n1, replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        _, _, (_, segs1) = oracle.trace(sc.depth, sc.normals, sc.albedo, sc.lights, sc.env, spp, bounces, seed, 0,
+                                        pixels=pix, fp32=True, threads=1, shared=shared)
+        dt1 = time.perf_counter() - t0
+        out["single_thread"] = {"value": segs1 / dt1 / 1e6, "unit": "Mrays/s", "cores": 1,
+                                "sample": f"{n1} random pixels, {segs1} segments, {dt1:.1f} s"}
+    return out
 
 
 def run_reference(args):
@@ -578,7 +588,7 @@ def main():
     if args.evaluate:
         line["evaluation"] = evaluate(irtps, sc, spp, n_iter, seed, opt, stream, dev)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sc, spp, bounces, shared=args.sampling == "shared")
+        line["cpu_baseline"] = cpu_baseline(sc, spp, bounces, shared=args.sampling == "shared", single_thread=True)
     ctx.close()
     if rank == 0:
         print(json.dumps(line))

@@ -1,6 +1,6 @@
 // Reverted Monte-Carlo trace (Sec. IV, Eq. 5-7): min/max pyramid build, the
-// per-(pixel, light) trace kernel, the stage-0 forward render, and geometry
-// probes used by the parity tests.
+// trace kernel (per light or light-shared, single object or batched), the
+// stage-0 forward render, and geometry probes used by the parity tests.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -164,8 +164,8 @@ __device__ __forceinline__ void env_lookup(const float *__restrict__ env, int EH
 }
 
 // ---------------------------------------------------------------------------
-// The trace.  Each thread owns one (light k, pixel p) and runs its spp sample
-// paths in order, Kahan-summing their radiance in FP32.  Sample path: bounce
+// The trace.  A work item (light k, pixel p) runs its spp sample paths in
+// order in one lane, Kahan-summing their radiance in FP32.  Sample path: bounce
 // b = 1..B draws Philox4x32-10 at counter {p, s, (k<<8)|(b<<4)|stream, iteration}
 // with key {seed_lo ^ obj, seed_hi}, samples a cosine direction about the
 // current normal estimate at the origin, and marches the heightfield.  Escape:
