@@ -122,11 +122,14 @@ int irtps_set_images(irtps_ctx *ctx, const void *images, int dtype, int on_devic
 
 /* IRT iterations (Sec. IV, stages 4-5 and the loop): n_iter times
  *   build the min/max pyramid of H_t; trace Lbar_t over (H_t, n_t, rho_t) with
- *   spp samples per (pixel, light) and bounces in 1..3 (the paper's r1..r3);
+ *   spp samples per (pixel, light) (per pixel with light-shared sampling) and
+ *   bounces in 1..3 (the paper's r1..r3);
  *   I = A0 - rho_t * Lbar_t (subtracted from the ORIGINAL images); PS -> n, rho;
- *   integrate -> H_{t+1}; D_H = max|H_{t+1} - H_t| / range(H_{t+1}).
+ *   integrate -> H_{t+1} (least squares, or the Huber M-estimator with
+ *   irls_iters > 0); D_H = max|H_{t+1} - H_t| / range(H_{t+1}).
  * Random draws: Philox4x32-10, key {seed_lo ^ object, seed_hi}, counter
- * {pixel, sample, light<<8 | bounce<<4 | 0, t}; t advances by one per iteration.
+ * {pixel, sample, light<<8 | bounce<<4 | 0, t} (light field 0 with light-shared
+ * sampling); t advances by one per iteration.
  * out_dH (nullable host pointer) receives D_H of the last iteration. */
 int irtps_iterate(irtps_ctx *ctx, int n_iter, int spp, int bounces, uint64_t seed, double *out_dH);
 
