@@ -345,6 +345,8 @@ def run_batch(args):
     launches0 = batch.stats()["launches"] + sum(c.stats()["launches"] for c in ctxs)
     with ClockSampler(local) as clk:
         res = timed(batched, args.steps)
+        if world > 1:
+            torch.distributed.barrier()
     launches = batch.stats()["launches"] + sum(c.stats()["launches"] for c in ctxs) - launches0
     ms = sum(r[0] for r in res)
     segs = sum(r[1]["segments"] for r in res)
@@ -524,6 +526,8 @@ def main():
             tot["depth_ms"] += st["depth_ms"]
             tot["cg_iters"] += st["cg_iterations"]
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
     launches = ctx.stats()["launches"] - launches0
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ms_all, segs_all = combine_ranks(ms, tot["segments"], world, dev)
