@@ -232,8 +232,8 @@ int irtps_autotune(irtps_ctx *ctx, int spp_probe, int bounces, uint64_t seed, do
  * per-item cost first), one PS launch, one cooperative depth-solve launch in
  * which each object's solve runs on its own team of blocks, and one D_H launch.
  * Objects may differ in H, W, K, spp, bounces and options; all must have the
- * same C, image dtype and sampling option, and least-squares integration
- * (irls_iters = 0).  Every object's results are bit-identical to its own
+ * same C, image dtype, sampling option and irls_iters (robust integration runs
+ * the same number of reweighting steps for every object; irls_delta may differ).  Every object's results are bit-identical to its own
  * irtps_iterate in the trace and the normal solve; the depth solve differs from
  * it only by the summation order of its reductions (team size), within cg_tol.
  *

@@ -20,6 +20,8 @@ struct irtps_batch {
   std::vector<irtps_ctx *> objs;
   int n = 0, C = 0;
   bool shared = false;  // light-shared sampling (every object's option)
+  int irls_iters = 0;   // robust-integration reweighting steps (every object's option)
+  int mg_levels = 0;    // most multigrid levels of an object
   int use_graph = 0;
   cudaStream_t stream = nullptr;      // where the batch's work runs
   cudaStream_t own_stream = nullptr;
@@ -114,6 +116,11 @@ int stage_mark(irtps_batch &b, int stage, bool start) {
   } while (0)
 
 int trace_grid(const irtps_batch &b) { return b.trace_per_sm * b.sms; }
+
+// Kernels the robust-integration steps add to each batched solve.
+int irls_kernels(const irtps_batch &b) {
+  return b.irls_iters > 0 ? b.irls_iters * (1 + (b.mg_levels - 1) + 7) + 1 : 0;
+}
 
 // Trace descriptors for this call: objects of larger per-item cost first, so
 // that the cheap items of the last claims fill the tail of the launch.
@@ -214,7 +221,7 @@ int enqueue_iteration(irtps_batch &b, uint32_t iter, bool captured) {
   BCK(irtps::launch_ps_batch(b.stream, b.C, b.objs[0]->c.images_dtype, b.d_ps, b.n, b.ps_blocks), "ps launch");
   BSTAGE(ST_PS, false);
   BSTAGE(ST_DEPTH, true);
-  BCK(irtps::solve_depth_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks), "depth solve launch");
+  BCK(irtps::solve_depth_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks, b.irls_iters, b.mg_levels), "depth solve launch");
   BSTAGE(ST_DEPTH, false);
   BCK(irtps::depth_change_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks), "depth change launch");
   if (captured) BCK(irtps::launch_next_iter(b.stream, b.iter_dev), "iteration counter");
@@ -384,9 +391,13 @@ int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int
   b.C = objs[0]->c.C;
   b.use_graph = use_graph ? 1 : 0;
   b.shared = objs[0]->c.opt.sampling == 1;
-  for (int i = 0; i < n_obj; ++i)
-    if (objs[i]->c.C != b.C || (objs[i]->c.opt.sampling == 1) != b.shared || objs[i]->c.opt.irls_iters != 0)
+  b.irls_iters = objs[0]->c.opt.irls_iters;
+  for (int i = 0; i < n_obj; ++i) {
+    if (objs[i]->c.C != b.C || (objs[i]->c.opt.sampling == 1) != b.shared ||
+        objs[i]->c.opt.irls_iters != b.irls_iters)
       return bail(IRTPS_EINVAL);
+    b.mg_levels = std::max(b.mg_levels, objs[i]->c.mg_levels);
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&b.sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                cudaSuccess)
@@ -488,12 +499,12 @@ int irtps_batch_set_images(irtps_batch *x, const void *const *images, int dtype,
   BSTAGE(ST_PS, false);
   BSTAGE(ST_DEPTH, true);
   BCK(irtps::zero_depth_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks), "depth reset");
-  BCK(irtps::solve_depth_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks), "depth solve launch");
+  BCK(irtps::solve_depth_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks, b.irls_iters, b.mg_levels), "depth solve launch");
   BSTAGE(ST_DEPTH, false);
   b.primary_per_iter = 0;
   rc = end_call(b, true, 0, nullptr);
   b.stats.iterations_done = 0;
-  b.stats.launches += 1 + 1 + 7;
+  b.stats.launches += 1 + 1 + 7 + irls_kernels(b);
   const int rj = join_out(b);
   return rc ? rc : rj;
 }
@@ -518,7 +529,7 @@ int irtps_batch_iterate(irtps_batch *x, int n_iter, const int *spp, const int *b
   }
   rc = end_call(b, true, n_iter, out_dH);
   {  // kernels per iteration: pyramid levels, trace, PS, seven of the solve, two of D_H (+ counter)
-    int k = 1 + 1 + 7 + 2 + (b.use_graph ? 1 : 0) + (b.shared ? 2 : 0);
+    int k = 1 + 1 + 7 + 2 + (b.use_graph ? 1 : 0) + (b.shared ? 2 : 0) + irls_kernels(b);
     for (int l = 0; l < b.pyr_levels; ++l) k += b.pyr_blocks[l] > 0 ? 1 : 0;
     b.stats.launches += (unsigned long long)k * n_iter;
   }

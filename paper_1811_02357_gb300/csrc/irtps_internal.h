@@ -207,7 +207,8 @@ int cg_grid_limit();  // co-resident blocks available to the cooperative solve
 size_t cg_job_bytes();
 void cg_fill_job(Ctx &c, int nblk, int blk_begin, DevStats *ds, void *dst);
 int cg_batch_grid_limit();
-cudaError_t solve_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks);
+cudaError_t solve_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks, int irls_iters,
+                                    int max_levels);
 cudaError_t depth_change_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks);
 cudaError_t zero_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks);
 void mg_layout(int H, int W, int *levels, int *h, int *w, int *off, int *total);

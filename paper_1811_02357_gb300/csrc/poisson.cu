@@ -843,8 +843,8 @@ __global__ void k_dh_final(const CG g, DevStats *ds) { dh_final_body(g, ds); }
 // edge the slope residual u = (x_b - x_a) / h - (s_a + s_b) / 2 (FP64) gives
 // w = 1 if |u| <= delta, else delta / |u|; written as the level-0 edge weights of
 // the multigrid pool (zero on the last column / row, as the unit weights).
-__global__ void __launch_bounds__(kThreads) k_irls_weights(const CG g, float *wh, float *wv, double delta) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.P; p += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void irls_weights_body(const CG &g, float *wh, float *wv, double delta, Team t) {
+  for (int p = t.bid * blockDim.x + threadIdx.x; p < g.P; p += t.nblk * blockDim.x) {
     const int i = p / g.W, j = p - i * g.W;
     double pc, qc, pn, qn;
     slopes(g.nrm, p, g.nz_min, pc, qc);
@@ -866,11 +866,11 @@ __global__ void __launch_bounds__(kThreads) k_irls_weights(const CG g, float *wh
 
 // Galerkin weights of level l+1 from level l (2x2 aggregates): the sum of the fine
 // edge weights crossing between two aggregates (the host's construction, on the device).
-__global__ void __launch_bounds__(kThreads) k_mg_coarsen(const MG m, int l, float *wh, float *wv) {
+__device__ __forceinline__ void mg_coarsen_body(const MG &m, int l, float *wh, float *wv, Team t) {
   const int Hf = m.H[l], Wf = m.W[l], Hc = m.H[l + 1], Wc = m.W[l + 1];
   const float *fh = wh + m.off[l], *fv = wv + m.off[l];
   float *ch = wh + m.off[l + 1], *cv = wv + m.off[l + 1];
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Hc * Wc; q += gridDim.x * blockDim.x) {
+  for (int q = t.bid * blockDim.x + threadIdx.x; q < Hc * Wc; q += t.nblk * blockDim.x) {
     const int I = q / Wc, J = q - I * Wc;
     float sh = 0.0f, sv = 0.0f;
     if (2 * J + 2 < Wf)
@@ -880,6 +880,13 @@ __global__ void __launch_bounds__(kThreads) k_mg_coarsen(const MG m, int l, floa
     ch[q] = sh;
     cv[q] = sv;
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_irls_weights(const CG g, float *wh, float *wv, double delta) {
+  irls_weights_body(g, wh, wv, delta, whole_grid());
+}
+__global__ void __launch_bounds__(kThreads) k_mg_coarsen(const MG m, int l, float *wh, float *wv) {
+  mg_coarsen_body(m, l, wh, wv, whole_grid());
 }
 
 // One depth solve, enqueued without host round trips: right-hand side, warm
@@ -970,10 +977,16 @@ struct CGJob {
   double tol;
   int max_iter, check, pre;
   int blk_begin;
+  // robust integration (IRLS): the object's writable level-0.. weights, their unit copy, threshold
+  float *wh, *wv;
+  const float *wh_unit, *wv_unit;
+  int mg_total;
+  float irls_delta;
 };
 
-// Copy the job of this block's team into shared memory and run body(job, team).
-template <typename F>
+// Copy the job of this block's team into shared memory and run body(job, team)
+// (PLAIN: with the unscaled coarse-grid correction of the weighted solves).
+template <bool PLAIN = false, typename F>
 __device__ __forceinline__ void for_team(const CGJob *__restrict__ jobs, int n, F &&body) {
   __shared__ CGJob sj;
   __shared__ int s_bid;
@@ -984,29 +997,33 @@ __device__ __forceinline__ void for_team(const CGJob *__restrict__ jobs, int n, 
       if (jobs[mid].blk_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
     }
     sj = jobs[lo];
+    if (PLAIN) sj.mg.cscale = 1.0f;
     s_bid = (int)blockIdx.x - jobs[lo].blk_begin;
   }
   __syncthreads();
   body(sj, Team{s_bid, sj.g.nblk});
 }
 
+template <bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads) k_rhs_b(const CGJob *jobs, int n) {
-  for_team(jobs, n, [](const CGJob &j, Team t) { rhs_body<false>(j.g, t); });
+  for_team(jobs, n, [](const CGJob &j, Team t) { rhs_body<WEIGHTED>(j.g, t); });
 }
 __global__ void __launch_bounds__(kThreads) k_load_x_b(const CGJob *jobs, int n) {
   for_team(jobs, n, [](const CGJob &j, Team t) { load_x_body(j.g, t); });
 }
+template <bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads) k_residual_b(const CGJob *jobs, int n) {
-  for_team(jobs, n, [](const CGJob &j, Team t) { residual_body<false>(j.g, S_RZ0, t); });
+  for_team(jobs, n, [](const CGJob &j, Team t) { residual_body<WEIGHTED>(j.g, S_RZ0, t); });
 }
 // one warp per job
 __global__ void k_cg_start_b(const CGJob *jobs) { cg_start_body(jobs[blockIdx.x].g, jobs[blockIdx.x].ctl); }
+template <bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads, IRTPS_CG_BATCH_MINB) k_cg_loop_b(const CGJob *jobs, int n) {
-  for_team(jobs, n, [](const CGJob &j, Team t) {
+  for_team<WEIGHTED>(jobs, n, [](const CGJob &j, Team t) {
     if (j.pre == 1)
-      cg_loop_body<1, false>(j.g, j.ctl, &j.ds->cg, j.tol, j.max_iter, j.check, j.mg, t);
+      cg_loop_body<1, WEIGHTED>(j.g, j.ctl, &j.ds->cg, j.tol, j.max_iter, j.check, j.mg, t);
     else
-      cg_loop_body<0, false>(j.g, j.ctl, &j.ds->cg, j.tol, j.max_iter, j.check, j.mg, t);
+      cg_loop_body<0, WEIGHTED>(j.g, j.ctl, &j.ds->cg, j.tol, j.max_iter, j.check, j.mg, t);
   });
 }
 __global__ void __launch_bounds__(kThreads) k_sum_x_b(const CGJob *jobs, int n) {
@@ -1019,6 +1036,22 @@ __global__ void __launch_bounds__(kThreads) k_depth_change_b(const CGJob *jobs, 
   for_team(jobs, n, [](const CGJob &j, Team t) { depth_change_body(j.g, j.old, t); });
 }
 __global__ void k_dh_final_b(const CGJob *jobs) { dh_final_body(jobs[blockIdx.x].g, jobs[blockIdx.x].ds); }
+__global__ void __launch_bounds__(kThreads) k_irls_weights_b(const CGJob *jobs, int n) {
+  for_team(jobs, n, [](const CGJob &j, Team t) { irls_weights_body(j.g, j.wh, j.wv, (double)j.irls_delta, t); });
+}
+__global__ void __launch_bounds__(kThreads) k_mg_coarsen_b(const CGJob *jobs, int n, int l) {
+  for_team(jobs, n, [l](const CGJob &j, Team t) {
+    if (l + 1 < j.mg.levels) mg_coarsen_body(j.mg, l, j.wh, j.wv, t);
+  });
+}
+__global__ void __launch_bounds__(kThreads) k_unit_weights_b(const CGJob *jobs, int n) {
+  for_team(jobs, n, [](const CGJob &j, Team t) {
+    for (int q = t.bid * blockDim.x + threadIdx.x; q < j.mg_total; q += t.nblk * blockDim.x) {
+      j.wh[q] = j.wh_unit[q];
+      j.wv[q] = j.wv_unit[q];
+    }
+  });
+}
 __global__ void __launch_bounds__(kThreads) k_zero_depth_b(const CGJob *jobs, int n) {
   for_team(jobs, n, [](const CGJob &j, Team t) {
     for (int p = t.bid * blockDim.x + threadIdx.x; p < j.g.P; p += t.nblk * blockDim.x) j.g.depth[p] = 0.0f;
@@ -1032,7 +1065,10 @@ int cg_batch_grid_limit() {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_loop_b, kThreads, 0) != cudaSuccess) return 0;
+  int per_w = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_loop_b<false>, kThreads, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_w, k_cg_loop_b<true>, kThreads, 0) != cudaSuccess) return 0;
+  per = per < per_w ? per : per_w;
   per = per < IRTPS_CG_BATCH_BLOCKS_PER_SM ? per : IRTPS_CG_BATCH_BLOCKS_PER_SM;
   return per * sms;
 }
@@ -1051,21 +1087,47 @@ void cg_fill_job(Ctx &c, int nblk, int blk_begin, DevStats *ds, void *dst) {
   j.check = c.opt.cg_check_every > 0 ? c.opt.cg_check_every : 10;
   j.pre = c.opt.precond == 1 ? 1 : 0;
   j.blk_begin = blk_begin;
+  j.wh = c.mg_wh;
+  j.wv = c.mg_wv;
+  j.wh_unit = c.mg_wh_unit;
+  j.wv_unit = c.mg_wv_unit;
+  j.mg_total = c.mg_total;
+  j.irls_delta = c.opt.irls_delta;
   std::memcpy(dst, &j, sizeof(j));
 }
 
-cudaError_t solve_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks) {
-  const CGJob *jobs = (const CGJob *)d_jobs;
-  k_rhs_b<<<blocks, kThreads, 0, s>>>(jobs, n);
+template <bool WEIGHTED>
+static cudaError_t solve_batch_once(cudaStream_t s, const CGJob *jobs, int n, int blocks) {
+  k_rhs_b<WEIGHTED><<<blocks, kThreads, 0, s>>>(jobs, n);
   k_load_x_b<<<blocks, kThreads, 0, s>>>(jobs, n);
-  k_residual_b<<<blocks, kThreads, 0, s>>>(jobs, n);
+  k_residual_b<WEIGHTED><<<blocks, kThreads, 0, s>>>(jobs, n);
   k_cg_start_b<<<n, 32, 0, s>>>(jobs);
   LAUNCH_CHECK();
   void *args[] = {(void *)&jobs, (void *)&n};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_cg_loop_b, dim3(blocks), dim3(kThreads), args, 0, s);
+  cudaError_t e =
+      cudaLaunchCooperativeKernel((const void *)k_cg_loop_b<WEIGHTED>, dim3(blocks), dim3(kThreads), args, 0, s);
   if (e != cudaSuccess) return e;
   k_sum_x_b<<<blocks, kThreads, 0, s>>>(jobs, n);
   k_store_depth_b<<<blocks, kThreads, 0, s>>>(jobs, n);
+  LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+// The batched solves; with irls_iters > 0 (the same for every object) each is
+// followed by that many reweighting steps of the Huber M-estimator, as in the
+// single-object solve, and the unit weights are put back at the end.
+cudaError_t solve_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks, int irls_iters,
+                                    int max_levels) {
+  const CGJob *jobs = (const CGJob *)d_jobs;
+  cudaError_t e = solve_batch_once<false>(s, jobs, n, blocks);
+  if (e != cudaSuccess || irls_iters <= 0) return e;
+  for (int it = 0; it < irls_iters; ++it) {
+    k_irls_weights_b<<<blocks, kThreads, 0, s>>>(jobs, n);
+    for (int l = 0; l + 1 < max_levels; ++l) k_mg_coarsen_b<<<blocks, kThreads, 0, s>>>(jobs, n, l);
+    LAUNCH_CHECK();
+    if ((e = solve_batch_once<true>(s, jobs, n, blocks)) != cudaSuccess) return e;
+  }
+  k_unit_weights_b<<<blocks, kThreads, 0, s>>>(jobs, n);
   LAUNCH_CHECK();
   return cudaSuccess;
 }

@@ -207,3 +207,50 @@ def test_batch_set_images_matches_single(lib, oracle_mod):
     finally:
         for c in ctxs:
             c.close()
+
+
+def test_batch_robust_integration(lib, oracle_mod):
+    """Objects with robust integration (Huber IRLS, the same number of reweighting steps,
+    their own thresholds) in one batch: iteration 0 gives each object's own normals bit for
+    bit and its surface within the solver's tolerance; a batched iteration matches the
+    oracle's robust loop."""
+    scs = _scenes(SMALL)
+    A = _images(oracle_mod, scs, 23)
+    deltas = [0.05, 0.08, 0.05, 0.03]
+    ctxs = []
+    for sc, dl in zip(scs, deltas):
+        opt = lib.irtps_default_options()
+        opt.irls_iters = 2
+        opt.irls_delta = dl
+        ctxs.append(lib.Context(sc.H, sc.W, sc.lights, sc.env, opt))
+    spp = [s[4] for s in SMALL]
+    bounces = [s[5] for s in SMALL]
+    try:
+        with lib.Batch(ctxs) as b:
+            b.set_images(A)
+            assert b.stats()["cg_rel_residual"] <= 1e-9
+            got0 = [(c.normals(), c.depth()) for c in ctxs]
+            b.iterate(1, spp, bounces, 7)
+            assert b.stats()["cg_rel_residual"] <= 1e-9
+            got1 = [(c.normals(), c.depth()) for c in ctxs]
+        for i, (sc, a, dl) in enumerate(zip(scs, A, deltas)):
+            opt = lib.irtps_default_options()
+            opt.irls_iters = 2
+            opt.irls_delta = dl
+            with lib.Context(sc.H, sc.W, sc.lights, sc.env, opt) as c:
+                c.set_images(a)
+                assert np.array_equal(got0[i][0], c.normals()), i
+                d = c.depth()
+                assert np.abs(got0[i][1] - d).max() <= 1e-5 * np.ptp(d), i
+            hist = oracle_mod.irtps_run(a, sc.lights, sc.env, 1, spp[i], bounces[i], 7, obj=i, irls_iters=2,
+                                        irls_delta=dl)
+            err = oracle_mod.angular_error_deg(got1[i][0][..., :3].reshape(-1, 3), hist[1]["normals"].reshape(-1, 3))
+            dabs = np.abs(got1[i][1] - hist[1]["depth"]) / np.ptp(hist[1]["depth"])
+            assert err.mean() <= 0.05 and dabs.mean() <= 1e-4 and dabs.max() <= 1e-3, (i, err.mean(), dabs.max())
+        mixed = [lib.Context(scs[0].H, scs[0].W, scs[0].lights, scs[0].env)]
+        with pytest.raises(lib.IrtpsError):  # reweighting steps must agree across the batch
+            lib.Batch([ctxs[0], mixed[0]])
+        mixed[0].close()
+    finally:
+        for c in ctxs:
+            c.close()
