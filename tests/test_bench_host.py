@@ -1,0 +1,45 @@
+"""Host-side parts of bench.py and the workload recipes (no GPU).
+
+* The evaluation errors the benchmark reports equal the oracle's definitions of the
+  paper's evaluation measures (height, albedo and normal error), on random estimates.
+* The batched workload follows its recipe: 64 objects, sides log-uniform in 96..1024,
+  K in {4, 8, 16, 32}, spp in {64, 128, 256}, bounces in {1, 2}.
+"""
+import os
+import sys
+
+import numpy as np
+
+import scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_evaluation_errors_match_oracle(oracle_mod):
+    sys.path.insert(0, ROOT)
+    import bench
+    sc = scenes.mixed(12, 21, 17, K=4, C=3)
+    rng = np.random.default_rng(3)
+    depth = (sc.depth + rng.normal(0, 0.01, sc.depth.shape)).astype(np.float32)
+    n = sc.normals + rng.normal(0, 0.05, sc.normals.shape)
+    n = (n / np.linalg.norm(n, axis=-1, keepdims=True)).astype(np.float32)
+    n4 = np.concatenate([n, np.ones(n.shape[:2] + (1,), np.float32)], axis=-1)
+    albedo = (sc.albedo + rng.normal(0, 0.02, sc.albedo.shape)).astype(np.float32)
+    got = bench.gt_errors(sc, depth, n4, albedo)
+    assert np.isclose(got["height"], oracle_mod.height_error(sc.depth, depth), rtol=1e-12)
+    assert np.isclose(got["albedo"], oracle_mod.albedo_error(sc.albedo, albedo), rtol=1e-12)
+    assert np.isclose(got["normal"], oracle_mod.normal_error(sc.normals, n), rtol=1e-12)
+    ang = oracle_mod.angular_error_deg(sc.normals, n).mean()
+    assert np.isclose(got["normal_deg"], ang, rtol=1e-9)
+
+
+def test_batch_recipe():
+    spec = scenes.batch_spec()
+    assert len(spec) == 64
+    sides = np.array([s[1] for s in spec])
+    assert sides.min() >= 96 and sides.max() <= 1024
+    assert {s[2] for s in spec} <= {4, 8, 16, 32} and {s[3] for s in spec} <= {64, 128, 256}
+    assert {s[4] for s in spec} <= {1, 2}
+    # log-uniform: about half of the sides below the geometric mean of the range
+    assert 0.3 < (sides < np.sqrt(96 * 1024)).mean() < 0.7
+    assert len({s[0] for s in spec}) == 64  # every object its own scene seed
