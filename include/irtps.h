@@ -78,6 +78,11 @@ typedef struct irtps_options {
   int irls_iters;     /* integration by the Huber M-estimator: reweighting steps after the
                          least-squares solve (0 = least squares only) (0) */
   float irls_delta;   /* Huber threshold on the edge slope residual (H_b - H_a)/h - mean slope (0.05) */
+  int early_escape;   /* 1: before each trace, bound every pixel's horizon in eight octants of azimuth
+                         from the pyramid; a rising primary ray above it skips its march after the
+                         triangle test of its first cell (results unchanged, bit for bit).  Pays
+                         only at high sample counts: the bounds cost about as much as 20 samples
+                         per pixel and light save (0) */
 } irtps_options;
 
 /* Counters of the last irtps_iterate / irtps_trace / irtps_integrate call. */

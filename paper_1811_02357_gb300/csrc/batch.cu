@@ -41,6 +41,7 @@ struct irtps_batch {
   // launch geometry
   int pyr_levels = 0;
   std::vector<int> pyr_blocks;
+  int hz_blocks = 0;  // batched horizon launch (early escape)
   int ps_blocks = 0, cg_blocks = 0;
   unsigned n_items = 0;
   unsigned long long primary_per_iter = 0;
@@ -203,6 +204,7 @@ int upload_trace(irtps_batch &b, const int *spp, const int *bounces, uint64_t se
 int enqueue_trace(irtps_batch &b, uint32_t iter, bool captured, bool timed) {
   BSTAGE(ST_TRACE, true);
   BCK(irtps::build_pyramid_batch(b.stream, b.d_pyr, b.n, b.pyr_levels, b.pyr_blocks.data()), "pyramid launch");
+  BCK(irtps::launch_horizon_batch(b.stream, b.d_pyr, b.n, b.hz_blocks), "horizon bounds");
   if (b.shared) BCK(irtps::launch_parts_batch(b.stream, true, b.d_reduce, b.n, b.reduce_blocks), "partial sums");
   BCK(irtps::launch_trace_batch(b.stream, b.C, b.shared, b.d_trace, b.n, b.n_items, b.d_stats[b.n].counts,
                                 b.next_item, captured ? b.iter_dev : nullptr, iter, trace_grid(b)),
@@ -417,6 +419,10 @@ int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int
     irtps::fill_pyr_obj(objs[i]->c, pyr[i]);
     b.pyr_levels = std::max(b.pyr_levels, objs[i]->c.levels);
   }
+  for (int i = 0; i < n_obj; ++i) {  // horizon bounds: 128 pixels per block for objects that keep them
+    pyr[i].hz_blk = b.hz_blocks;
+    if (pyr[i].hz) b.hz_blocks += (objs[i]->c.H * objs[i]->c.W + 127) / 128;
+  }
   b.pyr_blocks.assign(b.pyr_levels, 0);
   for (int l = 0; l < b.pyr_levels; ++l)
     for (int i = 0; i < n_obj; ++i) {
@@ -529,7 +535,8 @@ int irtps_batch_iterate(irtps_batch *x, int n_iter, const int *spp, const int *b
   }
   rc = end_call(b, true, n_iter, out_dH);
   {  // kernels per iteration: pyramid levels, trace, PS, seven of the solve, two of D_H (+ counter)
-    int k = 1 + 1 + 7 + 2 + (b.use_graph ? 1 : 0) + (b.shared ? 2 : 0) + irls_kernels(b);
+    int k = 1 + 1 + 7 + 2 + (b.use_graph ? 1 : 0) + (b.shared ? 2 : 0) + (b.hz_blocks > 0 ? 1 : 0) +
+            irls_kernels(b);
     for (int l = 0; l < b.pyr_levels; ++l) k += b.pyr_blocks[l] > 0 ? 1 : 0;
     b.stats.launches += (unsigned long long)k * n_iter;
   }

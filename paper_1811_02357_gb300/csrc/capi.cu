@@ -43,7 +43,7 @@ int dalloc(Ctx &c, T **p, size_t n, const char *what) {
 }
 
 void release(Ctx &c) {
-  void *bufs[] = {c.env, c.d_lights, c.shared_part, c.images, c.lbar, c.depth, c.depth_prev, c.nrm, c.albedo, c.valid, c.pmin, c.pmax,
+  void *bufs[] = {c.env, c.d_lights, c.horizon, c.shared_part, c.images, c.lbar, c.depth, c.depth_prev, c.nrm, c.albedo, c.valid, c.pmin, c.pmax,
                   c.cg_x, c.cg_b, c.cg_r, c.cg_z, c.cg_p, c.cg_ap, c.part, c.dstats, c.next_item, c.cg_ctl,
                   c.mg_x0, c.mg_x1, c.mg_b, c.mg_wh, c.mg_wv, c.mg_wh_unit, c.mg_wv_unit, c.iter_dev};
   for (void *b : bufs)
@@ -144,6 +144,7 @@ int trace_into(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, u
                uint32_t stream_tag, float *out, int32_t *rec, bool iter_from_device = false) {
   CK(irtps::build_pyramid(c), "pyramid build");
   if (!iter_from_device) STAGE(ST_TRACE, true);
+  CK(irtps::launch_horizon(c), "horizon bounds");
   CK(irtps::launch_trace(c, pixels, n_pix, spp, bounces, seed, iter, stream_tag, out, rec, iter_from_device),
      "trace launch");
   if (!iter_from_device) STAGE(ST_TRACE, false);
@@ -262,6 +263,7 @@ void irtps_default_options(irtps_options *opt) {
   opt->sampling = 0;
   opt->irls_iters = 0;
   opt->irls_delta = 0.05f;
+  opt->early_escape = 0;
 }
 
 int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *lights, const float *env, int EH,
@@ -359,6 +361,8 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
   c.part_stride = c.cg_blocks;
   if ((rc = dalloc(c, &c.env, (size_t)C * EH * EW, "environment")) ||
       (rc = dalloc(c, &c.d_lights, (size_t)K * 3, "lights")) ||
+      (c.opt.early_escape && H <= 16384 && W <= 16384 &&
+       (rc = dalloc(c, &c.horizon, (size_t)8 * P, "horizon bounds"))) ||
       (rc = dalloc(c, (float **)&c.images, (size_t)K * C * P, "images")) ||
       (rc = dalloc(c, &c.lbar, (size_t)K * C * P, "indirect")) || (rc = dalloc(c, &c.depth, P, "depth")) ||
       (rc = dalloc(c, &c.depth_prev, P, "depth")) || (rc = dalloc(c, &c.nrm, P, "normals")) ||

@@ -428,6 +428,33 @@ __device__ __forceinline__ bool march(const Field &f, const LevelTable &lt, F3 o
   return m.btri >= 0;
 }
 
+// ---------------------------------------------------------------------------
+// Early escape of primary rays.  For every pixel vertex p and each of the eight
+// octants of azimuth (signs of the grid direction's x and y, and whether |y|
+// exceeds |x|; the diagonals belong to both neighbours), hz bounds from above
+// the slope (height per grid unit) under which the terrain is seen from p:
+//   hz = max over cells c meeting the closed octant wedge at p, c not touching p,
+//        of (max height of c - H_p) / (distance from p to c).
+// A rising ray leaving p's lifted vertex with slope above hz is at every cell c of
+// the wedge above c's highest vertex (its height there is at least
+// H_p + dist * slope), so it can hit nothing beyond the cell it starts in.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int octant_of(float gx, float gy) {
+  return (gx < 0.0f ? 1 : 0) | (gy < 0.0f ? 2 : 0) | (fabsf(gy) > fabsf(gx) ? 4 : 0);
+}
+
+// Whether the rectangle [a1, a2] x [b1, b2] (relative to p) meets the closed wedge of octant o.
+__device__ __forceinline__ bool wedge_meets(int o, int a1, int a2, int b1, int b2) {
+  int A1 = a1, A2 = a2, B1 = b1, B2 = b2;
+  if (o & 1) { A1 = -a2; A2 = -a1; }
+  if (o & 2) { B1 = -b2; B2 = -b1; }
+  if (o & 4) {
+    int t = A1; A1 = B1; B1 = t;
+    t = A2; A2 = B2; B2 = t;
+  }
+  return A2 >= 0 && B2 >= 0 && max(B1, 0) <= A2;
+}
+
 // Nearest vertex index of a hit coordinate, ties to the lower index.
 __device__ __forceinline__ int nearest_index(float q, int n) {
   const int v = (int)ceilf(rsub(q, 0.5f));

@@ -57,6 +57,8 @@ struct ObjTrace {
   uint32_t iter0;         // added to the launch's iteration field
   float *part;            // light-shared sampling: partial sums, n_chunks x n_pix x K x C
   int n_chunks, chunk;    // light-shared sampling: sample chunks per pixel and samples per chunk
+  const float *hz;        // horizon bounds, 8 octants x H W (null: no early escape)
+  int hz_stride;          // H W
 };
 
 
@@ -81,6 +83,7 @@ struct Ctx {
   std::vector<float> h_lights;    // K*3
   std::vector<float> h_pinv;      // 3*K, (L^T L)^-1 L^T rounded to float
   float *d_lights = nullptr;      // K*3 on the device (read at trace hits)
+  float *horizon = nullptr;       // early escape: horizon bounds of every pixel, 8 x H x W (option)
   float *shared_part = nullptr;   // light-shared trace: partial sums of its sample chunks
   size_t shared_cap = 0;          // floats in shared_part
 
@@ -161,13 +164,17 @@ struct PyrObj {
   int H, W, levels;
   int off[kMaxLevels], lw[kMaxLevels], lh[kMaxLevels];
   int blk[kMaxLevels];  // first block of the object in the launch of each level
+  float *hz;            // horizon bounds (null: none)
+  int hz_blk;           // first block of the object in the batched horizon launch
 };
 constexpr int kPyrThreads = 256;
 
 // trace.cu
 cudaError_t build_pyramid(Ctx &c);
+cudaError_t launch_horizon(Ctx &c);  // horizon bounds of the current surface (after the pyramid)
 void fill_pyr_obj(const Ctx &c, PyrObj &o);
 cudaError_t build_pyramid_batch(cudaStream_t s, const PyrObj *d_objs, int n, int levels, const int *blocks);
+cudaError_t launch_horizon_batch(cudaStream_t s, const PyrObj *d_objs, int n, int blocks);
 cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
                          uint32_t iter, uint32_t stream, float *out, int32_t *rec, bool iter_from_device = false);
 cudaError_t launch_next_iter(Ctx &c);  // iter_dev += 1 (end of a captured iteration)

@@ -93,6 +93,8 @@ __global__ void k_pyramid_b(const PyrObj *__restrict__ objs, int n, int l) {
 }
 
 void fill_pyr_obj(const Ctx &c, PyrObj &o) {
+  o.hz = c.horizon;
+  o.hz_blk = 0;
   o.depth = c.depth;
   o.prev = c.depth_prev;
   o.pmin = c.pmin;
@@ -130,6 +132,134 @@ cudaError_t build_pyramid(Ctx &c) {
                                                c.lh[l - 1], c.pmin + c.off[l], c.pmax + c.off[l], c.lw[l],
                                                c.lh[l]);
   }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Horizon bounds (see octant_of in geom.cuh): one thread per pixel, a depth-first
+// branch-and-bound over the max pyramid for all eight octants at once.  A node
+// at distance d from p (d > 0) bounds every cell in it by (node max - H_p) / d; it
+// is opened only while that exceeds the best bound found so far in some octant it
+// meets.  FP32 with every rounding directed toward a larger bound.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void horizon_pixel(const float *__restrict__ depth, const float *__restrict__ pmax,
+                                              const int *off, const int *lw, int H, int W, int levels, int p,
+                                              float *__restrict__ hz) {
+  const int P = H * W, Wc = W - 1, Hc = H - 1;
+  const int pi = p / W, pj = p - pi * W;
+  const float zp = __ldg(depth + p);
+  float best[8];
+#pragma unroll
+  for (int o = 0; o < 8; ++o) best[o] = -INFINITY;
+  unsigned stack[64];  // level << 28 | ny << 14 | nx
+  int top = 0;
+  bool full = false;  // the stack ran out: no bound for this pixel
+  stack[top++] = (unsigned)(levels - 1) << 28;
+  while (top > 0) {
+    const unsigned e = stack[--top];
+    const int l = (int)(e >> 28), ny = (int)((e >> 14) & 0x3FFF), nx = (int)(e & 0x3FFF);
+    const int X0 = nx << l, Y0 = ny << l;
+    const int X1 = min(X0 + (1 << l), Wc), Y1 = min(Y0 + (1 << l), Hc);
+    const int a1 = X0 - pj, a2 = X1 - pj, b1 = Y0 - pi, b2 = Y1 - pi;
+    const int dx = max(max(a1, -a2), 0), dy = max(max(b1, -b2), 0);
+    bool meets[8], any = false;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      meets[o] = wedge_meets(o, a1, a2, b1, b2);
+      any = any || meets[o];
+    }
+    if (!any) continue;
+    const float nmax = __ldg(pmax + off[l] + ny * lw[l] + nx);
+    if (dx == 0 && dy == 0) {  // the node touches p: no bound from it, look inside (cells touching p are left out)
+      if (l == 0) continue;
+    } else {
+      // (nmax - zp) / distance, every rounding toward a larger bound
+      const float num = __fsub_ru(nmax, zp);
+      const float d2 = __fmaf_ru((float)dx, (float)dx, __fmul_ru((float)dy, (float)dy));
+      const float dist = num >= 0.0f ? __fsqrt_rd(__fmaf_rd((float)dx, (float)dx, __fmul_rd((float)dy, (float)dy)))
+                                     : __fsqrt_ru(d2);
+      const float bnd = __fdiv_ru(num, dist);
+      bool open = false;
+#pragma unroll
+      for (int o = 0; o < 8; ++o) open = open || (meets[o] && bnd > best[o]);
+      if (!open) continue;
+      if (l == 0) {
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+          if (meets[o]) best[o] = fmaxf(best[o], bnd);
+        continue;
+      }
+    }
+    // children, the farthest pushed first so that the nearest is opened first
+    const int cl = l - 1, cw = ((Wc - 1) >> cl) + 1, ch = ((Hc - 1) >> cl) + 1;
+    unsigned kid[4];
+    int kd[4], nk = 0;
+    for (int q = 0; q < 4; ++q) {
+      const int cx = 2 * nx + (q & 1), cy = 2 * ny + (q >> 1);
+      if (cx >= cw || cy >= ch) continue;
+      const int u1 = (cx << cl) - pj, u2 = min((cx + 1) << cl, Wc) - pj;
+      const int v1 = (cy << cl) - pi, v2 = min((cy + 1) << cl, Hc) - pi;
+      const int ddx = max(max(u1, -u2), 0), ddy = max(max(v1, -v2), 0);
+      kid[nk] = ((unsigned)cl << 28) | ((unsigned)cy << 14) | (unsigned)cx;
+      kd[nk] = ddx * ddx + ddy * ddy;
+      ++nk;
+    }
+    for (int a = 1; a < nk; ++a)  // sort by distance, nearest last
+      for (int b2i = a; b2i > 0 && kd[b2i] > kd[b2i - 1]; --b2i) {
+        const int td = kd[b2i]; kd[b2i] = kd[b2i - 1]; kd[b2i - 1] = td;
+        const unsigned tk = kid[b2i]; kid[b2i] = kid[b2i - 1]; kid[b2i - 1] = tk;
+      }
+    if (top + nk > 64) {
+      full = true;
+      break;
+    }
+    for (int a = 0; a < nk; ++a) stack[top++] = kid[a];
+  }
+#pragma unroll
+  for (int o = 0; o < 8; ++o) hz[(size_t)o * P + p] = full ? INFINITY : best[o];
+}
+
+// levels: of the full pyramid (its top node covers the grid), whatever the march uses.
+__global__ void k_horizon(const Field f, int levels, float *__restrict__ hz) {
+  __shared__ int s_off[kMaxLevels], s_lw[kMaxLevels];
+  if (threadIdx.x < kMaxLevels) {
+    s_off[threadIdx.x] = f.off[threadIdx.x];
+    s_lw[threadIdx.x] = f.lw[threadIdx.x];
+  }
+  __syncthreads();
+  const int P = f.H * f.W;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+    horizon_pixel(f.depth, f.pmax, s_off, s_lw, f.H, f.W, levels, p, hz);
+}
+
+// Batched: object o owns blocks [hz_blk of o, hz_blk of o + 1) (128 pixels each).
+__global__ void k_horizon_b(const PyrObj *__restrict__ objs, int n) {
+  __shared__ int s_o;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (objs[mid].hz_blk <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    s_o = lo;
+  }
+  __syncthreads();
+  const PyrObj &o = objs[s_o];
+  if (!o.hz) return;
+  const int p = ((int)blockIdx.x - o.hz_blk) * blockDim.x + threadIdx.x;
+  if (p < o.H * o.W) horizon_pixel(o.depth, o.pmax, o.off, o.lw, o.H, o.W, o.levels, p, o.hz);
+}
+
+cudaError_t launch_horizon(Ctx &c) {
+  if (!c.horizon) return cudaSuccess;
+  const int P = c.H * c.W;
+  k_horizon<<<(P + 127) / 128, 128, 0, c.stream>>>(c.field(), c.levels, c.horizon);
+  ++c.stats.launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_horizon_batch(cudaStream_t s, const PyrObj *d_objs, int n, int blocks) {
+  if (blocks > 0) k_horizon_b<<<blocks, 128, 0, s>>>(d_objs, n);
   return cudaGetLastError();
 }
 
@@ -435,11 +565,27 @@ __global__ void __launch_bounds__(kTraceThreads,
       const F3 org = b == 1 ? pixel_origin() : m.o;
       const float4 n4 = __ldg(ob->nrm + (b == 1 ? p : qp));
       const F3 dw = cosine_dir(F3{n4.x, n4.y, n4.z}, x.x, x.y);
-      walker_init(m, org, F3{rmul(dw.x, ob->Wf), rmul(dw.y, ob->Wf), dw.z}, false);
+      const F3 dg = {rmul(dw.x, ob->Wf), rmul(dw.y, ob->Wf), dw.z};
+      walker_init(m, org, dg, false);
       shadow = false;
       ++segs;
       ++w.draws;
       phase = PH_MARCH;
+      // early escape: a rising primary ray steeper than the pixel's horizon in its octant
+      // misses everything beyond its first cell; that cell gets its own triangle test
+      if (b == 1 && ob->hz && dg.z > 0.0f && dg.x != 0.0f && dg.y != 0.0f) {
+        const float slope = dg.z / sqrtf(dg.x * dg.x + dg.y * dg.y);
+        const float hz = __ldg(ob->hz + (size_t)octant_of(dg.x, dg.y) * ob->hz_stride + p);
+        if (slope > hz + 1e-5f * fabsf(hz) + 1e-7f) {
+          if ((unsigned)m.cx >= (unsigned)ob->f.Wc || (unsigned)m.cy >= (unsigned)ob->f.Hc) {
+            phase = PH_RESOLVE;  // leaves the grid at once
+          } else {
+            test_cell(ob->f, m.cy, m.cx, m.o, m.d, m.bt, m.btri, w);
+            if (m.btri < 0) phase = PH_RESOLVE;
+            else m.bt = __int_as_float(0x7f800000), m.btri = -1;  // a hit there: the plain march decides
+          }
+        }
+      }
     }
     const unsigned live = __ballot_sync(0xffffffffu, phase != PH_DONE);  // no lane finishes inside the march loop
     if (live == 0u) break;
@@ -591,6 +737,8 @@ void fill_obj_trace(const Ctx &c, ObjTrace &o) {
   o.part = nullptr;
   o.n_chunks = 1;
   o.chunk = 0;
+  o.hz = c.horizon;
+  o.hz_stride = c.H * c.W;
 }
 
 __global__ void k_next_iter(uint32_t *iter) { *iter += 1u; }

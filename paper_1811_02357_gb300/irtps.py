@@ -44,7 +44,7 @@ class irtps_options(ctypes.Structure):
                 ("cond_max", ctypes.c_double), ("nz_min", ctypes.c_float), ("cg_tol", ctypes.c_double),
                 ("cg_max_iter", ctypes.c_int), ("cg_check_every", ctypes.c_int), ("stop_tol", ctypes.c_double),
                 ("precond", ctypes.c_int), ("use_graph", ctypes.c_int), ("sampling", ctypes.c_int),
-                ("irls_iters", ctypes.c_int), ("irls_delta", ctypes.c_float)]
+                ("irls_iters", ctypes.c_int), ("irls_delta", ctypes.c_float), ("early_escape", ctypes.c_int)]
 
 
 class irtps_stats(ctypes.Structure):

@@ -133,3 +133,23 @@ def test_without_shadow_rays(lib, oracle_mod):
     assert (rec[..., 1] == 0).sum() == 0  # nothing is ever shadowed
     ok, worst = rel_close(lb, want, RTOL, 1e-7)
     assert ok, worst
+
+
+@pytest.mark.parametrize("case", ["mixed_45x38_c3", "mixed_33x70_c1", "bowl64_c1"])
+def test_early_escape_keeps_every_bit(lib, oracle_mod, case):
+    """The horizon test lets rising primary rays skip their march; records, Lbar and segment
+    counts are those of the plain march, with fewer node visits."""
+    sc = CASES[case]()
+    out = []
+    for early in (0, 1):
+        opt = lib.irtps_default_options()
+        opt.early_escape = early
+        with lib.Context(sc.H, sc.W, sc.lights, sc.env, opt) as ctx:
+            ctx.set_state(sc.depth, sc.normals, sc.albedo)
+            lb, rec = ctx.trace_pixels(np.arange(sc.H * sc.W, dtype=np.int32), 16, 2, 5, 3, records=True)
+            ctx.trace(16, 2, 5, 3)
+            out.append((lb, rec, ctx.indirect(), ctx.stats()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
+    assert out[0][3]["segments"] == out[1][3]["segments"]
+    assert out[1][3]["node_visits"] < out[0][3]["node_visits"]
