@@ -65,7 +65,7 @@ SM_COUNT = 152
 LANES_PER_SM = 128
 # DRAM bytes (read + write) of one trace launch of a workload, from the ncu capture summarised in
 # profiles/k_trace_bumps512_dram.md (the kernel has not changed since)
-TRACE_DRAM_BYTES = {"bumps_512": 10.50e6 + 1.65e6}
+TRACE_DRAM_BYTES = {"bumps_512": 10.24e6 + 1.79e6}
 
 
 def sm_max_mhz():
