@@ -44,6 +44,8 @@ WORKLOADS = {
     "bowl_64": ("bowl_64", {}, 64, 1, 3, 256, 1),
     # a small case of the same kernels for profiler captures (one IRT iteration per job)
     "bumps_256_profile": ("bumps_512", {"H": 256, "W": 256}, 32, 2, 1, 32, 2),
+    # the 2048x2048, K = 32 configuration at an eighth of its samples (64 spp), one IRT iteration per job
+    "bumps_2048_spp64": ("bumps_2048", {}, 64, 2, 1, 4, 1),
     # the 4096x4096, K = 64 configuration at a sixty-fourth of its samples (16 spp), one IRT iteration per job
     "bumps_4096_spp16": ("bumps_4096", {}, 16, 2, 1, 4, 1),
     # the batched pattern: 64 objects (sides 96..1024, K, spp, bounces per object), one IRT
