@@ -68,6 +68,8 @@ LANES_PER_SM = 128
 # DRAM bytes (read + write) of one trace launch of a workload, from the ncu capture summarised in
 # profiles/k_trace_bumps512_dram.md (the kernel has not changed since)
 TRACE_DRAM_BYTES = {"bumps_512": 10.24e6 + 1.79e6}
+# the same for light-shared sampling (profiles/k_trace_shared_bumps512_dram.md)
+TRACE_DRAM_BYTES_SHARED = {"bumps_512": 162.67e6 + 116.86e6}
 
 
 def sm_max_mhz():
@@ -569,7 +571,8 @@ def main():
     achieved = ops / (tot["trace_ms"] / 1e3) / 1e12
     peak = SM_COUNT * LANES_PER_SM * mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": TRACE_DRAM_BYTES.get(args.workload) if args.sampling == "per_light" else None,
+                "traffic": (TRACE_DRAM_BYTES if args.sampling == "per_light" else
+                            TRACE_DRAM_BYTES_SHARED).get(args.workload),
                 "kernel": "k_trace",
                 "launch_ms": tot["trace_ms"] / trace_launches,
                 "note": "lane-operation issue peak = 152 SMs x 128 lanes x max SM clock; ops counted per "
