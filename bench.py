@@ -69,7 +69,7 @@ LANES_PER_SM = 128
 # profiles/k_trace_bumps512_dram.md (the kernel has not changed since)
 TRACE_DRAM_BYTES = {"bumps_512": 10.24e6 + 1.79e6}
 # the same for light-shared sampling (profiles/k_trace_shared_bumps512_dram.md)
-TRACE_DRAM_BYTES_SHARED = {"bumps_512": 162.67e6 + 116.86e6}
+TRACE_DRAM_BYTES_SHARED = {"bumps_512": 322.63e6 + 270.69e6}
 
 
 def sm_max_mhz():

@@ -131,8 +131,7 @@ int upload_trace(irtps_batch &b, const int *spp, const int *bounces, uint64_t se
   auto cost = [&](int i) -> long long {  // samples x bounces of one work item (x K when shared)
     const Ctx &c = b.objs[i]->c;
     if (!b.shared) return (long long)spp[i] * bounces[i];
-    const int nc = irtps::shared_chunks(c.H * c.W, spp[i]);
-    return (long long)((spp[i] + nc - 1) / nc) * bounces[i] * c.K;
+    return (long long)irtps::shared_split(c.H * c.W, spp[i]).chunk * bounces[i] * c.K;
   };
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
   std::vector<irtps::ObjTrace> h(b.n);
@@ -156,10 +155,11 @@ int upload_trace(irtps_batch &b, const int *spp, const int *bounces, uint64_t se
     o.iter0 = c.t;
     unsigned long long n_it = (unsigned long long)P * c.K;
     if (b.shared) {  // (chunk, pixel) items; partial sums in the object's scratch
-      o.n_chunks = irtps::shared_chunks(P, spp[i]);
-      o.chunk = (spp[i] + o.n_chunks - 1) / o.n_chunks;
+      const irtps::SharedSplit sp = irtps::shared_split(P, spp[i]);
+      o.n_chunks = sp.n_chunks;
+      o.chunk = sp.chunk;
       bool g = false;
-      BCK(irtps::ensure_shared_scratch(c, (size_t)o.n_chunks * c.K * c.C * P, g), "light-shared partial sums");
+      BCK(irtps::ensure_shared_scratch(c, (size_t)o.n_chunks * (c.K + 1) * c.C * P, g), "light-shared partial sums");
       grown = grown || g;
       o.part = c.shared_part;
       n_it = (unsigned long long)P * o.n_chunks;
@@ -169,6 +169,7 @@ int upload_trace(irtps_batch &b, const int *spp, const int *bounces, uint64_t se
       q.n_chunks = o.n_chunks;
       q.n_pix = P;
       q.kc = c.K * c.C;
+      q.C = c.C;
       q.inv_spp = 1.0 / (double)spp[i];
       q.blk_begin = rblk;
       q.nblk = (int)std::min<long long>(4096, std::max<long long>(1, ((long long)P * q.kc + 2047) / 2048));

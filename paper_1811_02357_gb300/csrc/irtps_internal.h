@@ -55,7 +55,7 @@ struct ObjTrace {
   float eps, Wf;          // ray-origin lift; W (grid units per world unit in x and y)
   unsigned item_begin;    // first work item of the object (batched launches)
   uint32_t iter0;         // added to the launch's iteration field
-  float *part;            // light-shared sampling: partial sums, n_chunks x n_pix x K x C
+  float *part;            // light-shared sampling: partial sums, n_chunks x n_pix x K x C, then n_chunks x n_pix x C
   int n_chunks, chunk;    // light-shared sampling: sample chunks per pixel and samples per chunk
   const float *hz;        // horizon bounds, 8 octants x H W (null: no early escape)
   int hz_stride;          // H W
@@ -181,18 +181,21 @@ cudaError_t launch_next_iter(Ctx &c);  // iter_dev += 1 (end of a captured itera
 cudaError_t launch_next_iter(cudaStream_t s, uint32_t *iter_dev);
 cudaError_t launch_render(Ctx &c, uint64_t seed, float sigma, const float *lbar, float *out);
 int trace_grid_limit(int C, int n_obj = 0);  // resident blocks of the (batched) trace kernel, 0 if unknown
-void fill_obj_trace(const Ctx &c, ObjTrace &o);
-size_t shared_scratch_floats(const Ctx &c, int n_pix, int spp);  // light-shared chunk partials needed  // descriptor of a context's object (no sampling fields)
+void fill_obj_trace(const Ctx &c, ObjTrace &o);  // descriptor of a context's object (no sampling fields)
+size_t shared_scratch_floats(const Ctx &c, int n_pix, int spp);  // light-shared chunk partials needed
 cudaError_t launch_trace_batch(cudaStream_t s, int C, bool shared, const ObjTrace *d_objs, int n_obj,
                                unsigned n_items, unsigned long long *counts, unsigned *next_item,
                                const uint32_t *iter_dev, uint32_t iter, int grid_limit);
 // light-shared sampling: sample chunks per pixel (fixed by the sizes), scratch, batched zero / reduce
-int shared_chunks(int n_pix, int spp);
+struct SharedSplit {
+  int n_chunks, chunk;  // as in ObjTrace
+};
+SharedSplit shared_split(int n_pix, int spp);
 cudaError_t ensure_shared_scratch(Ctx &c, size_t need, bool &grown);
 struct ReduceObj {
-  float *part;     // n_chunks x n_pix x kc partial sums
+  float *part;     // n_chunks x n_pix x kc light partial sums, then n_chunks x n_pix x C environment sums
   float *out;      // kc x n_pix (Lbar)
-  int n_chunks, n_pix, kc;
+  int n_chunks, n_pix, kc, C;
   double inv_spp;
   int blk_begin, nblk;
 };

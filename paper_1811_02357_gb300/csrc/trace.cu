@@ -519,11 +519,11 @@ __global__ void __launch_bounds__(kTraceThreads,
     if (need) {
       if (item_done) {
         if constexpr (SHARED) {
-          // the environment part is common to every light
-          float *d = ob->part + ((size_t)j * ob->n_pix + ip) * ob->K * C;
-          for (int kk = 0; kk < ob->K; ++kk)
+          // the environment part, common to every light, in the item's own C sums
+          // (after all chunks' light sums); the reduction adds it to each light
+          float *e = ob->part + ((size_t)ob->n_chunks * ob->n_pix * ob->K + (size_t)j * ob->n_pix + ip) * C;
 #pragma unroll
-            for (int c = 0; c < C; ++c) d[kk * C + c] += sum[c];
+          for (int c = 0; c < C; ++c) e[c] = sum[c];
         } else {
           const float inv = 1.0f / (float)ob->spp;
 #pragma unroll
@@ -703,13 +703,18 @@ __global__ void __launch_bounds__(kTraceThreads,
 
 // Light-shared traces: Lbar(k, c, p) = (sum over the sample chunks of the partial
 // sums, n_chunks x n_pix x KC with KC = K C, in chunk order, FP64) / spp.
-__global__ void k_reduce_chunks(const float *__restrict__ part, int n_chunks, int n_pix, int kc, double inv_spp,
-                                float *__restrict__ out) {
+__global__ void k_reduce_chunks(const float *__restrict__ part, int n_chunks, int n_pix, int kc, int C,
+                                double inv_spp, float *__restrict__ out) {
   const size_t n = (size_t)n_pix * kc;
+  const float *env = part + (size_t)n_chunks * n;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    double v = 0.0;
-    for (int jj = 0; jj < n_chunks; ++jj) v += (double)part[(size_t)jj * n + i];
     const size_t ip = i / kc, e = i - ip * kc;
+    const size_t ie = ip * C + e % C;
+    double v = 0.0;
+    for (int jj = 0; jj < n_chunks; ++jj) {
+      v += (double)part[(size_t)jj * n + i];
+      v += (double)env[(size_t)jj * n_pix * C + ie];
+    }
     out[e * n_pix + ip] = (float)(v * inv_spp);
   }
 }
@@ -753,24 +758,35 @@ cudaError_t launch_next_iter(cudaStream_t s, uint32_t *iter_dev) {
   return cudaGetLastError();
 }
 
-// Light-shared sampling splits each pixel's samples into chunks so that there
-// are about 2^20 work items (several per lane of a full persistent grid), with at
-// least 16 samples per chunk: every chunk costs a K x C block of partial sums
-// (cleared, updated, reduced), which few samples would not pay for.  The split
-// depends on the sizes only, never on the grid, so that the summation order -
-// and every result bit - is the same for any tuning.
-constexpr long long kSharedItems = 1ll << 20;
-constexpr int kSharedMinChunk = 16;
-int shared_chunks(int n_pix, int spp) {
+// Light-shared sampling splits each pixel's samples into chunks, one work item
+// each: about 2^22 items (a few tens per lane of a full persistent grid), with at
+// least 16 samples per chunk.  Short items keep the lanes' loads even up to the
+// last item (a launch ends when its slowest lane does, and the cost of a pixel's
+// samples varies several-fold across a field), while every chunk costs a K x C
+// block of partial sums (cleared, updated, reduced), which few samples would not
+// pay for.  The split depends on the sizes only, never on the grid, so that the
+// summation order - and every result bit - is the same for any tuning.
+#ifndef IRTPS_SHARED_ITEMS_LOG2
+#define IRTPS_SHARED_ITEMS_LOG2 22
+#endif
+#ifndef IRTPS_SHARED_MIN_CHUNK
+#define IRTPS_SHARED_MIN_CHUNK 16
+#endif
+constexpr long long kSharedItems = 1ll << IRTPS_SHARED_ITEMS_LOG2;
+constexpr int kSharedMinChunk = IRTPS_SHARED_MIN_CHUNK;
+
+SharedSplit shared_split(int n_pix, int spp) {
   long long n = (kSharedItems + n_pix - 1) / n_pix;
   const long long most = spp / kSharedMinChunk > 1 ? spp / kSharedMinChunk : 1;
   n = n < 1 ? 1 : (n > most ? most : n);
-  const int chunk = (int)((spp + n - 1) / n);
-  return (spp + chunk - 1) / chunk;
+  SharedSplit r;
+  r.chunk = (int)((spp + n - 1) / n);
+  r.n_chunks = (spp + r.chunk - 1) / r.chunk;
+  return r;
 }
 
 size_t shared_scratch_floats(const Ctx &c, int n_pix, int spp) {
-  return (size_t)shared_chunks(n_pix, spp) * c.K * c.C * n_pix;
+  return (size_t)shared_split(n_pix, spp).n_chunks * (c.K + 1) * c.C * n_pix;
 }
 
 cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
@@ -794,12 +810,13 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
   a.stream = stream;
   long long n = (long long)n_pix * c.K;
   if (shared) {
-    a.one.n_chunks = shared_chunks(n_pix, spp);
-    a.one.chunk = (spp + a.one.n_chunks - 1) / a.one.n_chunks;
-    const size_t need = (size_t)a.one.n_chunks * c.K * c.C * n_pix;
-    if (need > c.shared_cap) return cudaErrorInvalidValue;  // scratch not prepared
+    const SharedSplit sp = shared_split(n_pix, spp);
+    a.one.n_chunks = sp.n_chunks;
+    a.one.chunk = sp.chunk;
+    const size_t lights = (size_t)a.one.n_chunks * c.K * c.C * n_pix;  // updated in place: cleared first
+    if (lights + (size_t)a.one.n_chunks * c.C * n_pix > c.shared_cap) return cudaErrorInvalidValue;  // not prepared
     a.one.part = c.shared_part;
-    if (cudaMemsetAsync(a.one.part, 0, sizeof(float) * need, c.stream) != cudaSuccess) return cudaGetLastError();
+    if (cudaMemsetAsync(a.one.part, 0, sizeof(float) * lights, c.stream) != cudaSuccess) return cudaGetLastError();
     n = (long long)n_pix * a.one.n_chunks;
   }
   a.n_items = (unsigned)n;
@@ -817,7 +834,8 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
       k_trace<3, false, true><<<(unsigned)blocks, threads, smem, c.stream>>>(a);
     const size_t m = (size_t)c.K * c.C * n_pix;
     const unsigned rb = (unsigned)std::min<size_t>((m + 255) / 256, 8192);
-    k_reduce_chunks<<<rb, 256, 0, c.stream>>>(a.one.part, a.one.n_chunks, n_pix, c.K * c.C, 1.0 / (double)spp, out);
+    k_reduce_chunks<<<rb, 256, 0, c.stream>>>(a.one.part, a.one.n_chunks, n_pix, c.K * c.C, c.C, 1.0 / (double)spp,
+                                              out);
     ++c.stats.launches;
   } else {
     if (c.C == 1)
@@ -891,8 +909,13 @@ __global__ void k_parts_b(const ReduceObj *__restrict__ objs, int n) {
   } else {
     for (size_t i = start; i < m; i += step) {
       double v = 0.0;
-      for (int jj = 0; jj < o.n_chunks; ++jj) v += (double)o.part[(size_t)jj * m + i];
       const size_t ip = i / o.kc, e = i - ip * o.kc;
+      const size_t ie = ip * o.C + e % o.C;
+      const float *env = o.part + (size_t)o.n_chunks * m;
+      for (int jj = 0; jj < o.n_chunks; ++jj) {
+        v += (double)o.part[(size_t)jj * m + i];
+        v += (double)env[(size_t)jj * o.n_pix * o.C + ie];
+      }
       o.out[e * o.n_pix + ip] = (float)(v * o.inv_spp);
     }
   }
