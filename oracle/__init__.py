@@ -28,6 +28,9 @@ Functions and the passages they follow:
                        extraction).
 * `render`           — stage 0 synthetic input images (direct + traced indirect +
                        Gaussian noise).
+* `hole_mask`, `interpolate_holes` — the single-sample variant of Sec. IV: pixels
+                       whose samples saw no surface point get no environment value
+                       and are filled by a non-uniform (pull-push) interpolation.
 * `irtps_run`        — the loop of Sec. IV: PS, integrate, trace, subtract, repeat;
                        D_H = H_{t+1} - H_t reported per iteration.
 * `height_error`, `albedo_error`, `normal_error` — the evaluation formulas of Sec. V.
@@ -287,6 +290,82 @@ def render(depth, normals, albedo, lights, env, spp, bounces, seed, sigma, *, sh
 
 
 # ----------------------------------------------------------------------------
+# Single-sample holes and their interpolation (Sec. IV, environment colour images)
+# ----------------------------------------------------------------------------
+def hole_mask(records):
+    """Holes of a per-light trace: (K, n_pix) bool, True where every sample of
+    (pixel, light) left the surface at its first segment, so that the pixel saw no
+    surface point and its environment image has no value there (Sec. IV: with a
+    single sample some pixels get none).  records as returned by `trace`:
+    (n_pix, K, spp, bounces, 2), field 0 of the first bounce = -1 on escape."""
+    r = np.asarray(records)
+    return np.all(r[:, :, :, 0, 0] == -1, axis=2).T
+
+
+def pyramid_sizes(H, W):
+    """Level sizes of the fill pyramid: halved (rounded up) until 1 x 1."""
+    sizes = [(H, W)]
+    while sizes[-1] != (1, 1):
+        h, w = sizes[-1]
+        sizes.append(((h + 1) // 2, (w + 1) // 2))
+    return sizes
+
+
+def _upsample_taps(n_fine, n_coarse):
+    """Coarse neighbours and weights of each fine index for 2x linear upsampling of
+    cell-centred samples: fine centre i sits at coarse coordinate i/2 - 1/4, so an
+    even i takes (i/2 - 1, i/2) with weights (1/4, 3/4), an odd i takes
+    ((i-1)/2, (i+1)/2) with (3/4, 1/4); indices clamp to the border."""
+    i = np.arange(n_fine)
+    lo = np.where(i % 2 == 0, i // 2 - 1, (i - 1) // 2)
+    hi = lo + 1
+    w_lo = np.where(i % 2 == 0, 0.25, 0.75)
+    return np.clip(lo, 0, n_coarse - 1), np.clip(hi, 0, n_coarse - 1), w_lo, 1.0 - w_lo
+
+
+def interpolate_holes(values, known):
+    """Non-uniform interpolation of the missing pixels of environment images (the
+    paper names a non-uniform interpolation without giving it; this is the pull-push
+    form of multiscale normalised convolution).
+
+    values (K, C, H, W), known (K, H, W) bool.  Pull: level l+1 holds, per coarse
+    pixel, the sum S of its (up to four) children's confidences and the
+    confidence-weighted mean of their values; its confidence is min(S, 1), with
+    confidence 1 at known and 0 at missing pixels of level 0.  Push, from the 1 x 1
+    level down: a pixel's value becomes w v + (1 - w) u, w its confidence and u the
+    2x linear upsampling of the finished coarser level.  Known pixels keep their
+    value; an image with no known pixel stays as it is.  FP64; returns a copy."""
+    v0 = np.asarray(values, np.float64)
+    w0 = np.asarray(known, bool).astype(np.float64)
+    K, C, H, W = v0.shape
+    sizes = pyramid_sizes(H, W)
+    V, Wt = [v0], [w0]
+    for (h, w), (h2, w2) in zip(sizes[:-1], sizes[1:]):
+        wp = np.zeros((K, 2 * h2, 2 * w2))
+        vp = np.zeros((K, C, 2 * h2, 2 * w2))
+        wp[:, :h, :w] = Wt[-1]
+        vp[:, :, :h, :w] = V[-1] * Wt[-1][:, None]
+        s_w = wp[:, 0::2, 0::2] + wp[:, 1::2, 0::2] + wp[:, 0::2, 1::2] + wp[:, 1::2, 1::2]
+        s_v = vp[:, :, 0::2, 0::2] + vp[:, :, 1::2, 0::2] + vp[:, :, 0::2, 1::2] + vp[:, :, 1::2, 1::2]
+        has = s_w > 0
+        V.append(np.where(has[:, None], s_v / np.where(has, s_w, 1.0)[:, None], 0.0))
+        Wt.append(np.minimum(s_w, 1.0))
+    out = V[-1]
+    for lvl in range(len(sizes) - 2, -1, -1):
+        h, w = sizes[lvl]
+        h2, w2 = sizes[lvl + 1]
+        y0, y1, a0, a1 = _upsample_taps(h, h2)
+        x0, x1, b0, b1 = _upsample_taps(w, w2)
+        u = (a0[:, None] * (b0[None, :] * out[:, :, y0][:, :, :, x0] + b1[None, :] * out[:, :, y0][:, :, :, x1]) +
+             a1[:, None] * (b0[None, :] * out[:, :, y1][:, :, :, x0] + b1[None, :] * out[:, :, y1][:, :, :, x1]))
+        wl = Wt[lvl][:, None]
+        out = wl * V[lvl] + (1.0 - wl) * u
+    none = Wt[-1][:, 0, 0] == 0  # images with no known pixel
+    out[none] = v0[none]
+    return out
+
+
+# ----------------------------------------------------------------------------
 # Photometric stereo (Eq. 3-4)
 # ----------------------------------------------------------------------------
 def pinv_lights(lights):
@@ -495,13 +574,17 @@ def ps_step(A0, rho_t, lbar, lights, tau_lo=TAU_LO, tau_hi=TAU_HI, cond_max=COND
 
 
 def irtps_run(A0, lights, env, n_iter, spp, bounces, seed, *, shadow_rays=True, fp32=True, threads=0,
-              tau_lo=TAU_LO, tau_hi=TAU_HI, obj=0, shared=False, irls_iters=0, irls_delta=0.05):
+              tau_lo=TAU_LO, tau_hi=TAU_HI, obj=0, shared=False, irls_iters=0, irls_delta=0.05,
+              fill_holes=False):
     """The IRT-PS loop: iteration 0 is classic PS + integration; each further
     iteration traces Lbar on the current estimate (iteration index t), subtracts
     rho_t * Lbar_t from the ORIGINAL images, re-solves PS and re-integrates.
     `obj` is the object index in the Philox key {seed_lo ^ obj, seed_hi}; `shared`
     selects light-shared sampling for the trace; irls_iters > 0 integrates with the
-    Huber M-estimator (irls_solve) instead of plain least squares.
+    Huber M-estimator (irls_solve) instead of plain least squares; fill_holes
+    replaces Lbar at the holes of each light's trace (hole_mask) by the non-uniform
+    interpolation of its known pixels (interpolate_holes; the single-sample variant,
+    per-light sampling).
     Returns a list of per-iteration dicts (depth, normals, albedo, lbar, dH)."""
     A0 = np.asarray(A0, np.float32)
     K, C, H, W = A0.shape
@@ -518,9 +601,15 @@ def irtps_run(A0, lights, env, n_iter, spp, bounces, seed, *, shadow_rays=True, 
                  lbar=None, dH=None, counts=(0, 0))]
     for t in range(n_iter):
         st = hist[-1]
-        lbar, _, counts = trace(st["depth"].astype(np.float32), st["normals"].astype(np.float32),
-                                st["albedo"].astype(np.float32), lights, env, spp, bounces, seed, t,
-                                obj=obj, shadow_rays=shadow_rays, fp32=fp32, threads=threads, shared=shared)
+        lbar, rec, counts = trace(st["depth"].astype(np.float32), st["normals"].astype(np.float32),
+                                  st["albedo"].astype(np.float32), lights, env, spp, bounces, seed, t,
+                                  obj=obj, shadow_rays=shadow_rays, fp32=fp32, threads=threads, shared=shared,
+                                  records=fill_holes)
+        if fill_holes:
+            if shared:
+                raise ValueError("hole filling follows per-light sampling")
+            known = ~hole_mask(rec).reshape(K, H, W)
+            lbar = interpolate_holes(lbar.reshape(K, C, H, W), known).reshape(K, C, H * W)
         n, rho, ok = ps_step(A0, st["albedo"].astype(np.float32).reshape(C, -1), lbar, lights, tau_lo,
                              tau_hi)
         depth = integrate(n)
