@@ -83,6 +83,15 @@ typedef struct irtps_options {
                          triangle test of its first cell (results unchanged, bit for bit).  Pays
                          only at high sample counts: the bounds cost about as much as 20 samples
                          per pixel and light save (0) */
+  int fill_holes;     /* 1: the single-sample variant of Sec. IV (per-light sampling only): a (pixel,
+                         light) none of whose samples hit the surface with its first segment has no
+                         environment value (a hole); after every trace of the IRT loop (irtps_iterate,
+                         irtps_trace) Lbar at the holes is replaced by a non-uniform interpolation
+                         of the known pixels of the same light and channel (pull-push normalised
+                         convolution: confidence-weighted 2x2 means up a pyramid to 1 x 1, then
+                         confidence blends with the 2x linear upsampling of the coarser level back
+                         down; known pixels keep their values, a light without known pixels keeps
+                         its traced values) (0) */
 } irtps_options;
 
 /* Counters of the last irtps_iterate / irtps_trace / irtps_integrate call. */
@@ -175,6 +184,9 @@ int irtps_get_albedo(irtps_ctx *ctx, float *out, int on_device);    /* C x H x W
 int irtps_get_depth(irtps_ctx *ctx, float *out, int on_device);     /* H x W, mean 0 */
 int irtps_get_indirect(irtps_ctx *ctx, float *out, int on_device);  /* K x C x H x W */
 int irtps_get_valid(irtps_ctx *ctx, uint8_t *out, int on_device);   /* H x W, 1 = normal solved */
+/* K x H x W, 1 = hole of the last whole-field trace (contexts created with
+ * fill_holes only; IRTPS_EINVAL otherwise). */
+int irtps_get_holes(irtps_ctx *ctx, uint8_t *out, int on_device);
 int irtps_get_stats(irtps_ctx *ctx, irtps_stats *out);
 
 /* Geometry probes for the parity tests.  Host arrays.
@@ -185,6 +197,18 @@ int irtps_get_stats(irtps_ctx *ctx, irtps_stats *out);
  * miss) and triangle index 2*(cell_row*(W-1) + cell_col) + {0, 1} (-1). */
 int irtps_probe_dirs(int n, const float *normals, const uint32_t *x0, const uint32_t *x1, float *out);
 int irtps_probe_rays(irtps_ctx *ctx, int n, const float *rays, float *out_t, int32_t *out_tri);
+
+/* The hole interpolation of fill_holes on caller data (Sec. IV: the missing
+ * pixels of single-sample environment images filled by a non-uniform
+ * interpolation), for staged use and testing.  Host arrays:
+ *   values : K x C x H x W float, in place; known pixels keep their values,
+ *            holes get the interpolation (their input values are ignored); an
+ *            image (k) without known pixels is left unchanged
+ *   holes  : K x H x W uint8, nonzero = missing
+ * C in {1, 3}, K, H, W >= 1, K*C*H*W < 2^31.  Allocates its device buffers for
+ * the call and returns after the result is copied back.  IRTPS_EINVAL on bad
+ * arguments, IRTPS_ENOMEM / IRTPS_ECUDA on CUDA failures. */
+int irtps_interpolate_holes(float *values, const uint8_t *holes, int K, int C, int H, int W);
 
 /* Depth integration without any device allocation.  The paper has no
  * counterpart: this entry exists for callers that cannot allocate device memory
@@ -238,7 +262,8 @@ int irtps_autotune(irtps_ctx *ctx, int spp_probe, int bounces, uint64_t seed, do
  * which each object's solve runs on its own team of blocks, and one D_H launch.
  * Objects may differ in H, W, K, spp, bounces and options; all must have the
  * same C, image dtype, sampling option and irls_iters (robust integration runs
- * the same number of reweighting steps for every object; irls_delta may differ).  Every object's results are bit-identical to its own
+ * the same number of reweighting steps for every object; irls_delta may differ),
+ * and none may have fill_holes (hole interpolation runs per context).  Every object's results are bit-identical to its own
  * irtps_iterate in the trace and the normal solve; the depth solve differs from
  * it only by the summation order of its reductions (team size), within cg_tol.
  *

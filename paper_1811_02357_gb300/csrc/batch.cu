@@ -397,7 +397,7 @@ int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int
   b.irls_iters = objs[0]->c.opt.irls_iters;
   for (int i = 0; i < n_obj; ++i) {
     if (objs[i]->c.C != b.C || (objs[i]->c.opt.sampling == 1) != b.shared ||
-        objs[i]->c.opt.irls_iters != b.irls_iters)
+        objs[i]->c.opt.irls_iters != b.irls_iters || objs[i]->c.opt.fill_holes)
       return bail(IRTPS_EINVAL);
     b.mg_levels = std::max(b.mg_levels, objs[i]->c.mg_levels);
   }

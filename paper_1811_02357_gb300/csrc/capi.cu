@@ -45,7 +45,8 @@ int dalloc(Ctx &c, T **p, size_t n, const char *what) {
 void release(Ctx &c) {
   void *bufs[] = {c.env, c.d_lights, c.horizon, c.shared_part, c.images, c.lbar, c.depth, c.depth_prev, c.nrm, c.albedo, c.valid, c.pmin, c.pmax,
                   c.cg_x, c.cg_b, c.cg_r, c.cg_z, c.cg_p, c.cg_ap, c.part, c.dstats, c.next_item, c.cg_ctl,
-                  c.mg_x0, c.mg_x1, c.mg_b, c.mg_wh, c.mg_wv, c.mg_wh_unit, c.mg_wv_unit, c.iter_dev};
+                  c.mg_x0, c.mg_x1, c.mg_b, c.mg_wh, c.mg_wv, c.mg_wh_unit, c.mg_wv_unit, c.iter_dev, c.holes,
+                  c.fill_v, c.fill_w};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (c.h_part) cudaFreeHost(c.h_part);
@@ -140,13 +141,23 @@ int end_call(Ctx &c, bool had_solve) {
   return IRTPS_OK;
 }
 
+// fill: the whole field's trace of the IRT loop with fill_holes on marks the holes
+// and replaces Lbar there by the interpolation of the known pixels.
 int trace_into(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed, uint32_t iter,
-               uint32_t stream_tag, float *out, int32_t *rec, bool iter_from_device = false) {
+               uint32_t stream_tag, float *out, int32_t *rec, bool iter_from_device = false, bool fill = false) {
+  fill = fill && c.opt.fill_holes && !pixels && out == c.lbar;
   CK(irtps::build_pyramid(c), "pyramid build");
   if (!iter_from_device) STAGE(ST_TRACE, true);
   CK(irtps::launch_horizon(c), "horizon bounds");
-  CK(irtps::launch_trace(c, pixels, n_pix, spp, bounces, seed, iter, stream_tag, out, rec, iter_from_device),
+  CK(irtps::launch_trace(c, pixels, n_pix, spp, bounces, seed, iter, stream_tag, out, rec, iter_from_device, fill),
      "trace launch");
+  if (fill) {
+    int launches = 0;
+    CK(irtps::launch_interpolate_holes(c.stream, c.lbar, c.holes, c.K, c.C, c.fill_py, c.fill_v, c.fill_w, c.sms,
+                                       launches),
+       "hole interpolation");
+    c.stats.launches += launches;
+  }
   if (!iter_from_device) STAGE(ST_TRACE, false);
   c.stats.primary_segments += (unsigned long long)n_pix * (c.opt.sampling == 1 ? 1 : c.K) * spp;
   return IRTPS_OK;
@@ -200,7 +211,8 @@ int enqueue_iteration(Ctx &c, int spp, int bounces, uint64_t seed, bool captured
   int rc;
   CK(cudaMemcpyAsync(c.depth_prev, c.depth, sizeof(float) * c.H * c.W, cudaMemcpyDeviceToDevice, c.stream),
      "iterate");
-  if ((rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, c.t, 0u, c.lbar, nullptr, captured))) return rc;
+  if ((rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, c.t, 0u, c.lbar, nullptr, captured, true)))
+    return rc;
   if (captured) {
     CK(irtps::launch_ps(c, false), "ps launch");
     CK(irtps::solve_depth_async(c), "depth solve launch");
@@ -264,6 +276,7 @@ void irtps_default_options(irtps_options *opt) {
   opt->irls_iters = 0;
   opt->irls_delta = 0.05f;
   opt->early_escape = 0;
+  opt->fill_holes = 0;
 }
 
 int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *lights, const float *env, int EH,
@@ -299,6 +312,10 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
     return bail(fail(c, IRTPS_EINVAL, "create: sampling must be 0 (per light) or 1 (light-shared)"));
   if (c.opt.irls_iters < 0 || c.opt.irls_iters > 100 || !(c.opt.irls_delta > 0.0f))
     return bail(fail(c, IRTPS_EINVAL, "create: irls_iters in 0..100 and irls_delta > 0"));
+  if (c.opt.fill_holes != 0 && c.opt.fill_holes != 1)
+    return bail(fail(c, IRTPS_EINVAL, "create: fill_holes must be 0 or 1"));
+  if (c.opt.fill_holes && c.opt.sampling != 0)
+    return bail(fail(c, IRTPS_EINVAL, "create: fill_holes needs per-light sampling (sampling = 0)"));
   c.eps = (float)1e-3 / (float)W;  // same expression as the oracle's lift
   // lights and pinv(L) = (L^T L)^-1 L^T in FP64 (Eq. 4)
   c.h_lights.assign(lights, lights + 3 * K);
@@ -376,6 +393,13 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
       (rc = dalloc(c, &c.iter_dev, 1, "iteration counter")) ||
       (rc = dalloc(c, (irtps::CGCtl **)&c.cg_ctl, 1, "solver control")))
     return bail(rc);
+  if (c.opt.fill_holes) {  // hole mask and the interpolation pyramid above level 0
+    c.fill_py = irtps::fill_pyramid(H, W);
+    if ((rc = dalloc(c, &c.holes, (size_t)K * P, "hole mask")) ||
+        (rc = dalloc(c, &c.fill_v, (size_t)K * C * c.fill_py.total, "hole interpolation")) ||
+        (rc = dalloc(c, &c.fill_w, (size_t)K * c.fill_py.total, "hole interpolation")))
+      return bail(rc);
+  }
   {  // multigrid hierarchy: layout and Galerkin weights built on the host once
     int total = 0;
     irtps::mg_layout(H, W, &c.mg_levels, c.mg_h, c.mg_w, c.mg_off, &total);
@@ -485,7 +509,8 @@ int irtps_trace(irtps_ctx *ctx, int spp, int bounces, uint64_t seed, uint32_t it
   int rc = prepare_trace(c, c.H * c.W, spp);
   if (rc) return rc;
   rc = begin_call(c);
-  if (rc || (rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, iteration, stream_tag, c.lbar, nullptr)))
+  if (rc || (rc = trace_into(c, nullptr, c.H * c.W, spp, bounces, seed, iteration, stream_tag, c.lbar, nullptr,
+                             false, true)))
     return rc;
   return end_call(c, false);
 }
@@ -642,6 +667,40 @@ int irtps_get_valid(irtps_ctx *ctx, uint8_t *out, int on_device) {
   Ctx &c = ctx->c;
   return copy_out(c, out, c.valid, (size_t)c.H * c.W, on_device);
 }
+int irtps_get_holes(irtps_ctx *ctx, uint8_t *out, int on_device) {
+  if (!ctx || !out) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (!c.holes) return fail(c, IRTPS_EINVAL, "get_holes: the context was created without fill_holes");
+  return copy_out(c, out, c.holes, (size_t)c.K * c.H * c.W, on_device);
+}
+
+int irtps_interpolate_holes(float *values, const uint8_t *holes, int K, int C, int H, int W) {
+  if (!values || !holes || K < 1 || (C != 1 && C != 3) || H < 1 || W < 1) return IRTPS_EINVAL;
+  if ((long long)K * C * H * W >= (1LL << 31)) return IRTPS_EINVAL;
+  const irtps::FillPyramid py = irtps::fill_pyramid(H, W);
+  const size_t P = (size_t)H * W;
+  int sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  float *dv = nullptr, *sv = nullptr, *sw = nullptr;
+  uint8_t *dh = nullptr;
+  cudaError_t e = cudaMalloc(&dv, sizeof(float) * K * C * P);
+  if (e == cudaSuccess) e = cudaMalloc(&dh, (size_t)K * P);
+  if (e == cudaSuccess) e = cudaMalloc(&sv, sizeof(float) * (K * C * py.total + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&sw, sizeof(float) * (K * py.total + 1));
+  if (e == cudaSuccess) e = cudaMemcpy(dv, values, sizeof(float) * K * C * P, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dh, holes, (size_t)K * P, cudaMemcpyHostToDevice);
+  int launches = 0;
+  if (e == cudaSuccess) e = irtps::launch_interpolate_holes(nullptr, dv, dh, K, C, py, sv, sw, sms, launches);
+  if (e == cudaSuccess) e = cudaMemcpy(values, dv, sizeof(float) * K * C * P, cudaMemcpyDeviceToHost);
+  const bool oom = e == cudaErrorMemoryAllocation;
+  if (e != cudaSuccess) cudaGetLastError();
+  cudaFree(dv);
+  cudaFree(dh);
+  cudaFree(sv);
+  cudaFree(sw);
+  return e == cudaSuccess ? IRTPS_OK : (oom ? IRTPS_ENOMEM : IRTPS_ECUDA);
+}
+
 int irtps_get_stats(irtps_ctx *ctx, irtps_stats *out) {
   if (!ctx || !out) return IRTPS_EINVAL;
   *out = ctx->c.stats;

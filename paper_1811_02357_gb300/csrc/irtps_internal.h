@@ -58,6 +58,7 @@ struct ObjTrace {
   float *part;            // light-shared sampling: partial sums, n_chunks x n_pix x K x C, then n_chunks x n_pix x C
   int n_chunks, chunk;    // light-shared sampling: sample chunks per pixel and samples per chunk
   const float *hz;        // horizon bounds, 8 octants x H W (null: no early escape)
+  uint8_t *hole;          // per-light sampling: K x n_pix, 1 where no sample's first segment hit (null: none)
   int hz_stride;          // H W
 };
 
@@ -67,6 +68,17 @@ inline int march_levels(int levels, int cut) {
   const int keep = levels < 2 ? levels : 2;
   return levels - cut > keep ? levels - cut : keep;
 }
+
+// Levels of the hole-interpolation pyramid: level 0 is the image (h[0] x w[0]),
+// each next one halves both sides (rounded up) down to 1 x 1; level l >= 1 starts
+// off[l] pixels into the per-image scratch of `total` pixels.
+constexpr int kMaxFillLevels = 32;
+struct FillPyramid {
+  int n = 0;
+  int h[kMaxFillLevels] = {0}, w[kMaxFillLevels] = {0};
+  size_t off[kMaxFillLevels] = {0};
+  size_t total = 0;
+};
 
 struct Ctx {
   int H = 0, W = 0, K = 0, C = 0, EH = 0, EW = 0;
@@ -85,6 +97,9 @@ struct Ctx {
   float *d_lights = nullptr;      // K*3 on the device (read at trace hits)
   float *horizon = nullptr;       // early escape: horizon bounds of every pixel, 8 x H x W (option)
   float *shared_part = nullptr;   // light-shared trace: partial sums of its sample chunks
+  uint8_t *holes = nullptr;       // fill_holes: K x H x W, 1 where the last trace saw no surface point
+  float *fill_v = nullptr, *fill_w = nullptr;  // fill_holes: pyramid levels >= 1, K C and K per pixel
+  FillPyramid fill_py;
   size_t shared_cap = 0;          // floats in shared_part
 
   // device buffers (owned)
@@ -176,7 +191,13 @@ void fill_pyr_obj(const Ctx &c, PyrObj &o);
 cudaError_t build_pyramid_batch(cudaStream_t s, const PyrObj *d_objs, int n, int levels, const int *blocks);
 cudaError_t launch_horizon_batch(cudaStream_t s, const PyrObj *d_objs, int n, int blocks);
 cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
-                         uint32_t iter, uint32_t stream, float *out, int32_t *rec, bool iter_from_device = false);
+                         uint32_t iter, uint32_t stream, float *out, int32_t *rec, bool iter_from_device = false,
+                         bool mark_holes = false);
+// hole interpolation (holes.cu): pyramid of an H x W image; fill the holes (K x H x W, nonzero = hole)
+// of a K x C x H x W device stack in place, scratch v_scr K C py.total and w_scr K py.total floats
+FillPyramid fill_pyramid(int H, int W);
+cudaError_t launch_interpolate_holes(cudaStream_t s, float *values, const uint8_t *holes, int K, int C,
+                                     const FillPyramid &py, float *v_scr, float *w_scr, int sms, int &launches);
 cudaError_t launch_next_iter(Ctx &c);  // iter_dev += 1 (end of a captured iteration)
 cudaError_t launch_next_iter(cudaStream_t s, uint32_t *iter_dev);
 cudaError_t launch_render(Ctx &c, uint64_t seed, float sigma, const float *lbar, float *out);

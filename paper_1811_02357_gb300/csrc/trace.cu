@@ -437,6 +437,7 @@ __global__ void __launch_bounds__(kTraceThreads,
   }
   Walker m;
   bool at_leaf = false;
+  bool seen = false;  // per-light item: some sample's first segment hit the surface
   Work w;
   uint32_t segs = 0;
   int overflow = 0;
@@ -528,6 +529,8 @@ __global__ void __launch_bounds__(kTraceThreads,
           const float inv = 1.0f / (float)ob->spp;
 #pragma unroll
           for (int c = 0; c < C; ++c) ob->out[((size_t)k * C + c) * ob->n_pix + ip] = sum[c] * inv;
+          if (ob->hole) ob->hole[(size_t)k * ob->n_pix + ip] = seen ? 0 : 1;
+          seen = false;
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) sum[c] = comp[c] = 0.0f;
@@ -644,6 +647,7 @@ __global__ void __launch_bounds__(kTraceThreads,
       } else {
         const int W = ob->f.W, H = ob->f.H;
         const float t = m.bt;
+        if (b == 1) seen = true;
         const F3 q = {radd(m.o.x, rmul(t, m.d.x)), radd(m.o.y, rmul(t, m.d.y)), radd(m.o.z, rmul(t, m.d.z))};
         qp = nearest_index(q.y, H) * W + nearest_index(q.x, W);
         const F3 o2 = {q.x, q.y, radd(q.z, ob->eps)};
@@ -744,6 +748,7 @@ void fill_obj_trace(const Ctx &c, ObjTrace &o) {
   o.chunk = 0;
   o.hz = c.horizon;
   o.hz_stride = c.H * c.W;
+  o.hole = nullptr;
 }
 
 __global__ void k_next_iter(uint32_t *iter) { *iter += 1u; }
@@ -790,7 +795,8 @@ size_t shared_scratch_floats(const Ctx &c, int n_pix, int spp) {
 }
 
 cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, uint64_t seed,
-                         uint32_t iter, uint32_t stream, float *out, int32_t *rec, bool iter_from_device) {
+                         uint32_t iter, uint32_t stream, float *out, int32_t *rec, bool iter_from_device,
+                         bool mark_holes) {
   const bool shared = c.opt.sampling == 1;
   TraceArgs a;
   fill_obj_trace(c, a.one);
@@ -799,6 +805,7 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
   a.one.bounces = bounces;
   a.one.key = make_uint2((uint32_t)seed ^ c.obj, (uint32_t)(seed >> 32));
   a.one.out = out;
+  a.one.hole = mark_holes && !shared && !pixels ? c.holes : nullptr;
   a.objs = nullptr;
   a.n_obj = 1;
   a.pixels = pixels;

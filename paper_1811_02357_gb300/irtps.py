@@ -31,7 +31,8 @@ EXPORTED = [
     "irtps_default_options", "irtps_create", "irtps_set_stream", "irtps_set_images", "irtps_iterate",
     "irtps_trace", "irtps_solve_normals", "irtps_integrate", "irtps_trace_pixels", "irtps_set_state",
     "irtps_set_indirect", "irtps_render", "irtps_get_normals", "irtps_get_albedo", "irtps_get_depth",
-    "irtps_get_indirect", "irtps_get_valid", "irtps_get_stats", "irtps_probe_dirs", "irtps_probe_rays",
+    "irtps_get_indirect", "irtps_get_valid", "irtps_get_holes", "irtps_get_stats", "irtps_probe_dirs",
+    "irtps_probe_rays", "irtps_interpolate_holes",
     "irtps_last_error", "irtps_destroy", "irtps_integrate_noalloc", "irtps_set_object", "irtps_set_tuning",
     "irtps_get_tuning", "irtps_autotune", "irtps_batch_create", "irtps_batch_set_stream", "irtps_batch_set_images", "irtps_batch_iterate", "irtps_batch_get_stats",
     "irtps_batch_set_tuning", "irtps_batch_get_tuning", "irtps_batch_autotune", "irtps_batch_last_error",
@@ -44,7 +45,8 @@ class irtps_options(ctypes.Structure):
                 ("cond_max", ctypes.c_double), ("nz_min", ctypes.c_float), ("cg_tol", ctypes.c_double),
                 ("cg_max_iter", ctypes.c_int), ("cg_check_every", ctypes.c_int), ("stop_tol", ctypes.c_double),
                 ("precond", ctypes.c_int), ("use_graph", ctypes.c_int), ("sampling", ctypes.c_int),
-                ("irls_iters", ctypes.c_int), ("irls_delta", ctypes.c_float), ("early_escape", ctypes.c_int)]
+                ("irls_iters", ctypes.c_int), ("irls_delta", ctypes.c_float), ("early_escape", ctypes.c_int),
+                ("fill_holes", ctypes.c_int)]
 
 
 class irtps_stats(ctypes.Structure):
@@ -90,6 +92,8 @@ def _load():
         "irtps_get_depth": (i32, [P, P, i32]),
         "irtps_get_indirect": (i32, [P, P, i32]),
         "irtps_get_valid": (i32, [P, P, i32]),
+        "irtps_get_holes": (i32, [P, P, i32]),
+        "irtps_interpolate_holes": (i32, [P, P, i32, i32, i32, i32]),
         "irtps_get_stats": (i32, [P, P]),
         "irtps_probe_dirs": (i32, [i32, P, P, P, P]),
         "irtps_probe_rays": (i32, [P, i32, P, P, P]),
@@ -255,6 +259,22 @@ def irtps_get_indirect(h, shape, out=None):
 
 def irtps_get_valid(h, shape, out=None):
     return _get(_lib.irtps_get_valid, h, shape, np.uint8, out)
+
+
+def irtps_get_holes(h, shape, out=None):
+    return _get(_lib.irtps_get_holes, h, shape, np.uint8, out)
+
+
+def irtps_interpolate_holes(values, holes):
+    """Non-uniform interpolation of the holes of a (K, C, H, W) float32 stack; holes (K, H, W),
+    nonzero = missing.  Returns the filled copy."""
+    v = np.array(_host(values, np.float32), np.float32, order="C", copy=True)
+    K, C, H, W = v.shape
+    m = _host(holes, np.uint8).reshape(K, H, W)
+    rc = _lib.irtps_interpolate_holes(_addr(v), _addr(m), K, C, H, W)
+    if rc != IRTPS_OK:
+        raise IrtpsError(rc, "interpolate_holes")
+    return v
 
 
 def irtps_get_stats(h):
@@ -464,6 +484,9 @@ class Context:
 
     def valid(self, out=None):
         return irtps_get_valid(self.h, (self.H, self.W), out)
+
+    def holes(self, out=None):
+        return irtps_get_holes(self.h, (self.K, self.H, self.W), out)
 
     def stats(self):
         return irtps_get_stats(self.h)
