@@ -53,7 +53,11 @@ WORKLOADS = {
     "batch_64": ("batch_objects", {}, None, None, 1, 32, 1),
     # a small batch of the same kernels for profiler captures (16 objects, sides 96..384)
     "batch_16_profile": ("batch_objects", {"n": 16, "side_hi": 384}, None, None, 1, 8, 1),
+    # the single-sample variant: one path per (pixel, light), holes filled by interpolation
+    "bumps_512_single": ("bumps_512", {}, 1, 2, 5, 256, 2),
 }
+# context options a workload sets beyond the defaults
+WORKLOAD_OPTIONS = {"bumps_512_single": {"fill_holes": 1}}
 
 # Algorithmic lane operations per unit of trace work (counted from the formulas:
 # Philox4x32-10 = 10 rounds x (2 mul.hi + 2 mul.lo + 4 xor) + 9 x 2 key adds;
@@ -149,25 +153,34 @@ def gt_errors(sc, depth, normals, albedo):
     return {"height": e_h, "albedo": e_rho, "normal": e_n, "normal_deg": ang}
 
 
-def evaluate(irtps, sc, spp, n_iter, seed, opt, stream, dev):
-    """Classic PS and IRT-PS with r = 1, 2, 3 traced reflections on images rendered with three."""
+def evaluate(irtps, sc, spp, n_iter, seed, opt, stream, dev, render_spp=None):
+    """Classic PS and IRT-PS with r = 1, 2, 3 traced reflections on images rendered with three
+    (render_spp samples per pixel and light for the images, default spp)."""
     import torch
     K, C, H, W = sc.K, sc.C, sc.H, sc.W
     A = torch.empty((K, C, H, W), dtype=torch.float32, device=dev)
     with irtps.Context(H, W, sc.lights, sc.env) as gt:
         gt.set_stream(stream.cuda_stream)
         gt.set_state(sc.depth, sc.normals, sc.albedo)
-        gt.render(spp, 3, 2000, 0.002, out=A)
+        rs = render_spp or spp
+        gt.render(rs, 3, 2000, 0.002, out=A)
     torch.cuda.synchronize()
-    out = {"images": f"rendered with 3 reflections, {spp} spp, sigma 0.002", "irt_iterations": n_iter}
-    for r in (1, 2, 3):
-        with irtps.Context(H, W, sc.lights, sc.env, opt) as ctx:
-            ctx.set_stream(stream.cuda_stream)
-            ctx.set_images(A, on_device=True)
-            if r == 1:
-                out["classic_ps"] = gt_errors(sc, ctx.depth(), ctx.normals(), ctx.albedo())
-            ctx.iterate(n_iter, spp, r, seed)
-            out[f"irtps_r{r}"] = gt_errors(sc, ctx.depth(), ctx.normals(), ctx.albedo())
+    out = {"images": f"rendered with 3 reflections, {rs} spp, sigma 0.002", "irt_iterations": n_iter,
+           "trace_spp": spp}
+    variants = [("", opt)]
+    if opt.fill_holes:  # the same loop without the hole interpolation, for comparison
+        plain = irtps.irtps_options.from_buffer_copy(opt)
+        plain.fill_holes = 0
+        variants.append(("_no_fill", plain))
+    for suffix, o in variants:
+        for r in (1, 2, 3):
+            with irtps.Context(H, W, sc.lights, sc.env, o) as ctx:
+                ctx.set_stream(stream.cuda_stream)
+                ctx.set_images(A, on_device=True)
+                if r == 1 and not suffix:
+                    out["classic_ps"] = gt_errors(sc, ctx.depth(), ctx.normals(), ctx.albedo())
+                ctx.iterate(n_iter, spp, r, seed)
+                out[f"irtps_r{r}{suffix}"] = gt_errors(sc, ctx.depth(), ctx.normals(), ctx.albedo())
     return out
 
 
@@ -479,6 +492,8 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     opt = irtps.irtps_default_options()
     opt.sampling = 1 if args.sampling == "shared" else 0
+    for key, val in WORKLOAD_OPTIONS.get(args.workload, {}).items():
+        setattr(opt, key, val)
     ctx = irtps.Context(H, W, sc.lights, sc.env, opt)
     ctx.set_stream(stream.cuda_stream)
     A0 = torch.empty((K, C, H, W), dtype=torch.float32, device=dev)
@@ -511,7 +526,7 @@ def main():
     launches0 = ctx.stats()["launches"]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     tot = dict(segments=0, primary=0, draws=0, nodes=0, tris=0, trace_ms=0.0, ps_ms=0.0, depth_ms=0.0,
-               cg_iters=0)
+               fill_ms=0.0, cg_iters=0)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         for i in range(args.steps):
@@ -528,6 +543,7 @@ def main():
             tot["trace_ms"] += st["trace_ms"]
             tot["ps_ms"] += st["ps_ms"]
             tot["depth_ms"] += st["depth_ms"]
+            tot["fill_ms"] += st["fill_ms"]
             tot["cg_iters"] += st["cg_iterations"]
         torch.cuda.synchronize()
         if world > 1:
@@ -583,19 +599,20 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "H": H, "W": W, "K": K, "C": C, "spp": spp, "images": args.images,
                        "sampling": args.sampling, "trace_blocks_per_sm": tuning[0], "mip_cut": tuning[1],
+                       "options": WORKLOAD_OPTIONS.get(args.workload, {}),
                        "bounces": bounces, "irt_iterations_per_step": n_iter, "parallelism": f"replicas{world}",
                        "l2": "512 MB buffer written between timed steps"},
             "pixel_iters_per_s": P * n_iter * world * args.steps / (ms_all / 1e3),
             "primary_mrays_per_s": tot["primary"] * world / (ms_all / 1e3) / 1e6,
             "stage_ms_per_step": {"trace": tot["trace_ms"] / args.steps, "ps": tot["ps_ms"] / args.steps,
-                                  "depth": tot["depth_ms"] / args.steps},
+                                  "depth": tot["depth_ms"] / args.steps, "hole_fill": tot["fill_ms"] / args.steps},
             "cg_iterations_last_solve": tot["cg_iters"] / args.steps,
             "work_per_segment": {"node_visits": tot["nodes"] / max(1, tot["segments"]),
                                  "tri_tests": tot["tris"] / max(1, tot["segments"]),
                                  "draws": tot["draws"] / max(1, tot["segments"])},
             "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e}
     if args.evaluate:
-        line["evaluation"] = evaluate(irtps, sc, spp, n_iter, seed, opt, stream, dev)
+        line["evaluation"] = evaluate(irtps, sc, spp, n_iter, seed, opt, stream, dev, render_spp=max(spp, rspp))
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, spp, bounces, shared=args.sampling == "shared", single_thread=True)
     ctx.close()

@@ -111,6 +111,7 @@ typedef struct irtps_stats {
   double depth_ms;                     /* device time of the depth solve(s) incl. host checks */
   unsigned long long launches;         /* kernels launched since irtps_create (cumulative) */
   unsigned long long draws;            /* sampled directions (primary and bounce segments) */
+  double fill_ms;                      /* device time of the hole interpolation (fill_holes) */
 } irtps_stats;
 
 /* Defaults listed beside each field of irtps_options. */

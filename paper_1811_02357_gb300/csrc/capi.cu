@@ -74,11 +74,11 @@ int copy_in(Ctx &c, void *dst, const void *src, size_t bytes, int on_device) {
 }
 
 // ---- per-call bookkeeping: device statistics cleared at the start, read once at the end ----
-enum Stage { ST_TRACE = 0, ST_PS = 1, ST_DEPTH = 2 };
+enum Stage { ST_TRACE = 0, ST_PS = 1, ST_DEPTH = 2, ST_FILL = 3 };
 
 int begin_call(Ctx &c) {
   CK(cudaMemsetAsync(c.dstats, 0, sizeof(irtps::DevStats), c.stream), "statistics reset");
-  c.stats.trace_ms = c.stats.ps_ms = c.stats.depth_ms = 0.0;
+  c.stats.trace_ms = c.stats.ps_ms = c.stats.depth_ms = c.stats.fill_ms = 0.0;
   c.stats.node_visits = c.stats.tri_tests = c.stats.draws = 0;
   c.stats.segments = c.stats.walk_overflows = c.stats.primary_segments = 0;
   c.tev_used = 0;
@@ -118,8 +118,8 @@ int end_call(Ctx &c, bool had_solve) {
   for (int i = 0; i < c.tev_used; ++i) {
     float ms = 0.0f;
     CK(cudaEventElapsedTime(&ms, c.tev[2 * i], c.tev[2 * i + 1]), "timing");
-    double *dst = c.tev_stage[i] == ST_TRACE ? &c.stats.trace_ms : (c.tev_stage[i] == ST_PS ? &c.stats.ps_ms : &c.stats.depth_ms);
-    *dst += ms;
+    double *const dst[] = {&c.stats.trace_ms, &c.stats.ps_ms, &c.stats.depth_ms, &c.stats.fill_ms};
+    *dst[c.tev_stage[i]] += ms;
   }
   c.stats.segments = h.counts[1];
   c.stats.walk_overflows = h.counts[2];
@@ -151,14 +151,16 @@ int trace_into(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, u
   CK(irtps::launch_horizon(c), "horizon bounds");
   CK(irtps::launch_trace(c, pixels, n_pix, spp, bounces, seed, iter, stream_tag, out, rec, iter_from_device, fill),
      "trace launch");
+  if (!iter_from_device) STAGE(ST_TRACE, false);
   if (fill) {
     int launches = 0;
+    if (!iter_from_device) STAGE(ST_FILL, true);
     CK(irtps::launch_interpolate_holes(c.stream, c.lbar, c.holes, c.K, c.C, c.fill_py, c.fill_v, c.fill_w, c.sms,
                                        launches),
        "hole interpolation");
+    if (!iter_from_device) STAGE(ST_FILL, false);
     c.stats.launches += launches;
   }
-  if (!iter_from_device) STAGE(ST_TRACE, false);
   c.stats.primary_segments += (unsigned long long)n_pix * (c.opt.sampling == 1 ? 1 : c.K) * spp;
   return IRTPS_OK;
 }

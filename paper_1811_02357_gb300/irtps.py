@@ -55,7 +55,8 @@ class irtps_stats(ctypes.Structure):
                 ("cg_rel_residual", ctypes.c_double), ("dH_max", ctypes.c_double), ("dH_rms", ctypes.c_double),
                 ("iterations_done", ctypes.c_int), ("node_visits", ctypes.c_ulonglong),
                 ("tri_tests", ctypes.c_ulonglong), ("trace_ms", ctypes.c_double), ("ps_ms", ctypes.c_double),
-                ("depth_ms", ctypes.c_double), ("launches", ctypes.c_ulonglong), ("draws", ctypes.c_ulonglong)]
+                ("depth_ms", ctypes.c_double), ("launches", ctypes.c_ulonglong), ("draws", ctypes.c_ulonglong),
+                ("fill_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
