@@ -67,7 +67,11 @@ typedef struct irtps_options {
   int cg_max_iter;    /* depth solve iteration cap (50000) */
   int cg_check_every; /* FP64 true-residual refresh and convergence test period (10) */
   double stop_tol;    /* irtps_iterate stops early when D_H < stop_tol; 0 = never (0) */
-  int precond;        /* depth-solve preconditioner: 0 Jacobi (diagonal), 1 multigrid V-cycle (1) */
+  int precond;        /* depth solve: 0 Jacobi-preconditioned CG, 1 multigrid-preconditioned CG,
+                         2 direct: unit-weight solves of grids up to 1024 x 1024 by the cosine
+                         transform that diagonalises the grid Laplacian (four FP64 transform
+                         products, then the same FP64 residual check against cg_tol); weighted
+                         (irls) solves, larger grids and batches use multigrid (2) */
   int use_graph;      /* 1: irtps_iterate captures one iteration as a CUDA graph and replays it (0);
                          per-stage times are then not measured (reported as 0) */
   int sampling;       /* trace sampling (0):

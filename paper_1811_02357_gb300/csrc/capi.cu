@@ -46,7 +46,7 @@ void release(Ctx &c) {
   void *bufs[] = {c.env, c.d_lights, c.horizon, c.shared_part, c.images, c.lbar, c.depth, c.depth_prev, c.nrm, c.albedo, c.valid, c.pmin, c.pmax,
                   c.cg_x, c.cg_b, c.cg_r, c.cg_z, c.cg_p, c.cg_ap, c.part, c.dstats, c.next_item, c.cg_ctl,
                   c.mg_x0, c.mg_x1, c.mg_b, c.mg_wh, c.mg_wv, c.mg_wh_unit, c.mg_wv_unit, c.iter_dev, c.holes,
-                  c.fill_v, c.fill_w};
+                  c.fill_v, c.fill_w, c.sp_ch, c.sp_cw, c.sp_mu, c.sp_nu, c.sp_t};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (c.h_part) cudaFreeHost(c.h_part);
@@ -272,7 +272,7 @@ void irtps_default_options(irtps_options *opt) {
   opt->cg_max_iter = 50000;
   opt->cg_check_every = 10;
   opt->stop_tol = 0.0;
-  opt->precond = 1;
+  opt->precond = 2;
   opt->use_graph = 0;
   opt->sampling = 0;
   opt->irls_iters = 0;
@@ -308,8 +308,8 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
     c.opt = *opt;
   else
     irtps_default_options(&c.opt);
-  if (c.opt.precond != 0 && c.opt.precond != 1)
-    return bail(fail(c, IRTPS_EINVAL, "create: precond must be 0 (Jacobi) or 1 (multigrid)"));
+  if (c.opt.precond < 0 || c.opt.precond > 2)
+    return bail(fail(c, IRTPS_EINVAL, "create: precond must be 0 (Jacobi), 1 (multigrid) or 2 (spectral)"));
   if (c.opt.sampling != 0 && c.opt.sampling != 1)
     return bail(fail(c, IRTPS_EINVAL, "create: sampling must be 0 (per light) or 1 (light-shared)"));
   if (c.opt.irls_iters < 0 || c.opt.irls_iters > 100 || !(c.opt.irls_delta > 0.0f))
@@ -395,6 +395,14 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
       (rc = dalloc(c, &c.iter_dev, 1, "iteration counter")) ||
       (rc = dalloc(c, (irtps::CGCtl **)&c.cg_ctl, 1, "solver control")))
     return bail(rc);
+  if (c.opt.precond == 2 && irtps::spectral_fits(H, W)) {
+    e = irtps::spectral_setup(c);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return bail(fail(c, e == cudaErrorMemoryAllocation ? IRTPS_ENOMEM : IRTPS_ECUDA,
+                       std::string("create: spectral solve: ") + cudaGetErrorString(e)));
+    }
+  }
   if (c.opt.fill_holes) {  // hole mask and the interpolation pyramid above level 0
     c.fill_py = irtps::fill_pyramid(H, W);
     if ((rc = dalloc(c, &c.holes, (size_t)K * P, "hole mask")) ||

@@ -100,6 +100,9 @@ struct Ctx {
   uint8_t *holes = nullptr;       // fill_holes: K x H x W, 1 where the last trace saw no surface point
   float *fill_v = nullptr, *fill_w = nullptr;  // fill_holes: pyramid levels >= 1, K C and K per pixel
   FillPyramid fill_py;
+  // spectral depth solve (precond = 2): DCT-II matrices H x H and W x W, path-Laplacian
+  // eigenvalues, one H x W work array (FP64)
+  double *sp_ch = nullptr, *sp_cw = nullptr, *sp_mu = nullptr, *sp_nu = nullptr, *sp_t = nullptr;
   size_t shared_cap = 0;          // floats in shared_part
 
   // device buffers (owned)
@@ -196,6 +199,11 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
 // hole interpolation (holes.cu): pyramid of an H x W image; fill the holes (K x H x W, nonzero = hole)
 // of a K x C x H x W device stack in place, scratch v_scr K C py.total and w_scr K py.total floats
 FillPyramid fill_pyramid(int H, int W);
+// spectral depth solve (spectral.cu): grids up to kSpectralMaxSide on both sides
+constexpr int kSpectralMaxSide = 1024;
+bool spectral_fits(int H, int W);
+cudaError_t spectral_setup(Ctx &c);                                 // matrices and work array
+cudaError_t launch_spectral(Ctx &c, const double *b, double *x);   // x = A^+ b, unit weights
 cudaError_t launch_interpolate_holes(cudaStream_t s, float *values, const uint8_t *holes, int K, int C,
                                      const FillPyramid &py, float *v_scr, float *w_scr, int sms, int &launches);
 cudaError_t launch_next_iter(Ctx &c);  // iter_dev += 1 (end of a captured iteration)

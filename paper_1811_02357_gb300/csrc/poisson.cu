@@ -889,8 +889,20 @@ __global__ void __launch_bounds__(kThreads) k_mg_coarsen(const MG m, int l, floa
   mg_coarsen_body(m, l, wh, wv, whole_grid());
 }
 
+// A direct (spectral) solve counts as one iteration; its FP64 residual is checked
+// against the tolerance like the last one of a PCG loop.
+__global__ void k_direct_done(const CGCtl *ctl, CGAcc *acc, double tol) {
+  const double rel = ctl->rel;
+  acc->iters += 1;
+  acc->last_iters = 1;
+  acc->rel_last = rel;
+  if (!isfinite(ctl->bnorm) || !isfinite(rel) || rel > tol) acc->bad = 1;
+}
+
 // One depth solve, enqueued without host round trips: right-hand side, warm
 // start, residual, |b| on the device, the cooperative PCG loop, mean removal.
+// Unit-weight solves with precond = 2 take the direct cosine-transform solve
+// instead of the loop, then the same residual check and mean removal.
 template <bool WEIGHTED>
 static cudaError_t solve_once(Ctx &c) {
   const CG g = make_cg(c);
@@ -898,6 +910,19 @@ static cudaError_t solve_once(Ctx &c) {
   CGCtl *ctl = (CGCtl *)c.cg_ctl;
   CGAcc *acc = &c.dstats->cg;
   k_rhs<WEIGHTED><<<nb, kThreads, 0, c.stream>>>(g);
+  if (!WEIGHTED && c.opt.precond == 2 && c.sp_t) {
+    LAUNCH_CHECK();
+    cudaError_t e = launch_spectral(c, c.cg_b, c.cg_x);
+    if (e != cudaSuccess) return e;
+    k_residual<false><<<nb, kThreads, 0, c.stream>>>(g, S_RZ0);
+    k_cg_start<<<1, 32, 0, c.stream>>>(g, ctl);
+    k_direct_done<<<1, 1, 0, c.stream>>>(ctl, acc, c.opt.cg_tol);
+    k_sum_x<<<nb, kThreads, 0, c.stream>>>(g);
+    k_store_depth<<<nb, kThreads, 0, c.stream>>>(g, ctl);
+    c.stats.launches += 6;
+    LAUNCH_CHECK();
+    return cudaSuccess;
+  }
   k_load_x<<<nb, kThreads, 0, c.stream>>>(g);
   k_residual<WEIGHTED><<<nb, kThreads, 0, c.stream>>>(g, S_RZ0);
   k_cg_start<<<1, 32, 0, c.stream>>>(g, ctl);
@@ -908,7 +933,8 @@ static cudaError_t solve_once(Ctx &c) {
   MG mg = make_mg(c);
   if (WEIGHTED) mg.cscale = 1.0f;
   void *args[] = {(void *)&g, (void *)&ctl, (void *)&acc, (void *)&tol, (void *)&max_iter, (void *)&m, (void *)&mg};
-  const void *fn = c.opt.precond == 1 ? (const void *)k_cg_loop<1, WEIGHTED> : (const void *)k_cg_loop<0, WEIGHTED>;
+  // multigrid for precond 1, and for the solves the spectral form does not cover
+  const void *fn = c.opt.precond != 0 ? (const void *)k_cg_loop<1, WEIGHTED> : (const void *)k_cg_loop<0, WEIGHTED>;
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(kThreads), args, 0, c.stream);
   if (e != cudaSuccess) return e;
   k_sum_x<<<nb, kThreads, 0, c.stream>>>(g);
@@ -1085,7 +1111,7 @@ void cg_fill_job(Ctx &c, int nblk, int blk_begin, DevStats *ds, void *dst) {
   j.tol = c.opt.cg_tol;
   j.max_iter = c.opt.cg_max_iter;
   j.check = c.opt.cg_check_every > 0 ? c.opt.cg_check_every : 10;
-  j.pre = c.opt.precond == 1 ? 1 : 0;
+  j.pre = c.opt.precond != 0 ? 1 : 0;  // batched solves: multigrid for precond 1 and 2
   j.blk_begin = blk_begin;
   j.wh = c.mg_wh;
   j.wv = c.mg_wv;

@@ -18,7 +18,7 @@ def _corrupted(seed, H, W):
     return sc, n
 
 
-@pytest.mark.parametrize("precond", [0, 1])
+@pytest.mark.parametrize("precond", [0, 1, 2])
 @pytest.mark.parametrize("H,W,iters", [(33, 47, 3), (64, 64, 5), (2, 9, 2)])
 def test_irls_integrate_matches_oracle(lib, oracle_mod, precond, H, W, iters):
     sc, n = _corrupted(90 + H, H, W)

@@ -44,8 +44,8 @@ def test_ps_stage(lib, oracle_mod, case, f16):
     assert n1[..., 3].reshape(-1)[ok].min() > 0
 
 
-@pytest.mark.parametrize("precond", [0, 1])
-@pytest.mark.parametrize("H,W", [(64, 64), (37, 53), (256, 256), (2, 5), (3, 301)])
+@pytest.mark.parametrize("precond", [0, 1, 2])
+@pytest.mark.parametrize("H,W", [(64, 64), (37, 53), (256, 256), (2, 5), (3, 301), (2, 1030)])
 def test_integrate(lib, oracle_mod, H, W, precond):
     sc = scenes.mixed(H * 7 + W, H, W, K=3, C=1) if H > 3 else None
     rs = np.random.default_rng(H * W)
@@ -64,6 +64,29 @@ def test_integrate(lib, oracle_mod, H, W, precond):
     assert np.abs(d - want).max() <= 1e-4 * rng, (np.abs(d - want).max() / rng, st)
     assert abs(float(d.astype(np.float64).mean())) < 1e-6 * rng + 1e-9
     assert st["cg_rel_residual"] <= 1e-9
+
+
+@pytest.mark.parametrize("H,W", [(2, 2), (17, 1024), (512, 512), (1024, 1024), (45, 38)])
+def test_spectral_solve_is_direct(lib, oracle_mod, H, W):
+    """precond = 2: one direct cosine-transform solve (the oracle's method, computed
+    independently: FP64 transform products on the GPU, scipy's DCT on the host) lands
+    within the FP32 rounding of the stored depth."""
+    rs = np.random.default_rng(H + 3 * W)
+    X, Y = scenes.grid(H, W)
+    gx = 0.6 * np.sin(7 * X) * np.cos(5 * Y) + rs.normal(0, 0.05, (H, W))
+    gy = 0.5 * np.cos(6 * X + 2 * Y) + rs.normal(0, 0.05, (H, W))
+    normals = scenes.normals_from_gradient(gx, gy).astype(np.float32)
+    opt = lib.irtps_default_options()
+    assert opt.precond == 2
+    with lib.Context(H, W, scenes.ring_lights(3, 45.0), np.zeros((1, 2, 2), np.float32), opt) as ctx:
+        ctx.set_state(depth=np.zeros((H, W), np.float32), normals=normals)
+        ctx.integrate()
+        d = ctx.depth()
+        st = ctx.stats()
+    want = oracle_mod.poisson_solve(normals.astype(np.float64), 1.0 / W)
+    rng = max(np.ptp(want), 1e-12)
+    assert st["cg_iterations"] == 1 and st["cg_rel_residual"] <= 1e-10, st
+    assert np.abs(d - want).max() <= 2e-6 * max(rng, np.abs(want).max()), np.abs(d - want).max() / rng
 
 
 def test_integrate_quadric_exact(lib, oracle_mod):
