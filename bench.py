@@ -299,6 +299,8 @@ def run_batch(args):
     ctxs, imgs = [], []
     opt = irtps.irtps_default_options()
     opt.sampling = 1 if args.sampling == "shared" else 0
+    if args.early_escape is not None:
+        opt.early_escape = args.early_escape
     for i, (sc, _, _) in enumerate(objs):
         c = irtps.Context(sc.H, sc.W, sc.lights, sc.env, opt)
         c.set_stream(stream.cuda_stream)
@@ -467,6 +469,8 @@ def main():
                          "with 1, 2 and 3 traced reflections (outside the timed region)")
     ap.add_argument("--sampling", default="per_light", choices=["per_light", "shared"],
                     help="trace sampling: spp paths per (pixel, light), or per pixel for all lights")
+    ap.add_argument("--early-escape", type=int, choices=[0, 1], default=None,
+                    help="horizon bounds before each trace (default: the library's option default)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -494,6 +498,8 @@ def main():
     opt.sampling = 1 if args.sampling == "shared" else 0
     for key, val in WORKLOAD_OPTIONS.get(args.workload, {}).items():
         setattr(opt, key, val)
+    if args.early_escape is not None:
+        opt.early_escape = args.early_escape
     ctx = irtps.Context(H, W, sc.lights, sc.env, opt)
     ctx.set_stream(stream.cuda_stream)
     A0 = torch.empty((K, C, H, W), dtype=torch.float32, device=dev)
@@ -599,7 +605,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "H": H, "W": W, "K": K, "C": C, "spp": spp, "images": args.images,
                        "sampling": args.sampling, "trace_blocks_per_sm": tuning[0], "mip_cut": tuning[1],
-                       "options": WORKLOAD_OPTIONS.get(args.workload, {}),
+                       "options": dict(WORKLOAD_OPTIONS.get(args.workload, {}), early_escape=opt.early_escape),
                        "bounces": bounces, "irt_iterations_per_step": n_iter, "parallelism": f"replicas{world}",
                        "l2": "512 MB buffer written between timed steps"},
             "pixel_iters_per_s": P * n_iter * world * args.steps / (ms_all / 1e3),

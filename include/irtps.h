@@ -82,11 +82,12 @@ typedef struct irtps_options {
   int irls_iters;     /* integration by the Huber M-estimator: reweighting steps after the
                          least-squares solve (0 = least squares only) (0) */
   float irls_delta;   /* Huber threshold on the edge slope residual (H_b - H_a)/h - mean slope (0.05) */
-  int early_escape;   /* 1: before each trace, bound every pixel's horizon in eight octants of azimuth
-                         from the pyramid; a rising primary ray above it skips its march after the
-                         triangle test of its first cell (results unchanged, bit for bit).  Pays
-                         only at high sample counts: the bounds cost about as much as 20 samples
-                         per pixel and light save (0) */
+  int early_escape;   /* before a trace, bound every pixel's horizon in eight octants of azimuth
+                         from the max pyramid (a fixed scan of nodes around the pixel per level);
+                         a rising primary ray above it skips its march after the triangle test of
+                         its first cell (results unchanged, bit for bit).  0 off, 1 on, 2 where it
+                         pays: per-light sampling, at least 16 samples per item, and H W K >= 2^18
+                         work items (a smaller object cannot fill the GPU; in a batch any size) (2) */
   int fill_holes;     /* 1: the single-sample variant of Sec. IV (per-light sampling only): a (pixel,
                          light) none of whose samples hit the surface with its first segment has no
                          environment value (a hole); after every trace of the IRT loop (irtps_iterate,

@@ -148,6 +148,7 @@ int upload_trace(irtps_batch &b, const int *spp, const int *bounces, uint64_t se
     irtps::fill_obj_trace(c, o);
     o.f.levels = irtps::march_levels(c.levels, b.mip_cut);
     o.spp = spp[i];
+    if (!irtps::early_escape_on(c, spp[i], true)) o.hz = nullptr;  // bounds computed, not used
     o.bounces = bounces[i];
     o.key = make_uint2((uint32_t)seed ^ c.obj, (uint32_t)(seed >> 32));
     o.out = c.lbar;

@@ -148,7 +148,7 @@ int trace_into(Ctx &c, const int32_t *pixels, int n_pix, int spp, int bounces, u
   fill = fill && c.opt.fill_holes && !pixels && out == c.lbar;
   CK(irtps::build_pyramid(c), "pyramid build");
   if (!iter_from_device) STAGE(ST_TRACE, true);
-  CK(irtps::launch_horizon(c), "horizon bounds");
+  CK(irtps::launch_horizon(c, spp), "horizon bounds");
   CK(irtps::launch_trace(c, pixels, n_pix, spp, bounces, seed, iter, stream_tag, out, rec, iter_from_device, fill),
      "trace launch");
   if (!iter_from_device) STAGE(ST_TRACE, false);
@@ -277,7 +277,7 @@ void irtps_default_options(irtps_options *opt) {
   opt->sampling = 0;
   opt->irls_iters = 0;
   opt->irls_delta = 0.05f;
-  opt->early_escape = 0;
+  opt->early_escape = 2;
   opt->fill_holes = 0;
 }
 
@@ -314,6 +314,8 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
     return bail(fail(c, IRTPS_EINVAL, "create: sampling must be 0 (per light) or 1 (light-shared)"));
   if (c.opt.irls_iters < 0 || c.opt.irls_iters > 100 || !(c.opt.irls_delta > 0.0f))
     return bail(fail(c, IRTPS_EINVAL, "create: irls_iters in 0..100 and irls_delta > 0"));
+  if (c.opt.early_escape < 0 || c.opt.early_escape > 2)
+    return bail(fail(c, IRTPS_EINVAL, "create: early_escape must be 0, 1 or 2"));
   if (c.opt.fill_holes != 0 && c.opt.fill_holes != 1)
     return bail(fail(c, IRTPS_EINVAL, "create: fill_holes must be 0 or 1"));
   if (c.opt.fill_holes && c.opt.sampling != 0)

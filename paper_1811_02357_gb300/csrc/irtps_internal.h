@@ -189,7 +189,20 @@ constexpr int kPyrThreads = 256;
 
 // trace.cu
 cudaError_t build_pyramid(Ctx &c);
-cudaError_t launch_horizon(Ctx &c);  // horizon bounds of the current surface (after the pyramid)
+// Early escape: option 1 always; option 2 where it was measured to pay: per-light
+// sampling with at least kEarlyEscapeMinSpp samples per item (fewer do not pay for the
+// bounds), on a grid whose work items fill the GPU - at least kEarlyEscapeMinItems
+// in a single-object trace (with fewer the launch waits on its longest items, which
+// the per-ray test only lengthens), any size in a batch (whose queue fills it).
+constexpr int kEarlyEscapeMinSpp = 16;
+constexpr long long kEarlyEscapeMinItems = 1ll << 18;
+inline bool early_escape_on(const Ctx &c, int spp, bool batched = false) {
+  if (!c.horizon || c.opt.early_escape == 0) return false;
+  if (c.opt.early_escape == 1) return true;
+  return c.opt.sampling == 0 && spp >= kEarlyEscapeMinSpp &&
+         (batched || (long long)c.H * c.W * c.K >= kEarlyEscapeMinItems);
+}
+cudaError_t launch_horizon(Ctx &c, int spp);  // horizon bounds of the current surface (after the pyramid)
 void fill_pyr_obj(const Ctx &c, PyrObj &o);
 cudaError_t build_pyramid_batch(cudaStream_t s, const PyrObj *d_objs, int n, int levels, const int *blocks);
 cudaError_t launch_horizon_batch(cudaStream_t s, const PyrObj *d_objs, int n, int blocks);

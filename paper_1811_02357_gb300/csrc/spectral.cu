@@ -9,10 +9,10 @@
 //
 // B and x the H x W arrays of b and x, which is the mean-zero least-squares
 // surface.  Four dense products of FP64 matrices (an H x H or W x W transform
-// against the H x W data): 4 H W (H + W) multiply-adds, done by one tiled FP64
+// against the H x W data): 2 H W (H + W) multiply-adds, done by one tiled FP64
 // kernel; the division by the eigenvalues is fused into the second product.
-// GB300's FP64 rate bounds it (about 0.85 ms at 512 x 512), far below the
-// barrier-bound multigrid PCG it replaces for unit weights at these sizes.
+// GB300's FP64 rate bounds it (about 1 ms at 512 x 512, 7 ms at 1024 x 1024),
+// below the barrier-bound multigrid PCG it replaces for unit weights up to 1024.
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -23,9 +23,12 @@ namespace irtps {
 
 namespace {
 
-constexpr int kTile = 32;      // output tile (rows and columns)
-constexpr int kTileK = 32;     // depth of one shared-memory stage
-constexpr int kGemmThreads = 256;
+// 16 x 16 output tiles, one output per thread: GB300's FP64 rate (about two
+// multiply-adds per clock per SM) is far below what shared memory feeds, so the
+// small tile costs nothing and spreads a 512 x 512 product over 1024 blocks
+// (about 7 per SM) instead of leaving whole SMs idle or doubly loaded.
+constexpr int kTile = 16;      // output tile (rows and columns) and depth of one shared-memory stage
+constexpr int kGemmThreads = kTile * kTile;
 
 // D = op(A) op(B), M x N, inner dimension K; op(A)(m, k) = TA ? A[k lda + m] : A[m lda + k],
 // op(B)(k, n) = TB ? B[n ldb + k] : B[k ldb + n].  SCALE: D(m, n) /= mu[m] + nu[n], D(0, 0) = 0.
@@ -35,47 +38,34 @@ __global__ void __launch_bounds__(kGemmThreads) k_dgemm(int M, int N, int K, con
                                                          double *__restrict__ D, int ldd,
                                                          const double *__restrict__ mu,
                                                          const double *__restrict__ nu) {
-  __shared__ double As[kTileK][kTile + 1];
-  __shared__ double Bs[kTileK][kTile + 1];
+  __shared__ double As[kTile][kTile + 1];  // [k][m]
+  __shared__ double Bs[kTile][kTile + 1];  // [k][n]
   const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 2 x 2 outputs per thread
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-  for (int k0 = 0; k0 < K; k0 += kTileK) {
-#pragma unroll
-    for (int r = 0; r < (kTile * kTileK) / kGemmThreads; ++r) {
-      const int e = threadIdx.x + r * kGemmThreads;
-      // A tile: the contiguous index of the source runs fastest across the threads
-      int mm, kk;
-      if (TA) { kk = e / kTile; mm = e - kk * kTile; } else { mm = e / kTileK; kk = e - mm * kTileK; }
+  const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < K; k0 += kTile) {
+    // the contiguous index of each source runs fastest across the threads
+    {
+      const int mm = TA ? tx : ty, kk = TA ? ty : tx;
       const int gm = m0 + mm, gk = k0 + kk;
       As[kk][mm] = (gm < M && gk < K) ? (TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : 0.0;
-      int nn;
-      if (TB) { nn = e / kTileK; kk = e - nn * kTileK; } else { kk = e / kTile; nn = e - kk * kTile; }
-      const int gn = n0 + nn, gk2 = k0 + kk;
-      Bs[kk][nn] = (gn < N && gk2 < K) ? (TB ? B[(size_t)gn * ldb + gk2] : B[(size_t)gk2 * ldb + gn]) : 0.0;
+    }
+    {
+      const int nn = TB ? ty : tx, kk = TB ? tx : ty;
+      const int gn = n0 + nn, gk = k0 + kk;
+      Bs[kk][nn] = (gn < N && gk < K) ? (TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn]) : 0.0;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < kTileK; ++kk) {
-      const double a0 = As[kk][2 * ty], a1 = As[kk][2 * ty + 1];
-      const double b0 = Bs[kk][2 * tx], b1 = Bs[kk][2 * tx + 1];
-      acc[0][0] = fma(a0, b0, acc[0][0]);
-      acc[0][1] = fma(a0, b1, acc[0][1]);
-      acc[1][0] = fma(a1, b0, acc[1][0]);
-      acc[1][1] = fma(a1, b1, acc[1][1]);
-    }
+#pragma unroll
+    for (int kk = 0; kk < kTile; ++kk) acc = fma(As[kk][ty], Bs[kk][tx], acc);
     __syncthreads();
   }
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const int m = m0 + 2 * ty + a, n = n0 + 2 * tx + b;
-      if (m >= M || n >= N) continue;
-      double v = acc[a][b];
-      if (SCALE) v = (m == 0 && n == 0) ? 0.0 : v / (mu[m] + nu[n]);
-      D[(size_t)m * ldd + n] = v;
-    }
+  const int m = m0 + ty, n = n0 + tx;
+  if (m < M && n < N) {
+    double v = acc;
+    if (SCALE) v = (m == 0 && n == 0) ? 0.0 : v / (mu[m] + nu[n]);
+    D[(size_t)m * ldd + n] = v;
+  }
 }
 
 template <bool TA, bool TB, bool SCALE>

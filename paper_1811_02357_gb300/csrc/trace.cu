@@ -136,12 +136,25 @@ cudaError_t build_pyramid(Ctx &c) {
 }
 
 // ---------------------------------------------------------------------------
-// Horizon bounds (see octant_of in geom.cuh): one thread per pixel, a depth-first
-// branch-and-bound over the max pyramid for all eight octants at once.  A node
-// at distance d from p (d > 0) bounds every cell in it by (node max - H_p) / d; it
-// is opened only while that exceeds the best bound found so far in some octant it
-// meets.  FP32 with every rounding directed toward a larger bound.
+// Horizon bounds (see octant_of in geom.cuh): one thread per pixel, all eight
+// octants at once, a fixed scan of the max pyramid.  At level l the thread looks
+// at the nodes within kHorizonRing nodes of p's own node, except those lying
+// wholly inside the window of level l - 1 (covered by finer nodes); the windows
+// are nested and the top level covers the grid, so every cell is covered by
+// some scanned node, and cells touching p (tested exactly by the march) only at
+// level 0, where they are left out.  A node bounds the cells it must cover - its
+// part outside the finer window - by (node max - H_p) / d, d the least distance
+// from p to that part (to a node's part beyond the window's left edge, at least
+// that edge's distance from p, and so on).  The bound is not tight (far cells are
+// judged by their coarse nodes) but costs a fixed number of nodes per level.
+// FP32 with every rounding directed toward a larger bound.
 // ---------------------------------------------------------------------------
+#ifndef IRTPS_HORIZON_RING
+#define IRTPS_HORIZON_RING 4
+#endif
+constexpr int kHorizonRing = IRTPS_HORIZON_RING;  // >= 2: nodes touching p stay inside the finer window
+static_assert(kHorizonRing >= 2, "a node touching p must lie inside the finer window");
+
 __device__ __forceinline__ void horizon_pixel(const float *__restrict__ depth, const float *__restrict__ pmax,
                                               const int *off, const int *lw, int H, int W, int levels, int p,
                                               float *__restrict__ hz) {
@@ -151,72 +164,64 @@ __device__ __forceinline__ void horizon_pixel(const float *__restrict__ depth, c
   float best[8];
 #pragma unroll
   for (int o = 0; o < 8; ++o) best[o] = -INFINITY;
-  unsigned stack[64];  // level << 28 | ny << 14 | nx
-  int top = 0;
-  bool full = false;  // the stack ran out: no bound for this pixel
-  stack[top++] = (unsigned)(levels - 1) << 28;
-  while (top > 0) {
-    const unsigned e = stack[--top];
-    const int l = (int)(e >> 28), ny = (int)((e >> 14) & 0x3FFF), nx = (int)(e & 0x3FFF);
-    const int X0 = nx << l, Y0 = ny << l;
-    const int X1 = min(X0 + (1 << l), Wc), Y1 = min(Y0 + (1 << l), Hc);
-    const int a1 = X0 - pj, a2 = X1 - pj, b1 = Y0 - pi, b2 = Y1 - pi;
-    const int dx = max(max(a1, -a2), 0), dy = max(max(b1, -b2), 0);
-    bool meets[8], any = false;
+  bool none = false;                        // a node touching p outside the finer window: no bound
+  int ix0 = 0, ix1 = 0, iy0 = 0, iy1 = 0;   // cells of the previous level's window (empty at level 0)
+  const int ci = min(pi, Hc - 1), cj = min(pj, Wc - 1);  // a cell at vertex p
+  for (int l = 0; l < levels && !none; ++l) {
+    const int nw = lw[l], nh = ((Hc - 1) >> l) + 1;
+    const int cx = cj >> l, cy = ci >> l;
+    const int x_lo = max(cx - kHorizonRing, 0), x_hi = min(cx + kHorizonRing, nw - 1);
+    const int y_lo = max(cy - kHorizonRing, 0), y_hi = min(cy + kHorizonRing, nh - 1);
+    for (int ny = y_lo; ny <= y_hi && !none; ++ny) {
+      const int Y0 = ny << l, Y1 = min(Y0 + (1 << l), Hc);
+      const int b1 = Y0 - pi, b2 = Y1 - pi;
+      const int dy = max(max(b1, -b2), 0);
+      const bool y_in = Y0 >= iy0 && Y1 <= iy1;
+      for (int nx = x_lo; nx <= x_hi; ++nx) {
+        const int X0 = nx << l, X1 = min(X0 + (1 << l), Wc);
+        if (y_in && X0 >= ix0 && X1 <= ix1) continue;  // covered by the finer levels
+        const int a1 = X0 - pj, a2 = X1 - pj;
+        const int dx = max(max(a1, -a2), 0);
+        if (dx == 0 && dy == 0 && l == 0) continue;  // a cell touching p
+        // squared distance to the node's part outside the finer window
+        int d2i = dx * dx + dy * dy;
+        if (l > 0) {
+          const int big = 1 << 30;
+          int hx = big, vy = big;  // across its columns beyond the window, its rows beyond the window
+          if (X0 < ix0) hx = min(hx, max(dx, pj - ix0));
+          if (X1 > ix1) hx = min(hx, max(dx, ix1 - pj));
+          if (Y0 < iy0) vy = min(vy, max(dy, pi - iy0));
+          if (Y1 > iy1) vy = min(vy, max(dy, iy1 - pi));
+          d2i = min(hx < big ? hx * hx + dy * dy : big, vy < big ? dx * dx + vy * vy : big);
+        }
+        if (d2i == 0) {
+          none = true;
+          break;
+        }
+        bool meets[8], any = false;
 #pragma unroll
-    for (int o = 0; o < 8; ++o) {
-      meets[o] = wedge_meets(o, a1, a2, b1, b2);
-      any = any || meets[o];
-    }
-    if (!any) continue;
-    const float nmax = __ldg(pmax + off[l] + ny * lw[l] + nx);
-    if (dx == 0 && dy == 0) {  // the node touches p: no bound from it, look inside (cells touching p are left out)
-      if (l == 0) continue;
-    } else {
-      // (nmax - zp) / distance, every rounding toward a larger bound
-      const float num = __fsub_ru(nmax, zp);
-      const float d2 = __fmaf_ru((float)dx, (float)dx, __fmul_ru((float)dy, (float)dy));
-      const float dist = num >= 0.0f ? __fsqrt_rd(__fmaf_rd((float)dx, (float)dx, __fmul_rd((float)dy, (float)dy)))
-                                     : __fsqrt_ru(d2);
-      const float bnd = __fdiv_ru(num, dist);
-      bool open = false;
-#pragma unroll
-      for (int o = 0; o < 8; ++o) open = open || (meets[o] && bnd > best[o]);
-      if (!open) continue;
-      if (l == 0) {
+        for (int o = 0; o < 8; ++o) {
+          meets[o] = wedge_meets(o, a1, a2, b1, b2);
+          any = any || meets[o];
+        }
+        if (!any) continue;
+        const float nmax = __ldg(pmax + off[l] + ny * nw + nx);
+        // (nmax - zp) / distance, every rounding toward a larger bound
+        const float num = __fsub_ru(nmax, zp);
+        const float dist = num >= 0.0f ? __fsqrt_rd((float)d2i) : __fsqrt_ru((float)d2i);  // d2i < 2^24: exact
+        const float bnd = __fdiv_ru(num, dist);
 #pragma unroll
         for (int o = 0; o < 8; ++o)
           if (meets[o]) best[o] = fmaxf(best[o], bnd);
-        continue;
       }
     }
-    // children, the farthest pushed first so that the nearest is opened first
-    const int cl = l - 1, cw = ((Wc - 1) >> cl) + 1, ch = ((Hc - 1) >> cl) + 1;
-    unsigned kid[4];
-    int kd[4], nk = 0;
-    for (int q = 0; q < 4; ++q) {
-      const int cx = 2 * nx + (q & 1), cy = 2 * ny + (q >> 1);
-      if (cx >= cw || cy >= ch) continue;
-      const int u1 = (cx << cl) - pj, u2 = min((cx + 1) << cl, Wc) - pj;
-      const int v1 = (cy << cl) - pi, v2 = min((cy + 1) << cl, Hc) - pi;
-      const int ddx = max(max(u1, -u2), 0), ddy = max(max(v1, -v2), 0);
-      kid[nk] = ((unsigned)cl << 28) | ((unsigned)cy << 14) | (unsigned)cx;
-      kd[nk] = ddx * ddx + ddy * ddy;
-      ++nk;
-    }
-    for (int a = 1; a < nk; ++a)  // sort by distance, nearest last
-      for (int b2i = a; b2i > 0 && kd[b2i] > kd[b2i - 1]; --b2i) {
-        const int td = kd[b2i]; kd[b2i] = kd[b2i - 1]; kd[b2i - 1] = td;
-        const unsigned tk = kid[b2i]; kid[b2i] = kid[b2i - 1]; kid[b2i - 1] = tk;
-      }
-    if (top + nk > 64) {
-      full = true;
-      break;
-    }
-    for (int a = 0; a < nk; ++a) stack[top++] = kid[a];
+    ix0 = x_lo << l;
+    ix1 = min((x_hi + 1) << l, Wc);
+    iy0 = y_lo << l;
+    iy1 = min((y_hi + 1) << l, Hc);
   }
 #pragma unroll
-  for (int o = 0; o < 8; ++o) hz[(size_t)o * P + p] = full ? INFINITY : best[o];
+  for (int o = 0; o < 8; ++o) hz[(size_t)o * P + p] = none ? INFINITY : best[o];
 }
 
 // levels: of the full pyramid (its top node covers the grid), whatever the march uses.
@@ -250,8 +255,8 @@ __global__ void k_horizon_b(const PyrObj *__restrict__ objs, int n) {
   if (p < o.H * o.W) horizon_pixel(o.depth, o.pmax, o.off, o.lw, o.H, o.W, o.levels, p, o.hz);
 }
 
-cudaError_t launch_horizon(Ctx &c) {
-  if (!c.horizon) return cudaSuccess;
+cudaError_t launch_horizon(Ctx &c, int spp) {
+  if (!early_escape_on(c, spp)) return cudaSuccess;
   const int P = c.H * c.W;
   k_horizon<<<(P + 127) / 128, 128, 0, c.stream>>>(c.field(), c.levels, c.horizon);
   ++c.stats.launches;
@@ -806,6 +811,7 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
   a.one.key = make_uint2((uint32_t)seed ^ c.obj, (uint32_t)(seed >> 32));
   a.one.out = out;
   a.one.hole = mark_holes && !shared && !pixels ? c.holes : nullptr;
+  if (!early_escape_on(c, spp)) a.one.hz = nullptr;
   a.objs = nullptr;
   a.n_obj = 1;
   a.pixels = pixels;

@@ -40,6 +40,7 @@ def test_default_options(binding):
     assert o.shadow_rays == 1 and abs(o.tau_lo - 0.02) < 1e-8 and abs(o.tau_hi - 0.98) < 1e-7
     assert o.cond_max == 1e8 and abs(o.nz_min - 0.05) < 1e-8 and o.cg_tol == 1e-9
     assert o.stop_tol == 0.0 and o.precond == 2 and o.use_graph == 0 and o.sampling == 0
+    assert o.irls_iters == 0 and abs(o.irls_delta - 0.05) < 1e-8 and o.early_escape == 2 and o.fill_holes == 0
 
 
 def test_struct_layouts_match_header(binding, tmp_path):

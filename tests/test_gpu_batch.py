@@ -254,3 +254,31 @@ def test_batch_robust_integration(lib, oracle_mod):
     finally:
         for c in ctxs:
             c.close()
+
+
+def test_batch_early_escape_keeps_every_bit(lib, oracle_mod):
+    """Batched horizon bounds (one launch over all objects) let rising primary rays
+    skip their march; every object's Lbar and normals stay those of the plain batch."""
+    spec = SMALL + [(66, 64, 48, 12, 8, 2)]
+    scs = _scenes(spec)
+    A = _images(oracle_mod, scs, 13)
+    spp = [s[4] for s in spec]
+    bounces = [s[5] for s in spec]
+    out, visits = [], []
+    for early in (0, 1):
+        opt = lib.irtps_default_options()
+        opt.early_escape = early
+        ctxs = [lib.Context(sc.H, sc.W, sc.lights, sc.env, opt) for sc in scs]
+        try:
+            for c, a in zip(ctxs, A):
+                c.set_images(a)
+            with lib.Batch(ctxs) as b:
+                b.iterate(1, spp, bounces, 29)
+                visits.append(b.stats()["node_visits"])
+                out.append([(c.indirect(), c.normals()) for c in ctxs])
+        finally:
+            for c in ctxs:
+                c.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert visits[1] < visits[0]

@@ -17,6 +17,13 @@ pytestmark = pytest.mark.gpu
 RTOL = 1e-4
 
 
+def _opts(lib, **kw):
+    opt = lib.irtps_default_options()
+    for k, v in kw.items():
+        setattr(opt, k, v)
+    return opt
+
+
 def _ctx(lib, sc):
     ctx = lib.Context(sc.H, sc.W, sc.lights, sc.env)
     ctx.set_state(sc.depth, sc.normals, sc.albedo)
@@ -151,5 +158,54 @@ def test_early_escape_keeps_every_bit(lib, oracle_mod, case):
             out.append((lb, rec, ctx.indirect(), ctx.stats()))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     assert np.array_equal(out[0][2], out[1][2])
+    assert out[0][3]["segments"] == out[1][3]["segments"]
+    assert out[1][3]["node_visits"] < out[0][3]["node_visits"]
+
+
+def test_early_escape_automatic_mode(lib):
+    """Option 2 (the default) bounds horizons only for per-light traces of 16 or more
+    samples per item over at least 2^18 work items; otherwise the trace runs without
+    them.  Results never change."""
+    sc = scenes.mixed(41, 160, 160, K=12, C=3)  # 307200 items
+    res = {}
+    for early in (0, 2):
+        opt = lib.irtps_default_options()
+        opt.early_escape = early
+        with lib.Context(sc.H, sc.W, sc.lights, sc.env, opt) as ctx:
+            ctx.set_state(sc.depth, sc.normals, sc.albedo)
+            for spp in (8, 16):
+                ctx.trace(spp, 2, 5, 3)
+                res[early, spp] = (ctx.indirect(), ctx.stats()["node_visits"])
+    assert lib.irtps_default_options().early_escape == 2
+    for spp in (8, 16):
+        assert np.array_equal(res[0, spp][0], res[2, spp][0])
+    assert res[2, 8][1] == res[0, 8][1]
+    assert res[2, 16][1] < res[0, 16][1]
+    small = CASES["mixed_45x38_c3"]()  # 8550 items: left off
+    with lib.Context(small.H, small.W, small.lights, small.env) as a, lib.Context(
+            small.H, small.W, small.lights, small.env, _opts(lib, early_escape=0)) as b:
+        for c in (a, b):
+            c.set_state(small.depth, small.normals, small.albedo)
+            c.trace(16, 2, 5, 3)
+        assert a.stats()["node_visits"] == b.stats()["node_visits"]
+
+
+def test_early_escape_keeps_every_bit_full_size(lib):
+    """The bench's 512x512 surface: the whole field's Lbar and the records of a pixel
+    sample are those of the plain march."""
+    sc = scenes.bumps_512()
+    rng = np.random.default_rng(3)
+    pix = np.sort(rng.choice(sc.H * sc.W, 2048, replace=False)).astype(np.int32)
+    out = []
+    for early in (0, 1):
+        opt = lib.irtps_default_options()
+        opt.early_escape = early
+        with lib.Context(sc.H, sc.W, sc.lights, sc.env, opt) as ctx:
+            ctx.set_state(sc.depth, sc.normals, sc.albedo)
+            lb, rec = ctx.trace_pixels(pix, 8, 2, 11, 1, records=True)
+            ctx.trace(4, 2, 11, 1)
+            out.append((lb, rec, ctx.indirect(), ctx.stats()))
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
     assert out[0][3]["segments"] == out[1][3]["segments"]
     assert out[1][3]["node_visits"] < out[0][3]["node_visits"]
