@@ -71,7 +71,7 @@ SM_COUNT = 152
 LANES_PER_SM = 128
 # DRAM bytes (read + write) of one trace launch of a workload, from the ncu capture summarised in
 # profiles/k_trace_bumps512_dram.md (the kernel has not changed since)
-TRACE_DRAM_BYTES = {"bumps_512": 10.24e6 + 1.79e6}
+TRACE_DRAM_BYTES = {"bumps_512": 19.29e6 + 2.27e6}
 # the same for light-shared sampling (profiles/k_trace_shared_bumps512_dram.md)
 TRACE_DRAM_BYTES_SHARED = {"bumps_512": 322.63e6 + 270.69e6}
 
