@@ -160,7 +160,8 @@ int irtps_iterate(irtps_ctx *ctx, int n_iter, int spp, int bounces, uint64_t see
 int irtps_trace(irtps_ctx *ctx, int spp, int bounces, uint64_t seed, uint32_t iteration, uint32_t stream_tag);
 /* Subtract + PS: images minus albedo * indirect, then Eq. 4 per pixel. */
 int irtps_solve_normals(irtps_ctx *ctx);
-/* Integrate the current normals into the depth (warm start from the current depth). */
+/* Integrate the current normals into the depth (the CG solves warm-start from the current depth;
+ * the direct solve of precond = 2 needs no start). */
 int irtps_integrate(irtps_ctx *ctx);
 
 /* Trace a list of pixels only (host arrays): out_lbar K x C x n_pix;
