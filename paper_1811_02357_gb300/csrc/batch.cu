@@ -419,6 +419,7 @@ int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int
   std::vector<irtps::PyrObj> pyr(n_obj);
   for (int i = 0; i < n_obj; ++i) {
     irtps::fill_pyr_obj(objs[i]->c, pyr[i]);
+    if (!irtps::early_escape_possible(objs[i]->c)) pyr[i].hz = nullptr;  // no trace of it would read them
     b.pyr_levels = std::max(b.pyr_levels, objs[i]->c.levels);
   }
   for (int i = 0; i < n_obj; ++i) {  // horizon bounds: 128 pixels per block for objects that keep them

@@ -196,6 +196,10 @@ cudaError_t build_pyramid(Ctx &c);
 // the per-ray test only lengthens), any size in a batch (whose queue fills it).
 constexpr int kEarlyEscapeMinSpp = 16;
 constexpr long long kEarlyEscapeMinItems = 1ll << 18;
+// whether some trace of the context may use the bounds (option 1, or option 2 with per-light sampling)
+inline bool early_escape_possible(const Ctx &c) {
+  return c.horizon && (c.opt.early_escape == 1 || (c.opt.early_escape == 2 && c.opt.sampling == 0));
+}
 inline bool early_escape_on(const Ctx &c, int spp, bool batched = false) {
   if (!c.horizon || c.opt.early_escape == 0) return false;
   if (c.opt.early_escape == 1) return true;
