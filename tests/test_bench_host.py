@@ -4,6 +4,7 @@
   paper's evaluation measures (height, albedo and normal error), on random estimates.
 * The batched workload follows its recipe: 64 objects, sides log-uniform in 96..1024,
   K in {4, 8, 16, 32}, spp in {64, 128, 256}, bounces in {1, 2}.
+* The workload table is self-consistent (scene factories, option names, traffic entries).
 """
 import os
 import sys
@@ -43,3 +44,20 @@ def test_batch_recipe():
     # log-uniform: about half of the sides below the geometric mean of the range
     assert 0.3 < (sides < np.sqrt(96 * 1024)).mean() < 0.7
     assert len({s[0] for s in spec}) == 64  # every object its own scene seed
+
+
+def test_workload_table_is_consistent():
+    """Every workload names a scene factory, its options are fields of irtps_options, and
+    the traced-roofline traffic table only names workloads that exist."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1811_02357_gb300 import irtps
+    fields = {name for name, _ in irtps.irtps_options._fields_}
+    for name, (factory, kw, spp, bounces, n_iter, rspp, rb) in bench.WORKLOADS.items():
+        assert callable(getattr(scenes, factory)), name
+        assert n_iter >= 1 and rspp >= 1 and rb in (1, 2, 3), name
+        assert spp is None or (spp >= 1 and bounces in (1, 2, 3)), name
+    for name, opts in bench.WORKLOAD_OPTIONS.items():
+        assert name in bench.WORKLOADS and set(opts) <= fields, name
+    for table in (bench.TRACE_DRAM_BYTES, bench.TRACE_DRAM_BYTES_SHARED):
+        assert set(table) <= set(bench.WORKLOADS)
