@@ -87,6 +87,7 @@ def _load():
             lib.oracle_tri_hit.argtypes = [i32, P, i32, P]
             lib.oracle_intersect.argtypes = [i32, i32, P, i32, P, i32, i32, P, P]
             lib.oracle_env_lookup.argtypes = [P, i32, i32, i32, i32, P, P]
+            lib.oracle_hit_pixels.argtypes = [i32, i32, P, i32, P, i32, P]
             lib.oracle_trace.argtypes = [i32, i32, i32, i32, P, P, P, P, P, i32, i32, P, i32, i32, i32,
                                          u64, u32, u32, u32, i32, i32, i32, P, P, P]
             lib.oracle_trace.restype = i32
@@ -170,6 +171,18 @@ def intersect(depth, rays, fp32=False, brute=False):
     tri = np.zeros(r.shape[0], np.int64)
     lib.oracle_intersect(H, W, _ptr(d), r.shape[0], _ptr(r), int(fp32), int(brute), _ptr(t), _ptr(tri))
     return t, tri
+
+
+def hit_pixels(depth, rays, fp32=True):
+    """Pixel index the trace shades at each ray's closest hit (nearest mesh vertex in x-y,
+    ties to the lower index), or -1 for an escaping ray; rays (n, 6) in grid coordinates."""
+    lib = _load()
+    d = _c(depth, np.float32)
+    H, W = d.shape
+    r = _c(rays, np.float64).reshape(-1, 6)
+    out = np.zeros(r.shape[0], np.int64)
+    lib.oracle_hit_pixels(H, W, _ptr(d), r.shape[0], _ptr(r), int(fp32), _ptr(out))
+    return out
 
 
 def env_lookup(env, dirs, c=0):

@@ -364,6 +364,17 @@ inline int nearest_index(T q, int n) {
   return std::min(n - 1, std::max(0, v));
 }
 
+// Hit point o + t d of a march (grid coordinates) and the pixel whose shading the
+// path reads there: the mesh vertex nearest in x-y, ties to the lower index.
+template <class T>
+inline V3<T> hit_point(const V3<T> &o, const V3<T> &d, T t) {
+  return {o.x + t * d.x, o.y + t * d.y, o.z + t * d.z};
+}
+template <class T>
+inline size_t hit_pixel(const V3<T> &q, int H, int W) {
+  return (size_t)nearest_index<T>(q.y, H) * W + nearest_index<T>(q.x, W);
+}
+
 template <class T>
 inline T eps_lift(int W) {
   return (T)1e-3 / (T)W;
@@ -414,9 +425,8 @@ void trace_path(const Scene &sc, int p, int k, int s, int B, uint32_t iter, uint
       }
       return;
     }
-    const V3<T> q = {o.x + h.t * dg.x, o.y + h.t * dg.y, o.z + h.t * dg.z};
-    const int qi = nearest_index<T>(q.y, H), qj = nearest_index<T>(q.x, W);
-    const size_t qp = (size_t)qi * W + qj;
+    const V3<T> q = hit_point<T>(o, dg, h.t);
+    const size_t qp = hit_pixel<T>(q, H, W);
     const V3<T> nq = {(T)sc.nrm[4 * qp + 0], (T)sc.nrm[4 * qp + 1], (T)sc.nrm[4 * qp + 2]};
     const V3<T> o2 = {q.x, q.y, q.z + eps};
     int vis = -1;
@@ -512,9 +522,8 @@ void trace_path_shared(const Scene &sc, int p, int s, int B, uint32_t iter, uint
         for (int k = 0; k <= K; ++k) r[k] = -1;
       return;
     }
-    const V3<T> q = {o.x + h.t * dg.x, o.y + h.t * dg.y, o.z + h.t * dg.z};
-    const int qi = nearest_index<T>(q.y, H), qj = nearest_index<T>(q.x, W);
-    const size_t qp = (size_t)qi * W + qj;
+    const V3<T> q = hit_point<T>(o, dg, h.t);
+    const size_t qp = hit_pixel<T>(q, H, W);
     const V3<T> nq = {(T)sc.nrm[4 * qp + 0], (T)sc.nrm[4 * qp + 1], (T)sc.nrm[4 * qp + 2]};
     const V3<T> o2 = {q.x, q.y, q.z + eps};
     if (r) r[0] = (int32_t)qp;
@@ -682,6 +691,28 @@ void oracle_intersect(int H, int W, const float *depth, int n, const double *ray
       const Hit<double> h = brute ? brute_force<double>(f, o, d) : march<double>(f, o, d);
       out_t[i] = h.hit ? h.t : NAN;
       out_tri[i] = h.hit ? h.tri : -1;
+    }
+  }
+}
+
+// Hit pixel of n rays (origin, direction in grid coordinates; 6 doubles each)
+// as the trace takes it: the march's closest hit, its point o + t d and the
+// nearest mesh vertex (ties to the lower index); -1 when the ray escapes.
+void oracle_hit_pixels(int H, int W, const float *depth, int n, const double *rays, int fp32, int64_t *out) {
+  Field f{H, W, depth, -std::numeric_limits<float>::infinity()};
+  for (size_t i = 0; i < (size_t)H * W; ++i) f.zmax = std::max(f.zmax, depth[i]);
+  for (int i = 0; i < n; ++i) {
+    const double *r = rays + 6 * i;
+    if (fp32) {
+      const V3<float> o = {(float)r[0], (float)r[1], (float)r[2]};
+      const V3<float> d = {(float)r[3], (float)r[4], (float)r[5]};
+      const Hit<float> h = march<float>(f, o, d);
+      out[i] = h.hit ? (int64_t)hit_pixel<float>(hit_point<float>(o, d, h.t), H, W) : -1;
+    } else {
+      const V3<double> o = {r[0], r[1], r[2]};
+      const V3<double> d = {r[3], r[4], r[5]};
+      const Hit<double> h = march<double>(f, o, d);
+      out[i] = h.hit ? (int64_t)hit_pixel<double>(hit_point<double>(o, d, h.t), H, W) : -1;
     }
   }
 }
