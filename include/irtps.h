@@ -97,6 +97,12 @@ typedef struct irtps_options {
                          confidence blends with the 2x linear upsampling of the coarser level back
                          down; known pixels keep their values, a light without known pixels keeps
                          its traced values) (0) */
+  int ps_tensor;      /* subtract + PS (Eq. 4) of a single context: 0 the contraction pinv(L) I on the
+                         FP32 pipes (four pixels a thread, vector loads); 1 on the tensor cores
+                         (tcgen05, 128 pixels a tile, BF16 hi + lo split of I and pinv(L), FP32
+                         accumulation: I_hi P_hi + I_lo P_hi + I_hi P_lo).  Row masks and masked pixels
+                         are decided and solved identically in both (FP32 masks, FP64 3x3 solves).
+                         Batches use the FP32 form (0) */
 } irtps_options;
 
 /* Counters of the last irtps_iterate / irtps_trace / irtps_integrate call. */
@@ -221,10 +227,14 @@ int irtps_interpolate_holes(float *values, const uint8_t *holes, int K, int C, i
  * counterpart: this entry exists for callers that cannot allocate device memory
  * when they need the surface (a host framework that owns the whole device pool
  * through its own allocator, or a latency-critical loop that cannot accept the
- * device-wide synchronisation of cudaMalloc / cudaFree).  It runs the same solve
- * as irtps_integrate, with its working vectors in one file-scope device array
- * that holds at most 512 x 512 = 262144 pixels (about 11 MB, kept by every GPU
- * that loads the library until the process exits).
+ * device-wide synchronisation of cudaMalloc / cudaFree).  It always runs the
+ * unweighted least-squares solve by Jacobi-preconditioned CG (FP32 vectors, the
+ * FP64 residual refreshed every 10 iterations), whatever the options of any
+ * context, so its surface agrees with irtps_integrate (which by default solves
+ * directly by the cosine transform) to within the solver tolerance, not bit for
+ * bit.  Its working vectors live in one file-scope device array that holds at
+ * most 512 x 512 = 262144 pixels (about 11 MB, kept by every GPU that loads the
+ * library until the process exits).
  *   normals : device, H x W x 4 float (nx, ny, nz, unused), read only
  *   depth   : device, H x W float; in: warm start, out: the surface, mean 0
  *   nz_min, tol, max_iter: as irtps_options.nz_min, cg_tol, cg_max_iter
@@ -232,10 +242,12 @@ int irtps_interpolate_holes(float *values, const uint8_t *holes, int K, int C, i
  *             returns after the work on it has finished
  * Returns IRTPS_EINVAL for H or W < 2, H*W > 262144 or bad tolerances,
  * IRTPS_ENUMERIC if the residual stays above tol, IRTPS_ETIMEOUT if a grid
- * barrier gave up, IRTPS_ECUDA on a CUDA failure.  The first call on a device
- * looks up the array's device address (make it before any stream capture).  All
- * calls share the array: calls that overlap on the GPU race and must not be
- * issued. */
+ * barrier gave up, IRTPS_ECUDA on a CUDA failure (after waiting for the work it
+ * had queued).  The first call on a device looks up the array's device address
+ * and keeps it for the life of the process (make that first call before any
+ * stream capture; a cudaDeviceReset invalidates the kept address, so the entry
+ * point is not for use across device resets).  All calls share the array: calls
+ * that overlap on the GPU race and must not be issued. */
 int irtps_integrate_noalloc(const float *normals, int H, int W, float nz_min, double tol, int max_iter, float *depth,
                             void *stream);
 
@@ -256,9 +268,18 @@ int irtps_set_object(irtps_ctx *ctx, uint32_t object);
  *                   (0 = full depth; clamped so that two levels remain) */
 int irtps_set_tuning(irtps_ctx *ctx, int blocks_per_sm, int mip_cut);
 int irtps_get_tuning(irtps_ctx *ctx, int *blocks_per_sm, int *mip_cut);
+/* Pixels per thread of the FP32 subtract + PS kernel (Eq. 4; ps_tensor = 0):
+ * 1, 2 or 4 consecutive pixels, one vector load per plane row for all of them
+ * (0 = the default, 2).  A grid whose pixel count is not a multiple of the width
+ * runs one pixel per thread.  No result bit depends on it. */
+int irtps_set_ps_tuning(irtps_ctx *ctx, int pixels_per_thread);
+int irtps_get_ps_tuning(irtps_ctx *ctx, int *pixels_per_thread); /* the width in use */
 /* Time the trace of the current state with spp_probe samples for each candidate
- * (blocks_per_sm, mip_cut) and keep the fastest.  Writes the indirect buffer
- * (re-trace before using it).  out_ms (nullable) receives the best time. */
+ * (blocks_per_sm, mip_cut) and keep the fastest; right after irtps_set_images
+ * (iteration 0) it also times the PS widths 1, 2, 4 by re-running classic PS,
+ * which rewrites the normals and albedo the context already holds, bit for bit.
+ * Writes the indirect buffer (re-trace before using it).  out_ms (nullable)
+ * receives the best trace time. */
 int irtps_autotune(irtps_ctx *ctx, int spp_probe, int bounces, uint64_t seed, double *out_ms);
 
 /* ---- Batches: many objects, one launch per IRT stage ----

@@ -32,6 +32,7 @@ struct irtps_batch {
   void *d_ps = nullptr;    // PS descriptors (iterations: Lbar subtracted)
   void *d_ps0 = nullptr;   // PS descriptors of iteration 0 (classic PS: Lbar taken as 0)
   void *d_jobs = nullptr;  // depth-solve jobs
+  irtps::SpectralBatch spectral;  // the direct solves of the objects that take them
   irtps::PyrObj *d_pyr = nullptr;
   irtps::ReduceObj *d_reduce = nullptr;  // light-shared: partial-sum buffers of the objects
   int reduce_blocks = 0;
@@ -80,7 +81,8 @@ int bcuda(irtps_batch &b, cudaError_t e, const char *what) {
   } while (0)
 
 void release(irtps_batch &b) {
-  void *bufs[] = {b.d_trace, b.d_ps, b.d_ps0, b.d_jobs, b.d_pyr, b.d_reduce, b.d_stats, b.next_item, b.iter_dev};
+  void *bufs[] = {b.d_trace,  b.d_ps,    b.d_ps0,     b.d_jobs,  b.d_pyr, b.d_reduce,
+                  b.d_stats, b.next_item, b.iter_dev, b.spectral.table};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (b.graph) cudaGraphExecDestroy(b.graph);
@@ -122,6 +124,9 @@ int trace_grid(const irtps_batch &b) { return b.trace_per_sm * b.sms; }
 int irls_kernels(const irtps_batch &b) {
   return b.irls_iters > 0 ? b.irls_iters * (1 + (b.mg_levels - 1) + 7) + 1 : 0;
 }
+
+// Kernels of the least-squares solve: seven, plus the six transform passes when some object solves directly.
+int solve_kernels(const irtps_batch &b) { return 7 + (b.spectral.n > 0 ? 6 : 0); }
 
 // Trace descriptors for this call: objects of larger per-item cost first, so
 // that the cheap items of the last claims fill the tail of the launch.
@@ -225,7 +230,7 @@ int enqueue_iteration(irtps_batch &b, uint32_t iter, bool captured) {
   BCK(irtps::launch_ps_batch(b.stream, b.C, b.objs[0]->c.images_dtype, b.d_ps, b.n, b.ps_blocks), "ps launch");
   BSTAGE(ST_PS, false);
   BSTAGE(ST_DEPTH, true);
-  BCK(irtps::solve_depth_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks, b.irls_iters, b.mg_levels), "depth solve launch");
+  BCK(irtps::solve_depth_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks, b.irls_iters, b.mg_levels, b.spectral), "depth solve launch");
   BSTAGE(ST_DEPTH, false);
   BCK(irtps::depth_change_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks), "depth change launch");
   if (captured) BCK(irtps::launch_next_iter(b.stream, b.iter_dev), "iteration counter");
@@ -406,7 +411,7 @@ int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&b.sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                cudaSuccess)
     return bail(IRTPS_ECUDA);
-  const int limit = irtps::trace_grid_limit(b.C, n_obj);
+  const int limit = irtps::trace_grid_limit(b.C, n_obj, b.shared);
   b.trace_per_sm_max = b.sms > 0 ? limit / b.sms : 0;
   if (b.trace_per_sm_max < 1) return bail(IRTPS_ECUDA);
   b.trace_per_sm = b.trace_per_sm_max;
@@ -472,6 +477,14 @@ int irtps_batch_create(irtps_batch **out, irtps_ctx *const *objs, int n_obj, int
     irtps::cg_fill_job(objs[i]->c, nblk[i], b.cg_blocks, b.d_stats + i, jobs.data() + job_bytes * i);
     b.cg_blocks += nblk[i];
   }
+  {
+    std::vector<Ctx *> cs;
+    for (int i = 0; i < n_obj; ++i) cs.push_back(&objs[i]->c);
+    if (irtps::spectral_batch_setup(cs, b.spectral) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(IRTPS_ENOMEM);
+    }
+  }
   if (cudaMemcpy(b.d_pyr, pyr.data(), sizeof(irtps::PyrObj) * n_obj, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b.d_ps, ps.data(), ps_bytes * n_obj, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b.d_ps0, ps0.data(), ps_bytes * n_obj, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -508,12 +521,12 @@ int irtps_batch_set_images(irtps_batch *x, const void *const *images, int dtype,
   BSTAGE(ST_PS, false);
   BSTAGE(ST_DEPTH, true);
   BCK(irtps::zero_depth_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks), "depth reset");
-  BCK(irtps::solve_depth_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks, b.irls_iters, b.mg_levels), "depth solve launch");
+  BCK(irtps::solve_depth_batch_async(b.stream, b.d_jobs, b.n, b.cg_blocks, b.irls_iters, b.mg_levels, b.spectral), "depth solve launch");
   BSTAGE(ST_DEPTH, false);
   b.primary_per_iter = 0;
   rc = end_call(b, true, 0, nullptr);
   b.stats.iterations_done = 0;
-  b.stats.launches += 1 + 1 + 7 + irls_kernels(b);
+  b.stats.launches += 1 + 1 + solve_kernels(b) + irls_kernels(b);
   const int rj = join_out(b);
   return rc ? rc : rj;
 }
@@ -537,8 +550,8 @@ int irtps_batch_iterate(irtps_batch *x, int n_iter, const int *spp, const int *b
       if ((rc = enqueue_iteration(b, (uint32_t)it, false))) return rc;
   }
   rc = end_call(b, true, n_iter, out_dH);
-  {  // kernels per iteration: pyramid levels, trace, PS, seven of the solve, two of D_H (+ counter)
-    int k = 1 + 1 + 7 + 2 + (b.use_graph ? 1 : 0) + (b.shared ? 2 : 0) + (b.hz_blocks > 0 ? 1 : 0) +
+  {  // kernels per iteration: pyramid levels, trace, PS, the solve's, two of D_H (+ counter)
+    int k = 1 + 1 + solve_kernels(b) + 2 + (b.use_graph ? 1 : 0) + (b.shared ? 2 : 0) + (b.hz_blocks > 0 ? 1 : 0) +
             irls_kernels(b);
     for (int l = 0; l < b.pyr_levels; ++l) k += b.pyr_blocks[l] > 0 ? 1 : 0;
     b.stats.launches += (unsigned long long)k * n_iter;

@@ -46,7 +46,8 @@ void release(Ctx &c) {
   void *bufs[] = {c.env, c.d_lights, c.horizon, c.shared_part, c.images, c.lbar, c.depth, c.depth_prev, c.nrm, c.albedo, c.valid, c.pmin, c.pmax,
                   c.cg_x, c.cg_b, c.cg_r, c.cg_z, c.cg_p, c.cg_ap, c.part, c.dstats, c.next_item, c.cg_ctl,
                   c.mg_x0, c.mg_x1, c.mg_b, c.mg_wh, c.mg_wv, c.mg_wh_unit, c.mg_wv_unit, c.iter_dev, c.holes,
-                  c.fill_v, c.fill_w, c.sp_ch, c.sp_cw, c.sp_mu, c.sp_nu, c.sp_t};
+                  c.fill_v, c.fill_w, c.sp_ch, c.sp_cw, c.sp_mu, c.sp_nu, c.sp_t, c.ps_pix, c.ps_mask,
+                  c.ps_rhs, c.ps_count};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (c.h_part) cudaFreeHost(c.h_part);
@@ -133,6 +134,7 @@ int end_call(Ctx &c, bool had_solve) {
     c.stats.cg_rel_residual = h.cg.rel_last;
   }
   if (h.counts[2]) return fail(c, IRTPS_ETIMEOUT, "trace: a heightfield march exhausted its step budget");
+  if (h.counts[6]) return fail(c, IRTPS_ETIMEOUT, "ps: a tensor-core product did not complete in time");
   if (had_solve && h.cg.err) return fail(c, IRTPS_ETIMEOUT, "depth solve: a grid barrier timed out");
   if (had_solve && h.cg.bad)
     return fail(c, IRTPS_ENUMERIC, "depth solve: relative residual " + std::to_string(h.cg.rel_last) +
@@ -279,6 +281,7 @@ void irtps_default_options(irtps_options *opt) {
   opt->irls_delta = 0.05f;
   opt->early_escape = 2;
   opt->fill_holes = 0;
+  opt->ps_tensor = 0;
 }
 
 int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *lights, const float *env, int EH,
@@ -320,6 +323,8 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
     return bail(fail(c, IRTPS_EINVAL, "create: fill_holes must be 0 or 1"));
   if (c.opt.fill_holes && c.opt.sampling != 0)
     return bail(fail(c, IRTPS_EINVAL, "create: fill_holes needs per-light sampling (sampling = 0)"));
+  if (c.opt.ps_tensor != 0 && c.opt.ps_tensor != 1)
+    return bail(fail(c, IRTPS_EINVAL, "create: ps_tensor must be 0 or 1"));
   c.eps = (float)1e-3 / (float)W;  // same expression as the oracle's lift
   // lights and pinv(L) = (L^T L)^-1 L^T in FP64 (Eq. 4)
   c.h_lights.assign(lights, lights + 3 * K);
@@ -373,7 +378,7 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "create: events"));
   }
   c.cg_blocks = (int)std::min<size_t>((P + 255) / 256, (size_t)irtps::cg_grid_limit());
-  c.trace_blocks = irtps::trace_grid_limit(C);
+  c.trace_blocks = irtps::trace_grid_limit(C, 0, c.opt.sampling == 1);
   {
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
@@ -388,6 +393,9 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
       (rc = dalloc(c, &c.lbar, (size_t)K * C * P, "indirect")) || (rc = dalloc(c, &c.depth, P, "depth")) ||
       (rc = dalloc(c, &c.depth_prev, P, "depth")) || (rc = dalloc(c, &c.nrm, P, "normals")) ||
       (rc = dalloc(c, &c.albedo, (size_t)C * P, "albedo")) || (rc = dalloc(c, &c.valid, P, "valid")) ||
+      (rc = dalloc(c, &c.ps_pix, P, "masked-pixel list")) || (rc = dalloc(c, &c.ps_mask, P, "masked-pixel list")) ||
+      (rc = dalloc(c, &c.ps_rhs, (size_t)9 * P, "masked-pixel list")) ||
+      (rc = dalloc(c, &c.ps_count, 1, "masked-pixel list")) ||
       (rc = dalloc(c, &c.pmin, (size_t)total, "pyramid")) || (rc = dalloc(c, &c.pmax, (size_t)total, "pyramid")) ||
       (rc = dalloc(c, &c.cg_x, P, "cg")) || (rc = dalloc(c, &c.cg_b, P, "cg")) ||
       (rc = dalloc(c, &c.cg_r, P, "cg")) || (rc = dalloc(c, &c.cg_z, P, "cg")) ||
@@ -805,6 +813,25 @@ int irtps_get_tuning(irtps_ctx *ctx, int *blocks_per_sm, int *mip_cut) {
   return IRTPS_OK;
 }
 
+int irtps_set_ps_tuning(irtps_ctx *ctx, int pixels_per_thread) {
+  if (!ctx) return IRTPS_EINVAL;
+  Ctx &c = ctx->c;
+  if (pixels_per_thread != 0 && pixels_per_thread != 1 && pixels_per_thread != 2 && pixels_per_thread != 4)
+    return fail(c, IRTPS_EINVAL, "ps tuning: pixels_per_thread must be 0, 1, 2 or 4");
+  c.ps_vec = pixels_per_thread == 0 ? 2 : pixels_per_thread;
+  if (c.graph) {
+    cudaGraphExecDestroy(c.graph);
+    c.graph = nullptr;
+  }
+  return IRTPS_OK;
+}
+
+int irtps_get_ps_tuning(irtps_ctx *ctx, int *pixels_per_thread) {
+  if (!ctx) return IRTPS_EINVAL;
+  if (pixels_per_thread) *pixels_per_thread = irtps::ps_vec_for(ctx->c);
+  return IRTPS_OK;
+}
+
 int irtps_autotune(irtps_ctx *ctx, int spp_probe, int bounces, uint64_t seed, double *out_ms) {
   if (!ctx) return IRTPS_EINVAL;
   Ctx &c = ctx->c;
@@ -840,6 +867,29 @@ int irtps_autotune(irtps_ctx *ctx, int spp_probe, int bounces, uint64_t seed, do
     }
   c.trace_blocks = best_ps * c.sms;
   c.mip_cut = best_cut;
+  // PS pixels per thread: timed at iteration 0 only, where the probe (classic PS from the
+  // images) writes the state the context already holds, bit for bit
+  if (!rc && c.have_images && c.t == 0 && !c.opt.ps_tensor) {
+    float best_v_ms = INFINITY;
+    int best_v = c.ps_vec;
+    for (int v : {1, 2, 4}) {
+      if ((c.H * c.W) % v) continue;
+      c.ps_vec = v;
+      for (int rep = 0; rep < 2 && !rc; ++rep) {
+        c.tev_used = 0;
+        rc = run_ps(c, true);
+      }
+      if (rc) break;
+      float ms = 0.0f;
+      CK(cudaEventSynchronize(c.tev[1]), "autotune");
+      CK(cudaEventElapsedTime(&ms, c.tev[0], c.tev[1]), "autotune");
+      if (ms < best_v_ms) {
+        best_v_ms = ms;
+        best_v = v;
+      }
+    }
+    c.ps_vec = best_v;
+  }
   c.tev_used = 0;
   if (c.graph) {
     cudaGraphExecDestroy(c.graph);

@@ -35,11 +35,12 @@ struct CGAcc {
 
 // Device-side results of one call, read by the host once at its end.
 struct DevStats {
-  unsigned long long counts[8];  // {unused, segments, walk overflows, node visits, triangle tests, draws}
+  unsigned long long counts[8];  // {unused, segments, walk overflows, node visits, triangle tests, draws,
+                                 //  tensor-core PS waits that ran out}
   CGAcc cg;
   double dh_max, dh_rms;         // D_H of the last iteration
 };
-constexpr int kCounters = 6;  // used slots of DevStats::counts
+constexpr int kCounters = 7;  // used slots of DevStats::counts
 
 // Per-object trace descriptor: the current surface and state estimates, the
 // environment, the lights and the output of one object.
@@ -115,10 +116,15 @@ struct Ctx {
   float4 *nrm = nullptr;          // H*W
   float *albedo = nullptr;        // C*H*W
   uint8_t *valid = nullptr;       // H*W, 1 = normal solved
+  int *ps_pix = nullptr;          // PS: pixels with masked rows (H*W capacity), their row masks and
+  unsigned long long *ps_mask = nullptr;  // right-hand sides (9 floats each), count
+  float *ps_rhs = nullptr;
+  unsigned *ps_count = nullptr;
   float *pmin = nullptr, *pmax = nullptr;  // pyramid, all levels
   int levels = 0;
   int trace_blocks = 0;           // resident blocks of the persistent trace grid (0: one lane per item)
   int mip_cut = 0;                // top pyramid levels the march leaves out (tuning; results do not change)
+  int ps_vec = 2;                 // pixels per thread of the PS kernel, 1, 2 or 4 (tuning; results do not change)
   int sms = 0, trace_per_sm_max = 0;  // SM count; resident trace blocks per SM at full occupancy
   int off[kMaxLevels] = {0}, lw[kMaxLevels] = {0}, lh[kMaxLevels] = {0};
   // depth solve
@@ -221,12 +227,45 @@ constexpr int kSpectralMaxSide = 1024;
 bool spectral_fits(int H, int W);
 cudaError_t spectral_setup(Ctx &c);                                 // matrices and work array
 cudaError_t launch_spectral(Ctx &c, const double *b, double *x);   // x = A^+ b, unit weights
+// whether a context's unit-weight solves are direct (option precond = 2 on a grid the transform covers)
+inline bool direct_solve(const Ctx &c) { return c.opt.precond == 2 && c.sp_t != nullptr; }
+// pass descriptors of the direct solve (one 16 x 16 output tile per block)
+struct DctFwd {
+  int M, N, K, L;
+  const double *A;
+  int lda;
+  const double *B;
+  int ldb;
+  double *D;
+  int ldd, dro, dco;
+  const double *mu, *nu;
+  int tiles_n, blk_begin;  // tiles along N; first block of the object in a batched launch
+};
+struct DctInv {
+  int M, N, K1, K2, M2, N2, L;
+  const double *A1, *A2;
+  int lda1, lda2;
+  const double *B1, *B2;
+  int ldb1, ldb2;
+  double *D;
+  int ldd;
+  int tiles_n, blk_begin;
+};
+// the direct solves of a batch's objects: six pass tables (four forward, two inverse) in one device block
+struct SpectralBatch {
+  int n = 0;          // objects with direct solves
+  int blocks[6] = {0};
+  void *table = nullptr;  // owned
+};
+cudaError_t spectral_batch_setup(const std::vector<Ctx *> &objs, SpectralBatch &sb);
+cudaError_t launch_spectral_batch(cudaStream_t s, const SpectralBatch &sb);
 cudaError_t launch_interpolate_holes(cudaStream_t s, float *values, const uint8_t *holes, int K, int C,
                                      const FillPyramid &py, float *v_scr, float *w_scr, int sms, int &launches);
 cudaError_t launch_next_iter(Ctx &c);  // iter_dev += 1 (end of a captured iteration)
 cudaError_t launch_next_iter(cudaStream_t s, uint32_t *iter_dev);
 cudaError_t launch_render(Ctx &c, uint64_t seed, float sigma, const float *lbar, float *out);
-int trace_grid_limit(int C, int n_obj = 0);  // resident blocks of the (batched) trace kernel, 0 if unknown
+// resident blocks of the (batched) trace kernel, per-light or light-shared, 0 if unknown
+int trace_grid_limit(int C, int n_obj = 0, bool shared = false);
 void fill_obj_trace(const Ctx &c, ObjTrace &o);  // descriptor of a context's object (no sampling fields)
 size_t shared_scratch_floats(const Ctx &c, int n_pix, int spp);  // light-shared chunk partials needed
 cudaError_t launch_trace_batch(cudaStream_t s, int C, bool shared, const ObjTrace *d_objs, int n_obj,
@@ -250,6 +289,8 @@ cudaError_t launch_probe_dirs(cudaStream_t s, int n, const float *normals, const
                               float *out);
 cudaError_t launch_probe_rays(Ctx &c, int n, const float *rays, float *t_out, int32_t *tri_out, int *overflow);
 // ps.cu
+// pixels per thread the PS kernel takes: the tuned width when the pixel count is a multiple of it, else 1
+inline int ps_vec_for(const Ctx &c) { return (c.H * c.W) % c.ps_vec == 0 ? c.ps_vec : 1; }
 cudaError_t launch_ps(Ctx &c, bool zero_indirect);
 size_t ps_args_bytes();
 void ps_fill_args(const Ctx &c, bool zero_indirect, int blk_begin, void *dst);
@@ -264,7 +305,7 @@ size_t cg_job_bytes();
 void cg_fill_job(Ctx &c, int nblk, int blk_begin, DevStats *ds, void *dst);
 int cg_batch_grid_limit();
 cudaError_t solve_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks, int irls_iters,
-                                    int max_levels);
+                                    int max_levels, const SpectralBatch &sb);
 cudaError_t depth_change_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks);
 cudaError_t zero_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks);
 void mg_layout(int H, int W, int *levels, int *h, int *w, int *off, int *total);

@@ -1002,6 +1002,7 @@ struct CGJob {
   const float *old;  // previous surface (D_H)
   double tol;
   int max_iter, check, pre;
+  int direct;      // unit-weight solves by the cosine transform (their passes run before the loop)
   int blk_begin;
   // robust integration (IRLS): the object's writable level-0.. weights, their unit copy, threshold
   float *wh, *wv;
@@ -1034,8 +1035,12 @@ template <bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads) k_rhs_b(const CGJob *jobs, int n) {
   for_team(jobs, n, [](const CGJob &j, Team t) { rhs_body<WEIGHTED>(j.g, t); });
 }
+// the warm start of the iterative solves (a direct solve has its x already)
+template <bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads) k_load_x_b(const CGJob *jobs, int n) {
-  for_team(jobs, n, [](const CGJob &j, Team t) { load_x_body(j.g, t); });
+  for_team(jobs, n, [](const CGJob &j, Team t) {
+    if (WEIGHTED || !j.direct) load_x_body(j.g, t);
+  });
 }
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads) k_residual_b(const CGJob *jobs, int n) {
@@ -1046,6 +1051,17 @@ __global__ void k_cg_start_b(const CGJob *jobs) { cg_start_body(jobs[blockIdx.x]
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads, IRTPS_CG_BATCH_MINB) k_cg_loop_b(const CGJob *jobs, int n) {
   for_team<WEIGHTED>(jobs, n, [](const CGJob &j, Team t) {
+    if (!WEIGHTED && j.direct) {  // solved directly: one iteration, its FP64 residual checked
+      if (t.bid == 0 && threadIdx.x == 0) {
+        const double rel = j.ctl->rel;
+        CGAcc *acc = &j.ds->cg;
+        acc->iters += 1;
+        acc->last_iters = 1;
+        acc->rel_last = rel;
+        if (!isfinite(j.ctl->bnorm) || !isfinite(rel) || rel > j.tol) acc->bad = 1;
+      }
+      return;
+    }
     if (j.pre == 1)
       cg_loop_body<1, WEIGHTED>(j.g, j.ctl, &j.ds->cg, j.tol, j.max_iter, j.check, j.mg, t);
     else
@@ -1111,7 +1127,8 @@ void cg_fill_job(Ctx &c, int nblk, int blk_begin, DevStats *ds, void *dst) {
   j.tol = c.opt.cg_tol;
   j.max_iter = c.opt.cg_max_iter;
   j.check = c.opt.cg_check_every > 0 ? c.opt.cg_check_every : 10;
-  j.pre = c.opt.precond != 0 ? 1 : 0;  // batched solves: multigrid for precond 1 and 2
+  j.pre = c.opt.precond != 0 ? 1 : 0;  // iterative solves: multigrid for precond 1 and 2
+  j.direct = direct_solve(c) ? 1 : 0;
   j.blk_begin = blk_begin;
   j.wh = c.mg_wh;
   j.wv = c.mg_wv;
@@ -1123,9 +1140,14 @@ void cg_fill_job(Ctx &c, int nblk, int blk_begin, DevStats *ds, void *dst) {
 }
 
 template <bool WEIGHTED>
-static cudaError_t solve_batch_once(cudaStream_t s, const CGJob *jobs, int n, int blocks) {
+static cudaError_t solve_batch_once(cudaStream_t s, const CGJob *jobs, int n, int blocks, const SpectralBatch &sb) {
   k_rhs_b<WEIGHTED><<<blocks, kThreads, 0, s>>>(jobs, n);
-  k_load_x_b<<<blocks, kThreads, 0, s>>>(jobs, n);
+  if (!WEIGHTED) {
+    LAUNCH_CHECK();
+    cudaError_t e = launch_spectral_batch(s, sb);
+    if (e != cudaSuccess) return e;
+  }
+  k_load_x_b<WEIGHTED><<<blocks, kThreads, 0, s>>>(jobs, n);
   k_residual_b<WEIGHTED><<<blocks, kThreads, 0, s>>>(jobs, n);
   k_cg_start_b<<<n, 32, 0, s>>>(jobs);
   LAUNCH_CHECK();
@@ -1143,15 +1165,15 @@ static cudaError_t solve_batch_once(cudaStream_t s, const CGJob *jobs, int n, in
 // followed by that many reweighting steps of the Huber M-estimator, as in the
 // single-object solve, and the unit weights are put back at the end.
 cudaError_t solve_depth_batch_async(cudaStream_t s, const void *d_jobs, int n, int blocks, int irls_iters,
-                                    int max_levels) {
+                                    int max_levels, const SpectralBatch &sb) {
   const CGJob *jobs = (const CGJob *)d_jobs;
-  cudaError_t e = solve_batch_once<false>(s, jobs, n, blocks);
+  cudaError_t e = solve_batch_once<false>(s, jobs, n, blocks, sb);
   if (e != cudaSuccess || irls_iters <= 0) return e;
   for (int it = 0; it < irls_iters; ++it) {
     k_irls_weights_b<<<blocks, kThreads, 0, s>>>(jobs, n);
     for (int l = 0; l + 1 < max_levels; ++l) k_mg_coarsen_b<<<blocks, kThreads, 0, s>>>(jobs, n, l);
     LAUNCH_CHECK();
-    if ((e = solve_batch_once<true>(s, jobs, n, blocks)) != cudaSuccess) return e;
+    if ((e = solve_batch_once<true>(s, jobs, n, blocks, sb)) != cudaSuccess) return e;
   }
   k_unit_weights_b<<<blocks, kThreads, 0, s>>>(jobs, n);
   LAUNCH_CHECK();
@@ -1195,7 +1217,9 @@ constexpr size_t kNaBytes = kNaCtl + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
 // Device address of the scratch array on the current device: looked up once per
-// device (the first call on a device does it) and cached.
+// device (the first call on a device does it) and cached for the life of the
+// process; a cudaDeviceReset unloads the module, after which the cached address
+// is no longer valid (the entry point is not for use across device resets).
 static unsigned char *noalloc_base() {
   static std::mutex mu;
   static unsigned char *base[64] = {nullptr};
@@ -1244,23 +1268,29 @@ extern "C" int irtps_integrate_noalloc(const float *normals, int H, int W, float
   g.wh = g.wv = nullptr;
   CGCtl *ctl = reinterpret_cast<CGCtl *>(base + kNaCtl);
 
+  // a failure after the first launch waits for the queued kernels, so that none of
+  // them still works on the shared array when the call returns
+  auto failed = [s]() {
+    cudaStreamSynchronize(s);
+    return IRTPS_ECUDA;
+  };
   k_rhs<false><<<nb, kThreads, 0, s>>>(g);
   k_load_x<<<nb, kThreads, 0, s>>>(g);
   k_residual<false><<<nb, kThreads, 0, s>>>(g, S_RZ0);
   k_cg_start<<<1, 32, 0, s>>>(g, ctl);  // also clears the barrier state left by the previous call
-  if (cudaGetLastError() != cudaSuccess) return IRTPS_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return failed();
   int m = 10;
   const MG none{};
   CGAcc *acc = nullptr;
   void *args[] = {(void *)&g, (void *)&ctl, (void *)&acc, (void *)&tol, (void *)&max_iter, (void *)&m, (void *)&none};
   if (cudaLaunchCooperativeKernel((const void *)k_cg_loop<0, false>, dim3(nb), dim3(kThreads), args, 0, s) !=
       cudaSuccess)
-    return IRTPS_ECUDA;
+    return failed();
   k_sum_x<<<nb, kThreads, 0, s>>>(g);
   k_store_depth<<<nb, kThreads, 0, s>>>(g, ctl);
-  if (cudaGetLastError() != cudaSuccess) return IRTPS_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return failed();
   CGCtl h;
-  if (cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return IRTPS_ECUDA;
+  if (cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return failed();
   if (cudaStreamSynchronize(s) != cudaSuccess) return IRTPS_ECUDA;
   if (h.err) return IRTPS_ETIMEOUT;
   if (!std::isfinite(h.bnorm)) return IRTPS_ENUMERIC;

@@ -13,6 +13,7 @@
 // with coalesced [k][c][p] loads and the pixel's state written once.
 #include <cstdint>
 #include <cstring>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "irtps_internal.h"
@@ -41,95 +42,36 @@ __device__ __forceinline__ float load_img<float>(const float *p) { return __ldg(
 template <>
 __device__ __forceinline__ float load_img<__half>(const __half *p) { return __half2float(__ldg(p)); }
 
-template <int C, typename TI>
-__device__ __forceinline__ void ps_pixel(const PSArgs &a, int p) {
-  const TI *img = reinterpret_cast<const TI *>(a.images);
-  const size_t P = (size_t)a.P;
-  float rho[C];
+// Row k of pixel p: I(k, c) = A0 - rho_c Lbar (each operation rounded on its own)
+// and its validity (tau_lo < mean_c I < tau_hi), accumulated into G = pinv(L) I
+// over all rows and into R = L_v^T I over the valid rows (the right-hand side of
+// the masked normal equations), both in FP32.
+template <int C>
+__device__ __forceinline__ void ps_row(const PSArgs &a, int k, const float *rho, const float *a0, const float *lb,
+                                       float (&G)[3][C], float (&R)[3][C], unsigned long long &valid) {
+  float I[C];
 #pragma unroll
-  for (int c = 0; c < C; ++c) rho[c] = a.zero_indirect ? 0.0f : a.albedo[c * P + p];
-  float G[3][C];
+  for (int c = 0; c < C; ++c) I[c] = __fsub_rn(a0[c], __fmul_rn(rho[c], lb[c]));
+  float chat = I[0];
+  if (C == 3) chat = __fdiv_rn(__fadd_rn(__fadd_rn(I[0], I[1]), I[2]), 3.0f);
+  const bool ok = chat > a.tau_lo && chat < a.tau_hi;
+  if (ok) valid |= 1ull << k;
 #pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int c = 0; c < C; ++c) G[r][c] = 0.0f;
-  unsigned long long valid = 0;
-  for (int k = 0; k < a.K; ++k) {
-    float I[C];
+  for (int r = 0; r < 3; ++r) {
+    const float l = ok ? a.light[k][r] : 0.0f;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const size_t o = ((size_t)k * C + c) * P + p;
-      const float a0 = load_img<TI>(img + o);
-      const float lb = a.zero_indirect ? 0.0f : __ldg(a.lbar + o);
-      I[c] = __fsub_rn(a0, __fmul_rn(rho[c], lb));
-    }
-    float chat = I[0];
-    if (C == 3) chat = __fdiv_rn(__fadd_rn(__fadd_rn(I[0], I[1]), I[2]), 3.0f);
-    if (chat > a.tau_lo && chat < a.tau_hi) valid |= 1ull << k;
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < C; ++c) G[r][c] = fmaf(a.pinv[r][k], I[c], G[r][c]);
-  }
-  const unsigned long long all = a.K == 64 ? ~0ull : ((1ull << a.K) - 1ull);
-  bool ok = true;
-  if (valid != all) {
-    // masked pixel: FP64 normal equations over the valid rows
-    if (__popcll(valid) < 3) {
-      ok = false;
-    } else {
-      double M00 = 0, M01 = 0, M02 = 0, M11 = 0, M12 = 0, M22 = 0;
-      double R[3][C];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < C; ++c) R[r][c] = 0.0;
-      for (int k = 0; k < a.K; ++k) {
-        if (!((valid >> k) & 1ull)) continue;
-        const double lx = a.light[k][0], ly = a.light[k][1], lz = a.light[k][2];
-        M00 += lx * lx;
-        M01 += lx * ly;
-        M02 += lx * lz;
-        M11 += ly * ly;
-        M12 += ly * lz;
-        M22 += lz * lz;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const size_t o = ((size_t)k * C + c) * P + p;
-          const double lb = a.zero_indirect ? 0.0 : (double)__ldg(a.lbar + o);
-          const double Iv = (double)load_img<TI>(img + o) - (double)rho[c] * lb;
-          R[0][c] += lx * Iv;
-          R[1][c] += ly * Iv;
-          R[2][c] += lz * Iv;
-        }
-      }
-      // inverse by the adjugate; 1-norm condition number
-      const double A00 = M11 * M22 - M12 * M12, A01 = M02 * M12 - M01 * M22, A02 = M01 * M12 - M02 * M11;
-      const double A11 = M00 * M22 - M02 * M02, A12 = M01 * M02 - M00 * M12, A22 = M00 * M11 - M01 * M01;
-      const double det = M00 * A00 + M01 * A01 + M02 * A02;
-      if (!(det != 0.0) || !isfinite(det)) {
-        ok = false;
-      } else {
-        const double id = 1.0 / det;
-        const double i00 = A00 * id, i01 = A01 * id, i02 = A02 * id, i11 = A11 * id, i12 = A12 * id, i22 = A22 * id;
-        const double nM = fmax(fabs(M00) + fabs(M01) + fabs(M02),
-                               fmax(fabs(M01) + fabs(M11) + fabs(M12), fabs(M02) + fabs(M12) + fabs(M22)));
-        const double nI = fmax(fabs(i00) + fabs(i01) + fabs(i02),
-                               fmax(fabs(i01) + fabs(i11) + fabs(i12), fabs(i02) + fabs(i12) + fabs(i22)));
-        const double cond = nM * nI;
-        if (!(cond <= a.cond_max)) {
-          ok = false;
-        } else {
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            G[0][c] = (float)(i00 * R[0][c] + i01 * R[1][c] + i02 * R[2][c]);
-            G[1][c] = (float)(i01 * R[0][c] + i11 * R[1][c] + i12 * R[2][c]);
-            G[2][c] = (float)(i02 * R[0][c] + i12 * R[1][c] + i22 * R[2][c]);
-          }
-        }
-      }
+      G[r][c] = fmaf(a.pinv[r][k], I[c], G[r][c]);
+      R[r][c] = fmaf(l, I[c], R[r][c]);
     }
   }
+}
+
+// Normal and albedo of pixel p from G (Eq. 4 and the text after it): n = normalize(sum_c G_c),
+// rho_c = |G_c|; a pixel whose solve failed (ok false) or whose sum vanishes is invalid.
+template <int C>
+__device__ __forceinline__ void ps_store(const PSArgs &a, int p, const float (&G)[3][C], bool ok) {
+  const size_t P = (size_t)a.P;
   float sx = 0.0f, sy = 0.0f, sz = 0.0f;
 #pragma unroll
   for (int c = 0; c < C; ++c) {
@@ -157,10 +99,274 @@ __device__ __forceinline__ void ps_pixel(const PSArgs &a, int p) {
   a.valid[p] = ok ? 1 : 0;
 }
 
+// A pixel with masked rows: the normal equations (L_v^T L_v) G_c = L_v^T I_v,c over the
+// valid rows.  The matrix, its inverse (by the adjugate) and its 1-norm condition number
+// are computed in FP64 from the lights; fewer than 3 rows, a singular or ill-conditioned
+// system (condition above cond_max): ok = false.  The right-hand side R is the FP32 sum
+// of ps_row, except for systems whose condition number exceeds kRefineCond, where the
+// FP32 rounding of R would be amplified: their R is summed again in FP64 from the
+// pixel's valid rows (read again).
+constexpr double kRefineCond = 16.0;
+
 template <int C, typename TI>
-__global__ void __launch_bounds__(256) k_ps(const PSArgs a) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < a.P) ps_pixel<C, TI>(a, p);
+__device__ __forceinline__ bool ps_masked_solve(const PSArgs &a, int p, const float (&R)[3][C], float (&G)[3][C],
+                                                unsigned long long valid) {
+  if (__popcll(valid) < 3) return false;
+  double M00 = 0, M01 = 0, M02 = 0, M11 = 0, M12 = 0, M22 = 0;
+  for (int k = 0; k < a.K; ++k) {
+    if (!((valid >> k) & 1ull)) continue;
+    const double lx = a.light[k][0], ly = a.light[k][1], lz = a.light[k][2];
+    M00 += lx * lx;
+    M01 += lx * ly;
+    M02 += lx * lz;
+    M11 += ly * ly;
+    M12 += ly * lz;
+    M22 += lz * lz;
+  }
+  // inverse by the adjugate; 1-norm condition number
+  const double A00 = M11 * M22 - M12 * M12, A01 = M02 * M12 - M01 * M22, A02 = M01 * M12 - M02 * M11;
+  const double A11 = M00 * M22 - M02 * M02, A12 = M01 * M02 - M00 * M12, A22 = M00 * M11 - M01 * M01;
+  const double det = M00 * A00 + M01 * A01 + M02 * A02;
+  if (!(det != 0.0) || !isfinite(det)) return false;
+  const double id = 1.0 / det;
+  const double i00 = A00 * id, i01 = A01 * id, i02 = A02 * id, i11 = A11 * id, i12 = A12 * id, i22 = A22 * id;
+  const double nM = fmax(fabs(M00) + fabs(M01) + fabs(M02),
+                         fmax(fabs(M01) + fabs(M11) + fabs(M12), fabs(M02) + fabs(M12) + fabs(M22)));
+  const double nI = fmax(fabs(i00) + fabs(i01) + fabs(i02),
+                         fmax(fabs(i01) + fabs(i11) + fabs(i12), fabs(i02) + fabs(i12) + fabs(i22)));
+  const double cond = nM * nI;
+  if (!(cond <= a.cond_max)) return false;
+  double Rd[3][C];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < C; ++c) Rd[r][c] = R[r][c];
+  if (cond > kRefineCond) {  // ill-conditioned: the right-hand side in FP64
+    const TI *img = reinterpret_cast<const TI *>(a.images);
+    const size_t P = (size_t)a.P;
+    float rho[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) rho[c] = a.zero_indirect ? 0.0f : a.albedo[c * P + p];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < C; ++c) Rd[r][c] = 0.0;
+    for (int k = 0; k < a.K; ++k) {
+      if (!((valid >> k) & 1ull)) continue;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const size_t o = ((size_t)k * C + c) * P + p;
+        const double lb = a.zero_indirect ? 0.0 : (double)__ldg(a.lbar + o);
+        const double Iv = (double)load_img<TI>(img + o) - (double)rho[c] * lb;
+        Rd[0][c] += (double)a.light[k][0] * Iv;
+        Rd[1][c] += (double)a.light[k][1] * Iv;
+        Rd[2][c] += (double)a.light[k][2] * Iv;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    G[0][c] = (float)(i00 * Rd[0][c] + i01 * Rd[1][c] + i02 * Rd[2][c]);
+    G[1][c] = (float)(i01 * Rd[0][c] + i11 * Rd[1][c] + i12 * Rd[2][c]);
+    G[2][c] = (float)(i02 * Rd[0][c] + i12 * Rd[1][c] + i22 * Rd[2][c]);
+  }
+  return true;
+}
+
+// The rest of pixel p once every row is in: the FP64 solve when some row is masked, then
+// the stored normal, albedo and validity.
+template <int C, typename TI>
+__device__ __forceinline__ void ps_finish(const PSArgs &a, int p, const float (&R)[3][C], float (&G)[3][C],
+                                          unsigned long long valid) {
+  const unsigned long long all = a.K == 64 ? ~0ull : ((1ull << a.K) - 1ull);
+  bool ok = true;
+  if (valid != all) ok = ps_masked_solve<C, TI>(a, p, R, G, valid);
+  ps_store<C>(a, p, G, ok);
+}
+
+template <int C, typename TI>
+__device__ __forceinline__ void ps_pixel(const PSArgs &a, int p) {
+  const TI *img = reinterpret_cast<const TI *>(a.images);
+  const size_t P = (size_t)a.P;
+  float rho[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) rho[c] = a.zero_indirect ? 0.0f : a.albedo[c * P + p];
+  float G[3][C], R[3][C];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < C; ++c) G[r][c] = R[r][c] = 0.0f;
+  unsigned long long valid = 0;
+  for (int k = 0; k < a.K; ++k) {
+    float a0[C], lb[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const size_t o = ((size_t)k * C + c) * P + p;
+      a0[c] = load_img<TI>(img + o);
+      lb[c] = a.zero_indirect ? 0.0f : __ldg(a.lbar + o);
+    }
+    ps_row<C>(a, k, rho, a0, lb, G, R, valid);
+  }
+  ps_finish<C, TI>(a, p, R, G, valid);
+}
+
+// The single-object form in two kernels, so that the common path stays small (few
+// registers, many resident threads, several pixels' loads in flight per thread):
+//   k_ps_fast: V consecutive pixels per thread (P a multiple of V, so that every
+//     plane row is 4V-byte aligned; one vector load per plane row for all V), the
+//     FP32 contraction and row masks; a pixel with every row valid is stored, a
+//     masked one goes to a list with its row mask;
+//   k_ps_masked: the normal equations of the listed pixels (ps_masked_solve: FP64 3 x 3
+//     system from the lights, FP32 right-hand side from the first pass; no image re-read).
+// Per pixel the arithmetic is that of ps_pixel, so both forms give the same bits.
+
+template <typename TI, int V>
+struct VecLoad;
+template <>
+struct VecLoad<float, 1> {
+  static __device__ __forceinline__ void get(const float *p, float (&v)[1]) { v[0] = __ldg(p); }
+};
+template <>
+struct VecLoad<float, 2> {
+  static __device__ __forceinline__ void get(const float *p, float (&v)[2]) {
+    const float2 x = __ldg(reinterpret_cast<const float2 *>(p));
+    v[0] = x.x;
+    v[1] = x.y;
+  }
+};
+template <>
+struct VecLoad<float, 4> {
+  static __device__ __forceinline__ void get(const float *p, float (&v)[4]) {
+    const float4 x = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+  }
+};
+template <>
+struct VecLoad<__half, 1> {
+  static __device__ __forceinline__ void get(const __half *p, float (&v)[1]) { v[0] = __half2float(__ldg(p)); }
+};
+template <>
+struct VecLoad<__half, 2> {
+  static __device__ __forceinline__ void get(const __half *p, float (&v)[2]) {
+    const float2 x = __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
+    v[0] = x.x;
+    v[1] = x.y;
+  }
+};
+template <>
+struct VecLoad<__half, 4> {
+  static __device__ __forceinline__ void get(const __half *p, float (&v)[4]) {
+    const uint2 x = __ldg(reinterpret_cast<const uint2 *>(p));
+    const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&x.x));
+    const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&x.y));
+    v[0] = lo.x;
+    v[1] = lo.y;
+    v[2] = hi.x;
+    v[3] = hi.y;
+  }
+};
+
+struct PSList {
+  int *pix;                  // masked pixels
+  unsigned long long *mask;  // their row masks
+  float *rhs;                // their right-hand sides R = L_v^T I, 9 floats each (3 x C used)
+  unsigned *count;           // entries (zero before the launch)
+};
+
+template <int C, typename TI, int V>
+__global__ void __launch_bounds__(256) k_ps_fast(const PSArgs a, const PSList L) {
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+  const bool in = p < a.P;
+  const TI *img = reinterpret_cast<const TI *>(a.images);
+  const size_t P = (size_t)a.P;
+  float rho[V][C];
+  float G[V][3][C], R[V][3][C];
+  unsigned long long valid[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    valid[j] = 0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < C; ++c) G[j][r][c] = R[j][r][c] = 0.0f;
+  }
+  if (in) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      float v[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) v[j] = 0.0f;
+      if (!a.zero_indirect) VecLoad<float, V>::get(a.albedo + c * P + p, v);
+#pragma unroll
+      for (int j = 0; j < V; ++j) rho[j][c] = v[j];
+    }
+#pragma unroll(4 / V)
+    for (int k = 0; k < a.K; ++k) {
+      float a0[C][V], lb[C][V];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const size_t o = ((size_t)k * C + c) * P + p;
+        VecLoad<TI, V>::get(img + o, a0[c]);
+        if (a.zero_indirect) {
+#pragma unroll
+          for (int j = 0; j < V; ++j) lb[c][j] = 0.0f;
+        } else {
+          VecLoad<float, V>::get(a.lbar + o, lb[c]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        float x0[C], x1[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          x0[c] = a0[c][j];
+          x1[c] = lb[c][j];
+        }
+        ps_row<C>(a, k, rho[j], x0, x1, G[j], R[j], valid[j]);
+      }
+    }
+  }
+  const unsigned long long all = a.K == 64 ? ~0ull : ((1ull << a.K) - 1ull);
+#pragma unroll
+  for (int j = 0; j < V; ++j) {
+    const bool masked = in && valid[j] != all;
+    if (in && !masked) ps_store<C>(a, p + j, G[j], true);
+    // masked pixels of the warp appended with one atomic
+    const unsigned mm = __ballot_sync(0xffffffffu, masked);
+    if (mm) {
+      const int lane = threadIdx.x & 31, leader = __ffs(mm) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(L.count, (unsigned)__popc(mm));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (masked) {
+        const unsigned i = base + __popc(mm & ((1u << lane) - 1u));
+        L.pix[i] = p + j;
+        L.mask[i] = valid[j];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < C; ++c) L.rhs[(size_t)i * 9 + r * C + c] = R[j][r][c];
+      }
+    }
+  }
+}
+
+template <int C, typename TI>
+__global__ void __launch_bounds__(128) k_ps_masked(const PSArgs a, const PSList L) {
+  const unsigned n = *L.count;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int p = L.pix[i];
+    float R[3][C], G[3][C] = {};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < C; ++c) R[r][c] = L.rhs[(size_t)i * 9 + r * C + c];
+    const bool ok = ps_masked_solve<C, TI>(a, p, R, G, L.mask[i]);
+    ps_store<C>(a, p, G, ok);
+  }
 }
 
 // Batched: the blocks of object o are [objs[o].blk_begin, objs[o + 1].blk_begin).
@@ -179,6 +385,233 @@ __global__ void __launch_bounds__(256) k_ps_b(const PSArgs *__restrict__ objs, i
   const PSArgs &a = objs[s_o];
   const int p = ((int)blockIdx.x - a.blk_begin) * blockDim.x + threadIdx.x;
   if (p < a.P) ps_pixel<C, TI>(a, p);
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core form of the contraction (option ps_tensor = 1).  A tile of 128
+// pixels is one [128 x KCp] x [KCp x 16] product on tcgen05: row p holds the
+// corrected values I(p, kk), kk = k C + c (the image layout's own plane index),
+// and column n = r C + c of the right operand holds pinv(L)[r][k] where the
+// channels agree (zero elsewhere), so that the accumulator row p is
+// G(p)[r][c] = sum_k pinv[r][k] I(p, k, c) (Eq. 4).  Split precision: I and
+// pinv are each a BF16 pair hi + lo (hi = bf16(x), lo = bf16(x - hi)); the chain
+// I_hi P_hi + I_lo P_hi + I_hi P_lo accumulates in FP32 in tensor memory (the
+// dropped I_lo P_lo is below 2^-16 of the product).  Row masks are decided in
+// FP32 from I exactly as in k_ps, and masked pixels take its FP64 path.
+//
+// Shared-memory operands use the canonical K-major layout without swizzle:
+// 8-row x 16-byte core matrices, the 16 core matrices of one 8-wide K column
+// of the 128 rows contiguous (stride 128 B between row groups), 2 KB between K
+// columns; segment hi, then lo.  One thread issues the MMAs; their completion
+// arrives on an mbarrier that all threads wait on (bounded), then each warp reads
+// its 32 accumulator rows from tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int kTcRows = 128;                 // M: pixels per tile, one per thread
+constexpr int kTcN = 16;                     // N: outputs (r, c), 3 C used
+constexpr int kTcSlack = 0;                  // spare shared memory after the operands
+constexpr long long kTcWaitPolls = 1ll << 22;  // bound of the MMA-completion wait
+
+// K*C padded: a multiple of 16 (the MMA's K) and of the fill chunk (24 for C = 3, 8 for C = 1).
+__host__ __device__ inline int tc_kcp(int K, int C) {
+  const int q = C == 3 ? 48 : 16;
+  return (K * C + q - 1) / q * q;
+}
+inline size_t tc_smem_bytes(int K, int C) {
+  const int kcp = tc_kcp(K, C);
+  return (size_t)512 * kcp + (size_t)64 * kcp + kTcSlack + 64;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start, leading (K-direction) and stride (row-group) byte offsets.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B (both K-major), N = 16, M = 128.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                              ((uint32_t)(kTcRows >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+  for (long long i = 0; i < kTcWaitPolls; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// x -> (hi, lo) in BF16, hi = bf16(x), lo = bf16(x - hi)
+__device__ __forceinline__ void split_bf16(float x, float &hi, float &lo) {
+  hi = __bfloat162float(__float2bfloat16_rn(x));
+  lo = __bfloat162float(__float2bfloat16_rn(x - hi));
+}
+
+template <int C, typename TI>
+__global__ void __launch_bounds__(kTcRows) k_ps_tc(const PSArgs a, unsigned long long *err) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  const int kc = a.K * C, kcp = tc_kcp(a.K, C), ncol = kcp / 8;
+  unsigned char *As = tc_smem;                            // 2 segments x ncol x 2 KB
+  unsigned char *Bs = tc_smem + (size_t)512 * kcp;        // 2 segments x ncol x 256 B
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(Bs + (size_t)64 * kcp + kTcSlack);
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(mbar + 1);
+  int *s_fail = reinterpret_cast<int *>(mbar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  // operands: zero A (its padding columns stay zero); B = pinv(L) per channel, hi and lo
+  for (int i = tid; i < 128 * kcp / 4; i += kTcRows) reinterpret_cast<uint32_t *>(As)[i] = 0u;
+  for (int i = tid; i < 2 * ncol * kTcN; i += kTcRows) {
+    const int seg = i / (ncol * kTcN), rem = i - seg * ncol * kTcN, q = rem / kTcN, n = rem - q * kTcN;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int kk = 8 * q + e;
+      float x = 0.0f;
+      if (kk < kc && n < 3 * C && (n % C) == (kk % C)) x = a.pinv[n / C][kk / C];
+      float hi, lo;
+      split_bf16(x, hi, lo);
+      v[e] = seg == 0 ? hi : lo;
+    }
+    uint4 w = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+    *reinterpret_cast<uint4 *>(Bs + (size_t)(seg * ncol + q) * 256 + (n >> 3) * 128 + (n & 7) * 16) = w;
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *s_fail = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(s_tmem))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *s_tmem;
+
+  const TI *img = reinterpret_cast<const TI *>(a.images);
+  const size_t P = (size_t)a.P;
+  const int n_tiles = (a.P + kTcRows - 1) / kTcRows;
+  constexpr int CH = C == 3 ? 24 : 8;  // values per fill step: whole lights and whole core columns
+  uint32_t phase = 0;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int p = tile * kTcRows + tid;
+    const bool in = p < a.P;
+    float rho[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) rho[c] = (in && !a.zero_indirect) ? a.albedo[c * P + p] : 0.0f;
+    unsigned long long valid = 0;
+    float R[3][C];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < C; ++c) R[r][c] = 0.0f;
+    unsigned char *row = As + (tid >> 3) * 128 + (tid & 7) * 16;
+    for (int q0 = 0; q0 < kcp; q0 += CH) {
+      float I[CH];
+#pragma unroll
+      for (int e = 0; e < CH; ++e) {
+        const int kk = q0 + e;
+        float a0 = 0.0f, lb = 0.0f;
+        if (in && kk < kc) {
+          a0 = load_img<TI>(img + (size_t)kk * P + p);
+          if (!a.zero_indirect) lb = __ldg(a.lbar + (size_t)kk * P + p);
+        }
+        I[e] = __fsub_rn(a0, __fmul_rn(rho[e % C], lb));
+      }
+      // row masks in FP32 and the masked system's right-hand side, as in ps_row
+#pragma unroll
+      for (int e = 0; e < CH; e += C) {
+        const int k = (q0 + e) / C;
+        float chat = I[e];
+        if (C == 3) chat = __fdiv_rn(__fadd_rn(__fadd_rn(I[e], I[e + 1]), I[e + 2]), 3.0f);
+        const bool ok = q0 + e < kc && chat > a.tau_lo && chat < a.tau_hi;
+        if (ok) valid |= 1ull << k;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const float l = ok ? a.light[k][r] : 0.0f;
+#pragma unroll
+          for (int c = 0; c < C; ++c) R[r][c] = fmaf(l, I[e + c], R[r][c]);
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < CH / 8; ++g) {
+        float hi[8], lo[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) split_bf16(I[8 * g + e], hi[e], lo[e]);
+        const int q = q0 / 8 + g;
+        *reinterpret_cast<uint4 *>(row + (size_t)q * 2048) =
+            make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]),
+                       pack_bf16(hi[6], hi[7]));
+        *reinterpret_cast<uint4 *>(row + (size_t)(ncol + q) * 2048) =
+            make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]), pack_bf16(lo[4], lo[5]),
+                       pack_bf16(lo[6], lo[7]));
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+      for (int j = 0; j < kcp / 16; ++j) {
+        const uint64_t ah = umma_desc(a0 + (uint32_t)(2 * j) * 2048u, 2048u, 128u);
+        const uint64_t al = umma_desc(a0 + (uint32_t)(ncol + 2 * j) * 2048u, 2048u, 128u);
+        const uint64_t bh = umma_desc(b0 + (uint32_t)(2 * j) * 256u, 256u, 128u);
+        const uint64_t bl = umma_desc(b0 + (uint32_t)(ncol + 2 * j) * 256u, 256u, 128u);
+        umma_bf16(tmem, ah, bh, j > 0 ? 1u : 0u);
+        umma_bf16(tmem, al, bh, 1u);
+        umma_bf16(tmem, ah, bl, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(mbar))
+                   : "memory");
+    }
+    const bool done = mbar_wait(smem_u32(mbar), phase);
+    phase ^= 1u;
+    if (!done) *s_fail = 1;
+    __syncthreads();
+    if (*s_fail) break;  // every thread leaves; the tensor memory is freed below
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    uint32_t d[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
+          "=r"(d[8]), "=r"(d[9]), "=r"(d[10]), "=r"(d[11]), "=r"(d[12]), "=r"(d[13]), "=r"(d[14]), "=r"(d[15])
+        : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (in) {
+      float G[3][C];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) G[r][c] = __uint_as_float(d[r * C + c]);
+      ps_finish<C, TI>(a, p, R, G, valid);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (tid == 0 && *s_fail) atomicAdd(err, 1ull);
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
 static void fill_ps_args(const Ctx &c, bool zero_indirect, PSArgs &a) {
@@ -227,24 +660,54 @@ cudaError_t launch_ps_batch(cudaStream_t s, int C, int dtype, const void *d_args
   return cudaGetLastError();
 }
 
+template <int C, typename TI>
+static cudaError_t launch_ps_tc_t(Ctx &c, const PSArgs &a) {
+  const size_t smem = tc_smem_bytes(c.K, C);
+  cudaError_t e = cudaFuncSetAttribute(k_ps_tc<C, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ps_tc<C, TI>, kTcRows, smem);
+  if (e != cudaSuccess) return e;
+  const int tiles = (a.P + kTcRows - 1) / kTcRows;
+  int blocks = (per > 0 ? per : 1) * (c.sms > 0 ? c.sms : 1);
+  if (blocks > tiles) blocks = tiles;
+  k_ps_tc<C, TI><<<blocks, kTcRows, smem, c.stream>>>(a, c.dstats->counts + 6);
+  return cudaGetLastError();
+}
+
+template <int C, typename TI>
+static cudaError_t launch_ps_split(Ctx &c, const PSArgs &a) {
+  const PSList L{c.ps_pix, c.ps_mask, c.ps_rhs, c.ps_count};
+  cudaError_t e = cudaMemsetAsync(c.ps_count, 0, sizeof(unsigned), c.stream);
+  if (e != cudaSuccess) return e;
+  const int threads = 256;
+  const int v = ps_vec_for(c);
+  const int n = (a.P + v - 1) / v;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  if (v == 4)
+    k_ps_fast<C, TI, 4><<<blocks, threads, 0, c.stream>>>(a, L);
+  else if (v == 2)
+    k_ps_fast<C, TI, 2><<<blocks, threads, 0, c.stream>>>(a, L);
+  else
+    k_ps_fast<C, TI, 1><<<blocks, threads, 0, c.stream>>>(a, L);
+  // one listed pixel per thread (the list can hold every pixel; threads past its end return)
+  k_ps_masked<C, TI><<<(unsigned)((a.P + 127) / 128), 128, 0, c.stream>>>(a, L);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ps(Ctx &c, bool zero_indirect) {
   PSArgs a;
   fill_ps_args(c, zero_indirect, a);
-  const int threads = 256;
-  const unsigned blocks = (unsigned)((a.P + threads - 1) / threads);
-  ++c.stats.launches;
-  if (c.C == 1) {
-    if (c.images_dtype == IRTPS_F16)
-      k_ps<1, __half><<<blocks, threads, 0, c.stream>>>(a);
-    else
-      k_ps<1, float><<<blocks, threads, 0, c.stream>>>(a);
-  } else {
-    if (c.images_dtype == IRTPS_F16)
-      k_ps<3, __half><<<blocks, threads, 0, c.stream>>>(a);
-    else
-      k_ps<3, float><<<blocks, threads, 0, c.stream>>>(a);
+  if (c.opt.ps_tensor) {
+    ++c.stats.launches;
+    if (c.C == 1)
+      return c.images_dtype == IRTPS_F16 ? launch_ps_tc_t<1, __half>(c, a) : launch_ps_tc_t<1, float>(c, a);
+    return c.images_dtype == IRTPS_F16 ? launch_ps_tc_t<3, __half>(c, a) : launch_ps_tc_t<3, float>(c, a);
   }
-  return cudaGetLastError();
+  c.stats.launches += 2;
+  if (c.C == 1)
+    return c.images_dtype == IRTPS_F16 ? launch_ps_split<1, __half>(c, a) : launch_ps_split<1, float>(c, a);
+  return c.images_dtype == IRTPS_F16 ? launch_ps_split<3, __half>(c, a) : launch_ps_split<3, float>(c, a);
 }
 
 }  // namespace irtps

@@ -38,15 +38,14 @@ constexpr int kGemmThreads = kTile * kTile;
 // A'(m, k) = A[m lda + k] (FA = 0) or A[m lda + k] + FA A[m lda + L-1-k] (the fold of a row of
 // length L; the middle element of an odd row alone), and B'(k, n) = B[n ldb + k] (TB) or the same
 // fold along B's rows (FB).  SCALE divides by mu[m + dro] + nu[n + dco] and drops the (0, 0) term.
+// One 16 x 16 output tile at (m0, n0) per block.
 template <int FA, int FB, bool TB, bool SCALE>
-__global__ void __launch_bounds__(kGemmThreads) k_dct_fwd(int M, int N, int K, int L, const double *__restrict__ A,
-                                                           int lda, const double *__restrict__ B, int ldb,
-                                                           double *__restrict__ D, int ldd, int dro, int dco,
-                                                           const double *__restrict__ mu,
-                                                           const double *__restrict__ nu) {
+__device__ __forceinline__ void dct_fwd_tile(const DctFwd &p, int m0, int n0) {
   __shared__ double As[kTile][kTile + 1];  // [k][m]
   __shared__ double Bs[kTile][kTile + 1];  // [k][n]
-  const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
+  const int M = p.M, N = p.N, K = p.K, L = p.L, lda = p.lda, ldb = p.ldb;
+  const double *__restrict__ A = p.A;
+  const double *__restrict__ B = p.B;
   const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
   double acc = 0.0;
   for (int k0 = 0; k0 < K; k0 += kTile) {
@@ -81,9 +80,9 @@ __global__ void __launch_bounds__(kGemmThreads) k_dct_fwd(int M, int N, int K, i
   const int m = m0 + ty, n = n0 + tx;
   if (m < M && n < N) {
     double v = acc;
-    const int gm = m + dro, gn = n + dco;
-    if (SCALE) v = (gm == 0 && gn == 0) ? 0.0 : v / (mu[gm] + nu[gn]);
-    D[(size_t)gm * ldd + gn] = v;
+    const int gm = m + p.dro, gn = n + p.dco;
+    if (SCALE) v = (gm == 0 && gn == 0) ? 0.0 : v / (p.mu[gm] + p.nu[gn]);
+    p.D[(size_t)gm * p.ldd + gn] = v;
   }
 }
 
@@ -93,14 +92,10 @@ __global__ void __launch_bounds__(kGemmThreads) k_dct_fwd(int M, int N, int K, i
 // ROWS: the output index m is a row i < ceil(L/2): D[i] = a + b, D[L-1-i] = a - b;
 // else n is a column j < ceil(L/2): D[., j] = a + b, D[., L-1-j] = a - b.
 template <bool TA, bool ROWS>
-__global__ void __launch_bounds__(kGemmThreads) k_dct_inv(int M, int N, int K1, int K2, int M2, int N2, int L,
-                                                           const double *__restrict__ A1, const double *__restrict__ A2,
-                                                           int lda1, int lda2, const double *__restrict__ B1,
-                                                           const double *__restrict__ B2, int ldb1, int ldb2,
-                                                           double *__restrict__ D, int ldd) {
+__device__ __forceinline__ void dct_inv_tile(const DctInv &p, int m0, int n0) {
   __shared__ double As1[kTile][kTile + 1], As2[kTile][kTile + 1];  // [k][m]
   __shared__ double Bs1[kTile][kTile + 1], Bs2[kTile][kTile + 1];  // [k][n]
-  const int m0 = blockIdx.y * kTile, n0 = blockIdx.x * kTile;
+  const int M = p.M, N = p.N, K1 = p.K1, K2 = p.K2, M2 = p.M2, N2 = p.N2, L = p.L;
   const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
   const int K = K1 > K2 ? K1 : K2;
   double a = 0.0, b = 0.0;
@@ -108,15 +103,15 @@ __global__ void __launch_bounds__(kGemmThreads) k_dct_inv(int M, int N, int K1, 
     {
       const int mm = TA ? tx : ty, kk = TA ? ty : tx;
       const int gm = m0 + mm, gk = k0 + kk;
-      const size_t i1 = TA ? (size_t)gk * lda1 + gm : (size_t)gm * lda1 + gk;
-      const size_t i2 = TA ? (size_t)gk * lda2 + gm : (size_t)gm * lda2 + gk;
-      As1[kk][mm] = (gm < M && gk < K1) ? A1[i1] : 0.0;
-      As2[kk][mm] = (gm < M2 && gk < K2) ? A2[i2] : 0.0;
+      const size_t i1 = TA ? (size_t)gk * p.lda1 + gm : (size_t)gm * p.lda1 + gk;
+      const size_t i2 = TA ? (size_t)gk * p.lda2 + gm : (size_t)gm * p.lda2 + gk;
+      As1[kk][mm] = (gm < M && gk < K1) ? p.A1[i1] : 0.0;
+      As2[kk][mm] = (gm < M2 && gk < K2) ? p.A2[i2] : 0.0;
     }
     {
       const int gn = n0 + tx, gk = k0 + ty;
-      Bs1[ty][tx] = (gn < N && gk < K1) ? B1[(size_t)gk * ldb1 + gn] : 0.0;
-      Bs2[ty][tx] = (gn < N2 && gk < K2) ? B2[(size_t)gk * ldb2 + gn] : 0.0;
+      Bs1[ty][tx] = (gn < N && gk < K1) ? p.B1[(size_t)gk * p.ldb1 + gn] : 0.0;
+      Bs2[ty][tx] = (gn < N2 && gk < K2) ? p.B2[(size_t)gk * p.ldb2 + gn] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -128,6 +123,8 @@ __global__ void __launch_bounds__(kGemmThreads) k_dct_inv(int M, int N, int K1, 
   }
   const int m = m0 + ty, n = n0 + tx;
   if (m >= M || n >= N) return;
+  double *D = p.D;
+  const int ldd = p.ldd;
   if (ROWS) {
     D[(size_t)m * ldd + n] = a + b;
     if (L - 1 - m != m) D[(size_t)(L - 1 - m) * ldd + n] = a - b;
@@ -135,6 +132,46 @@ __global__ void __launch_bounds__(kGemmThreads) k_dct_inv(int M, int N, int K1, 
     D[(size_t)m * ldd + n] = a + b;
     if (L - 1 - n != n) D[(size_t)m * ldd + (L - 1 - n)] = a - b;
   }
+}
+
+// Single object: blockIdx (x, y) = tile (column, row).
+template <int FA, int FB, bool TB, bool SCALE>
+__global__ void __launch_bounds__(kGemmThreads) k_dct_fwd(const DctFwd p) {
+  dct_fwd_tile<FA, FB, TB, SCALE>(p, blockIdx.y * kTile, blockIdx.x * kTile);
+}
+template <bool TA, bool ROWS>
+__global__ void __launch_bounds__(kGemmThreads) k_dct_inv(const DctInv p) {
+  dct_inv_tile<TA, ROWS>(p, blockIdx.y * kTile, blockIdx.x * kTile);
+}
+
+// Batched: the tiles of every object's pass in one launch; object o owns blocks
+// [blk_begin of o, blk_begin of o + 1), its tiles in row-major order.
+template <typename D>
+__device__ __forceinline__ int dct_object(const D *__restrict__ ps, int n, int &tile) {
+  __shared__ int s_o;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ps[mid].blk_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    s_o = lo;
+  }
+  __syncthreads();
+  tile = (int)blockIdx.x - ps[s_o].blk_begin;
+  return s_o;
+}
+template <int FA, int FB, bool TB, bool SCALE>
+__global__ void __launch_bounds__(kGemmThreads) k_dct_fwd_b(const DctFwd *__restrict__ ps, int n) {
+  int tile;
+  const DctFwd &p = ps[dct_object(ps, n, tile)];
+  dct_fwd_tile<FA, FB, TB, SCALE>(p, tile / p.tiles_n * kTile, tile % p.tiles_n * kTile);
+}
+template <bool TA, bool ROWS>
+__global__ void __launch_bounds__(kGemmThreads) k_dct_inv_b(const DctInv *__restrict__ ps, int n) {
+  int tile;
+  const DctInv &p = ps[dct_object(ps, n, tile)];
+  dct_inv_tile<TA, ROWS>(p, tile / p.tiles_n * kTile, tile % p.tiles_n * kTile);
 }
 
 dim3 grid_of(int M, int N) { return dim3((N + kTile - 1) / kTile, (M + kTile - 1) / kTile); }
@@ -191,32 +228,91 @@ cudaError_t spectral_setup(Ctx &c) {
   return e;
 }
 
-// x = A^+ b for the unit-weight grid Laplacian (b, x: H x W, FP64 device arrays).  The spectral
-// array between the passes holds the even frequencies of each axis before the odd ones.
-cudaError_t launch_spectral(Ctx &c, const double *b, double *x) {
+// The six passes of x = A^+ b for the unit-weight grid Laplacian of a context (b, x:
+// H x W, FP64 device arrays).  The spectral array between the passes holds the even
+// frequencies of each axis before the odd ones.
+static void spectral_passes(const Ctx &c, const double *b, double *x, DctFwd f[4], DctInv v[2]) {
   const int H = c.H, W = c.W;
   const int heH = (H + 1) / 2, hoH = H / 2, heW = (W + 1) / 2, hoW = W / 2;
   const double *EH = c.sp_ch, *OH = c.sp_ch + (size_t)heH * heH;
   const double *EW = c.sp_cw, *OW = c.sp_cw + (size_t)heW * heW;
   double *t = c.sp_t;
-  cudaStream_t s = c.stream;
   // columns: t = C_H b (even rows from the row sums, odd rows from the differences)
-  k_dct_fwd<0, 1, false, false><<<grid_of(heH, W), kGemmThreads, 0, s>>>(heH, W, heH, H, EH, heH, b, W, t, W, 0,
-                                                                        0, nullptr, nullptr);
-  k_dct_fwd<0, -1, false, false><<<grid_of(hoH, W), kGemmThreads, 0, s>>>(hoH, W, hoH, H, OH, hoH, b, W, t, W,
-                                                                         heH, 0, nullptr, nullptr);
+  f[0] = DctFwd{heH, W, heH, H, EH, heH, b, W, t, W, 0, 0, nullptr, nullptr, 0, 0};
+  f[1] = DctFwd{hoH, W, hoH, H, OH, hoH, b, W, t, W, heH, 0, nullptr, nullptr, 0, 0};
   // rows: x = (t C_W^T) ./ (mu + nu), the (0, 0) term dropped
-  k_dct_fwd<1, 0, true, true><<<grid_of(H, heW), kGemmThreads, 0, s>>>(H, heW, heW, W, t, W, EW, heW, x, W, 0, 0,
-                                                                      c.sp_mu, c.sp_nu);
-  k_dct_fwd<-1, 0, true, true><<<grid_of(H, hoW), kGemmThreads, 0, s>>>(H, hoW, hoW, W, t, W, OW, hoW, x, W, 0,
-                                                                       heW, c.sp_mu, c.sp_nu);
+  f[2] = DctFwd{H, heW, heW, W, t, W, EW, heW, x, W, 0, 0, c.sp_mu, c.sp_nu, 0, 0};
+  f[3] = DctFwd{H, hoW, hoW, W, t, W, OW, hoW, x, W, 0, heW, c.sp_mu, c.sp_nu, 0, 0};
   // columns back: t = C_H^T x
-  k_dct_inv<true, true><<<grid_of(heH, W), kGemmThreads, 0, s>>>(heH, W, heH, hoH, hoH, W, H, EH, OH, heH, hoH, x,
-                                                                 x + (size_t)heH * W, W, W, t, W);
+  v[0] = DctInv{heH, W, heH, hoH, hoH, W, H, EH, OH, heH, hoH, x, x + (size_t)heH * W, W, W, t, W, 0, 0};
   // rows back: x = t C_W
-  k_dct_inv<false, false><<<grid_of(H, heW), kGemmThreads, 0, s>>>(H, heW, heW, hoW, H, hoW, W, t, t + heW, W, W,
-                                                                   EW, OW, heW, hoW, x, W);
+  v[1] = DctInv{H, heW, heW, hoW, H, hoW, W, t, t + heW, W, W, EW, OW, heW, hoW, x, W, 0, 0};
+  for (int i = 0; i < 4; ++i) f[i].tiles_n = (f[i].N + kTile - 1) / kTile;
+  for (int i = 0; i < 2; ++i) v[i].tiles_n = (v[i].N + kTile - 1) / kTile;
+}
+
+cudaError_t launch_spectral(Ctx &c, const double *b, double *x) {
+  DctFwd f[4];
+  DctInv v[2];
+  spectral_passes(c, b, x, f, v);
+  cudaStream_t s = c.stream;
+  k_dct_fwd<0, 1, false, false><<<grid_of(f[0].M, f[0].N), kGemmThreads, 0, s>>>(f[0]);
+  k_dct_fwd<0, -1, false, false><<<grid_of(f[1].M, f[1].N), kGemmThreads, 0, s>>>(f[1]);
+  k_dct_fwd<1, 0, true, true><<<grid_of(f[2].M, f[2].N), kGemmThreads, 0, s>>>(f[2]);
+  k_dct_fwd<-1, 0, true, true><<<grid_of(f[3].M, f[3].N), kGemmThreads, 0, s>>>(f[3]);
+  k_dct_inv<true, true><<<grid_of(v[0].M, v[0].N), kGemmThreads, 0, s>>>(v[0]);
+  k_dct_inv<false, false><<<grid_of(v[1].M, v[1].N), kGemmThreads, 0, s>>>(v[1]);
   c.stats.launches += 6;
+  return cudaGetLastError();
+}
+
+// Batched direct solves: one launch per pass over the objects whose unit-weight
+// solves are direct; each object's pass descriptors point at its own arrays.
+cudaError_t spectral_batch_setup(const std::vector<Ctx *> &objs, SpectralBatch &sb) {
+  sb.n = 0;
+  std::vector<DctFwd> f[4];
+  std::vector<DctInv> v[2];
+  for (int i = 0; i < 4; ++i) sb.blocks[i] = 0;
+  sb.blocks[4] = sb.blocks[5] = 0;
+  for (Ctx *c : objs) {
+    if (!direct_solve(*c)) continue;
+    DctFwd ff[4];
+    DctInv vv[2];
+    spectral_passes(*c, c->cg_b, c->cg_x, ff, vv);
+    for (int i = 0; i < 4; ++i) {
+      ff[i].blk_begin = sb.blocks[i];
+      sb.blocks[i] += ((ff[i].M + kTile - 1) / kTile) * ff[i].tiles_n;
+      f[i].push_back(ff[i]);
+    }
+    for (int i = 0; i < 2; ++i) {
+      vv[i].blk_begin = sb.blocks[4 + i];
+      sb.blocks[4 + i] += ((vv[i].M + kTile - 1) / kTile) * vv[i].tiles_n;
+      v[i].push_back(vv[i]);
+    }
+    ++sb.n;
+  }
+  if (sb.n == 0) return cudaSuccess;
+  const size_t fb = sizeof(DctFwd) * sb.n, vb = sizeof(DctInv) * sb.n;
+  cudaError_t e = cudaMalloc(&sb.table, 4 * fb + 2 * vb);
+  if (e != cudaSuccess) return e;
+  unsigned char *t = (unsigned char *)sb.table;
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMemcpy(t + i * fb, f[i].data(), fb, cudaMemcpyHostToDevice);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    e = cudaMemcpy(t + 4 * fb + i * vb, v[i].data(), vb, cudaMemcpyHostToDevice);
+  return e;
+}
+
+cudaError_t launch_spectral_batch(cudaStream_t s, const SpectralBatch &sb) {
+  if (sb.n == 0) return cudaSuccess;
+  const DctFwd *f = (const DctFwd *)sb.table;
+  const DctInv *v = (const DctInv *)(f + 4 * sb.n);
+  const int n = sb.n;
+  k_dct_fwd_b<0, 1, false, false><<<sb.blocks[0], kGemmThreads, 0, s>>>(f, n);
+  k_dct_fwd_b<0, -1, false, false><<<sb.blocks[1], kGemmThreads, 0, s>>>(f + n, n);
+  k_dct_fwd_b<1, 0, true, true><<<sb.blocks[2], kGemmThreads, 0, s>>>(f + 2 * n, n);
+  k_dct_fwd_b<-1, 0, true, true><<<sb.blocks[3], kGemmThreads, 0, s>>>(f + 3 * n, n);
+  k_dct_inv_b<true, true><<<sb.blocks[4], kGemmThreads, 0, s>>>(v, n);
+  k_dct_inv_b<false, false><<<sb.blocks[5], kGemmThreads, 0, s>>>(v + n, n);
   return cudaGetLastError();
 }
 

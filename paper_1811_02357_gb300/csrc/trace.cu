@@ -834,11 +834,11 @@ cudaError_t launch_trace(Ctx &c, const int32_t *pixels, int n_pix, int spp, int 
   }
   a.n_items = (unsigned)n;
   const int threads = kTraceThreads;
+  if (cudaMemsetAsync(a.next_item, 0, sizeof(unsigned), c.stream) != cudaSuccess) return cudaGetLastError();
+  ++c.stats.launches;
   // a persistent grid: as many blocks as stay resident, each lane claiming items until none remain
   long long blocks = (n + threads - 1) / threads;
   if (c.trace_blocks > 0 && blocks > c.trace_blocks) blocks = c.trace_blocks;
-  if (cudaMemsetAsync(a.next_item, 0, sizeof(unsigned), c.stream) != cudaSuccess) return cudaGetLastError();
-  ++c.stats.launches;
   const size_t smem = trace_smem_bytes(1);
   if (shared) {
     if (c.C == 1)
@@ -878,10 +878,10 @@ cudaError_t launch_trace_batch(cudaStream_t s, int C, bool shared, const ObjTrac
   a.iter = iter;
   a.stream = 0u;
   const int threads = kTraceThreads;
+  if (cudaMemsetAsync(next_item, 0, sizeof(unsigned), s) != cudaSuccess) return cudaGetLastError();
   long long blocks = ((long long)n_items + threads - 1) / threads;
   if (grid_limit > 0 && blocks > grid_limit) blocks = grid_limit;
   if (blocks < 1) blocks = 1;
-  if (cudaMemsetAsync(next_item, 0, sizeof(unsigned), s) != cudaSuccess) return cudaGetLastError();
   const size_t smem = trace_smem_bytes(n_obj);
   if (shared) {
     if (C == 1)
@@ -1010,21 +1010,31 @@ __global__ void k_render(const ObjTrace a, const float *__restrict__ lbar, float
 }
 
 // Resident blocks of the trace kernel for C channels (the persistent grid size);
-// n_obj > 0: the batched kernel over n_obj objects.
-int trace_grid_limit(int C, int n_obj) {
-  int dev = 0, sms = 0, per = 0;
+// n_obj > 0: the batched kernel over n_obj objects; shared: the light-shared kernel,
+// else the per-light one.
+template <typename F>
+static int grid_of(F kernel, size_t smem, int sms) {
+  int per = 0;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kTraceThreads, smem) != cudaSuccess) return 0;
+  return per * sms;
+}
+
+int trace_grid_limit(int C, int n_obj, bool shared) {
+  int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   const size_t smem = trace_smem_bytes(n_obj > 0 ? n_obj : 1);
-  cudaError_t e;
+  if (shared) {
+    if (n_obj > 0)
+      return C == 1 ? grid_of(k_trace<1, true, true>, smem, sms) : grid_of(k_trace<3, true, true>, smem, sms);
+    return C == 1 ? grid_of(k_trace<1, false, true>, smem, sms) : grid_of(k_trace<3, false, true>, smem, sms);
+  }
   if (n_obj > 0)
-    e = C == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<1, true, false>, kTraceThreads, smem)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<3, true, false>, kTraceThreads, smem);
-  else
-    e = C == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<1, false, false>, kTraceThreads, smem)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trace<3, false, false>, kTraceThreads, smem);
-  if (e != cudaSuccess) return 0;
-  return per * sms;
+    return C == 1 ? grid_of(k_trace<1, true, false>, smem, sms) : grid_of(k_trace<3, true, false>, smem, sms);
+  return C == 1 ? grid_of(k_trace<1, false, false>, smem, sms) : grid_of(k_trace<3, false, false>, smem, sms);
 }
 
 cudaError_t launch_render(Ctx &c, uint64_t seed, float sigma, const float *lbar, float *out) {

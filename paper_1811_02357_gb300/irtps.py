@@ -25,6 +25,7 @@ IRTPS_ETIMEOUT = -5
 IRTPS_ENUMERIC = -6
 IRTPS_F32 = 0
 IRTPS_F16 = 1
+NOALLOC_MAX_PIXELS = 512 * 512  # grid size limit of irtps_integrate_noalloc
 FORWARD_ITER = 0xFFFFFFFF
 
 EXPORTED = [
@@ -34,7 +35,7 @@ EXPORTED = [
     "irtps_get_indirect", "irtps_get_valid", "irtps_get_holes", "irtps_get_stats", "irtps_probe_dirs",
     "irtps_probe_rays", "irtps_interpolate_holes",
     "irtps_last_error", "irtps_destroy", "irtps_integrate_noalloc", "irtps_set_object", "irtps_set_tuning",
-    "irtps_get_tuning", "irtps_autotune", "irtps_batch_create", "irtps_batch_set_stream", "irtps_batch_set_images", "irtps_batch_iterate", "irtps_batch_get_stats",
+    "irtps_get_tuning", "irtps_autotune", "irtps_set_ps_tuning", "irtps_get_ps_tuning", "irtps_batch_create", "irtps_batch_set_stream", "irtps_batch_set_images", "irtps_batch_iterate", "irtps_batch_get_stats",
     "irtps_batch_set_tuning", "irtps_batch_get_tuning", "irtps_batch_autotune", "irtps_batch_last_error",
     "irtps_batch_destroy",
 ]
@@ -46,7 +47,7 @@ class irtps_options(ctypes.Structure):
                 ("cg_max_iter", ctypes.c_int), ("cg_check_every", ctypes.c_int), ("stop_tol", ctypes.c_double),
                 ("precond", ctypes.c_int), ("use_graph", ctypes.c_int), ("sampling", ctypes.c_int),
                 ("irls_iters", ctypes.c_int), ("irls_delta", ctypes.c_float), ("early_escape", ctypes.c_int),
-                ("fill_holes", ctypes.c_int)]
+                ("fill_holes", ctypes.c_int), ("ps_tensor", ctypes.c_int)]
 
 
 class irtps_stats(ctypes.Structure):
@@ -104,6 +105,8 @@ def _load():
         "irtps_set_object": (i32, [P, u32]),
         "irtps_set_tuning": (i32, [P, i32, i32]),
         "irtps_get_tuning": (i32, [P, P, P]),
+        "irtps_set_ps_tuning": (i32, [P, i32]),
+        "irtps_get_ps_tuning": (i32, [P, P]),
         "irtps_autotune": (i32, [P, i32, i32, u64, P]),
         "irtps_batch_create": (i32, [P, P, i32, i32]),
         "irtps_batch_iterate": (i32, [P, i32, P, P, u64, P]),
@@ -303,9 +306,24 @@ def irtps_probe_rays(h, rays):
     return t, tri
 
 
+def _device_f32(t, n, name, align=4):
+    """A CUDA float32 tensor, contiguous, with at least n elements and `align`-byte aligned (the
+    kernels read past no end of it); raises before the C call otherwise."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name}: need a contiguous float32 CUDA tensor")
+    if t.numel() < n:
+        raise ValueError(f"{name}: {t.numel()} elements, need {n}")
+    if t.data_ptr() % align:
+        raise ValueError(f"{name}: address not {align}-byte aligned")
+
+
 def irtps_integrate_noalloc(normals, depth, H, W, nz_min=0.05, tol=1e-9, max_iter=50000, stream=0):
     """Allocation-free depth solve on device buffers: normals (H, W, 4) float32, depth (H, W) float32
     (warm start in, surface out).  `stream` is a raw cudaStream_t value (0: legacy default stream)."""
+    runs = H >= 2 and W >= 2 and H * W <= NOALLOC_MAX_PIXELS  # else the library rejects the sizes itself
+    _device_f32(normals, 4 * H * W if runs else 0, "normals", 16)  # read as float4
+    _device_f32(depth, H * W if runs else 0, "depth")
     rc = _lib.irtps_integrate_noalloc(_addr(normals), H, W, nz_min, tol, max_iter, _addr(depth),
                                       ctypes.c_void_p(stream))
     if rc != IRTPS_OK:
@@ -322,6 +340,16 @@ def irtps_set_object(h, obj):
 
 def irtps_set_tuning(h, blocks_per_sm, mip_cut):
     _check(h, _lib.irtps_set_tuning(h, blocks_per_sm, mip_cut))
+
+
+def irtps_set_ps_tuning(h, pixels_per_thread):
+    _check(h, _lib.irtps_set_ps_tuning(h, pixels_per_thread))
+
+
+def irtps_get_ps_tuning(h):
+    v = ctypes.c_int(0)
+    _check(h, _lib.irtps_get_ps_tuning(h, ctypes.byref(v)))
+    return v.value
 
 
 def irtps_get_tuning(h):
@@ -503,6 +531,12 @@ class Context:
 
     def tuning(self):
         return irtps_get_tuning(self.h)
+
+    def set_ps_tuning(self, pixels_per_thread):
+        irtps_set_ps_tuning(self.h, pixels_per_thread)
+
+    def ps_tuning(self):
+        return irtps_get_ps_tuning(self.h)
 
     def autotune(self, spp_probe, bounces, seed):
         return irtps_autotune(self.h, spp_probe, bounces, seed)

@@ -101,3 +101,23 @@ def test_integrate_quadric_exact(lib, oracle_mod):
     want = f - f.mean()
     # exact up to the float32 rounding of the normals and of the stored depth
     assert np.abs(d - want).max() < 2e-5 * np.ptp(want)
+
+
+@pytest.mark.parametrize("H,W", [(64, 48), (45, 38), (20, 9)])
+def test_ps_widths_give_the_same_bits(lib, oracle_mod, H, W):
+    """One, two or four pixels per thread (a tuning knob; grids whose pixel count is not a
+    multiple fall back to one) and the tensor-core form's masks: the FP32 form's results do
+    not depend on the width, bit for bit, through classic PS and a traced iteration."""
+    sc = scenes.mixed(H + W, H, W, K=7, C=3)
+    A0 = _images(oracle_mod, sc, spp=8)
+    out = []
+    for v in (1, 2, 4):
+        with lib.Context(H, W, sc.lights, sc.env) as ctx:
+            ctx.set_ps_tuning(v)
+            assert ctx.ps_tuning() in ((v,) if (H * W) % v == 0 else (1,))
+            ctx.set_images(A0.astype(np.float16), lib.IRTPS_F16)
+            ctx.iterate(1, 4, 2, 3)
+            out.append((ctx.normals(), ctx.albedo(), ctx.valid()))
+    for o in out[1:]:
+        for x, y in zip(out[0], o):
+            assert np.array_equal(x, y)

@@ -28,13 +28,15 @@ def _reference_depth(lib, normals, H, W):
 def test_noalloc_matches_allocating_solve(lib):
     import torch
     stream = torch.cuda.current_stream().cuda_stream
-    for seed, H, W in [(3, 64, 48), (4, 37, 53)]:
+    # two small grids in a row (the second starts from the first's leftovers), then the size
+    # limit itself, square and long-and-thin: the whole scratch layout in use
+    for seed, H, W in [(3, 64, 48), (4, 37, 53), (5, 512, 512), (6, 128, 2048)]:
         sc = scenes.mixed(seed, H, W, K=3, C=1)
         want = _reference_depth(lib, sc.normals, H, W)
         n4 = torch.zeros((H, W, 4), dtype=torch.float32, device="cuda")
         n4[..., :3] = torch.from_numpy(sc.normals).cuda()
         depth = torch.zeros((H, W), dtype=torch.float32, device="cuda")
-        lib.irtps_integrate_noalloc(n4, depth, H, W, stream=stream)
+        lib.irtps_integrate_noalloc(n4, depth, H, W, stream=stream)  # raises unless IRTPS_OK
         got = depth.cpu().numpy()
         rng = np.ptp(want)
         assert np.abs(got - want).max() <= 1e-4 * rng, (H, W, np.abs(got - want).max() / rng)
@@ -47,3 +49,15 @@ def test_noalloc_rejects_oversize(lib):
     with pytest.raises(lib.IrtpsError) as e:
         lib.irtps_integrate_noalloc(n4, d, 513, 512)
     assert e.value.code == lib.IRTPS_EINVAL
+
+
+def test_noalloc_wrapper_checks_buffers(lib):
+    """The binding refuses buffers the kernels would read or write past, before any device work."""
+    import torch
+    H, W = 16, 12
+    n4 = torch.zeros((H, W, 4), dtype=torch.float32, device="cuda")
+    d = torch.zeros((H, W), dtype=torch.float32, device="cuda")
+    for bad_n, bad_d in [(n4[:, :, :3].contiguous(), d), (n4, d[:-1]), (n4.double(), d), (n4, d.cpu()),
+                         (n4.reshape(-1)[1:4 * H * W + 1], d)]:
+        with pytest.raises(ValueError):
+            lib.irtps_integrate_noalloc(bad_n, bad_d, H, W)
