@@ -1,19 +1,35 @@
-"""IRT-PS benchmark: Mrays/s of the whole loop on one seeded synthetic workload.
+"""IRT-PS benchmark: Mrays/s of the IRT-PS loop on one seeded synthetic workload.
 
-Workload `bumps_512` (default): 512x512 RGB heightfield of 20 Gaussian bumps and
-dents plus a 90-degree V-groove, Voronoi albedo, 32x64 RGB cosine environment,
-K = 12 lights; trace 256 spp, 2 bounces; one step = one whole job: iteration 0
-(classic PS + integration) from device-resident images, then 5 IRT iterations
-(pyramid, trace, subtract + PS, integration, D_H).  Input images are rendered
-once on the GPU from the ground truth (256 spp, 2 bounces, sigma 0.002).
+Workload `bumps_2048` (default; the 2048x2048 precision configuration at its full
+spec): 2048x2048 RGB heightfield of 200 Gaussian bumps and 4 concave bowls,
+Voronoi albedo, 64x128 RGB cosine environment, K = 32 lights on a jittered ring,
+images stored in FP16; trace 512 spp per (pixel, light), 2 bounces.  Input images
+are rendered once on the GPU from the ground truth (64 spp, 2 bounces, sigma 0.002).
 
-value      = traced segments (primary, bounce and shadow rays) / second, all ranks
-e2e        = the same through the C ABI from pinned host images, results copied back
+One step is what a user of the C ABI runs per IRT iteration: upload the images
+from pinned host memory (irtps_set_images, which also runs iteration 0: classic
+PS + integration), one IRT iteration (irtps_iterate: pyramid, horizon bounds,
+trace, subtract + PS, integration, D_H), and read the depth, normals and albedo
+back to pinned host memory.
+
+value      = traced segments (primary, bounce and shadow rays) / second of the IRT
+             iterations (CUDA events around irtps_iterate; inputs resident in HBM)
+e2e        = the same segments / second of the whole step (events around all three
+             calls: host->device images, iteration 0, the iteration, results back)
+accuracy   = stage-wise errors against the FP64 oracle (outside the timed region):
+             given the GPU's iteration-t state, the oracle traces sampled pixels,
+             solves their normals from the same FP16 images, and integrates the
+             GPU's normals over the whole grid
 roofline   = the trace kernel (dominant): algorithmic lane operations per second
              against the lane-issue peak (bound "alu")
 cpu_baseline = the oracle (plain C++) on the host cores over a pixel sample
 evaluation (--evaluate) = errors against the ground truth (height, albedo, normal; the paper's
              evaluation measures) of classic PS and of IRT-PS with 1, 2 and 3 traced reflections
+
+Other workloads: `bumps_512` (512x512 RGB bumps and a V-groove, K = 12, 256 spp,
+2 bounces; one step = a 5-iteration job), `bowl_64` (64x64 bowl), `bumps_4096_spp16`
+(4096x4096, K = 64 at 16 spp), `bumps_512_single` (one sample per (pixel, light),
+holes filled).
 
 Workload `batch_64`: 64 objects of scenes.batch_objects (sides log-uniform in
 96..1024, K in {4, 8, 16, 32}, spp in {64, 128, 256}, bounces in {1, 2}); one
@@ -39,14 +55,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # name: (scene factory, its arguments, spp, bounces, IRT iterations per job, render spp, render bounces)
+    # name: (scene factory, its arguments, spp, bounces, IRT iterations per step, render spp, render bounces)
+    # the 2048x2048, K = 32 precision configuration at its full spec (FP16 images, 512 spp, 2 bounces)
+    "bumps_2048": ("bumps_2048", {}, 512, 2, 1, 64, 2),
     "bumps_512": ("bumps_512", {}, 256, 2, 5, 256, 2),
     "bowl_64": ("bowl_64", {}, 64, 1, 3, 256, 1),
     # a small case of the same kernels for profiler captures (one IRT iteration per job)
     "bumps_256_profile": ("bumps_512", {"H": 256, "W": 256}, 32, 2, 1, 32, 2),
-    # the 2048x2048, K = 32 configuration at an eighth of its samples (64 spp), one IRT iteration per job
+    # the 2048x2048, K = 32 configuration at an eighth of its samples (64 spp)
     "bumps_2048_spp64": ("bumps_2048", {}, 64, 2, 1, 4, 1),
-    # the 4096x4096, K = 64 configuration at a sixty-fourth of its samples (16 spp), one IRT iteration per job
+    # the 4096x4096, K = 64 configuration at a sixty-fourth of its samples (16 spp)
     "bumps_4096_spp16": ("bumps_4096", {}, 16, 2, 1, 4, 1),
     # the batched pattern: 64 objects (sides 96..1024, K, spp, bounces per object), one IRT
     # iteration of all of them per step, against per-object launches (run_batch)
@@ -58,6 +76,10 @@ WORKLOADS = {
 }
 # context options a workload sets beyond the defaults
 WORKLOAD_OPTIONS = {"bumps_512_single": {"fill_holes": 1}}
+# image storage of a workload when --images is not given (the precision configurations keep FP16)
+WORKLOAD_IMAGES = {"bumps_2048": "f16", "bumps_2048_spp64": "f16", "bumps_4096_spp16": "f16"}
+# tuner probes take spp / this many samples (a few seconds of probes on the large grids)
+WORKLOAD_TUNE_DIV = {"bumps_2048": 64, "bumps_2048_spp64": 8, "bumps_4096_spp16": 4}
 
 # Algorithmic lane operations per unit of trace work (counted from the formulas:
 # Philox4x32-10 = 10 rounds x (2 mul.hi + 2 mul.lo + 4 xor) + 9 x 2 key adds;
@@ -67,13 +89,10 @@ WORKLOAD_OPTIONS = {"bumps_512_single": {"fill_holes": 1}}
 OPS_PER_DRAW = 98 + 47
 OPS_PER_NODE = 16
 OPS_PER_TRI = 57
-SM_COUNT = 152
 LANES_PER_SM = 128
-# DRAM bytes (read + write) of one trace launch of a workload, from the ncu capture summarised in
-# profiles/k_trace_bumps512_dram.md (the kernel has not changed since)
-TRACE_DRAM_BYTES = {"bumps_512": 19.29e6 + 2.27e6}
-# the same for light-shared sampling (profiles/k_trace_shared_bumps512_dram.md)
-TRACE_DRAM_BYTES_SHARED = {"bumps_512": 322.63e6 + 270.69e6}
+# DRAM bytes (read + write) of one trace launch, per workload and sampling, from ncu captures of the
+# same kernel; None where no capture of the current kernel exists
+TRACE_DRAM_BYTES = {}
 
 
 def sm_max_mhz():
@@ -198,6 +217,52 @@ def combine_ranks(ms, units, world, device):
     return float(t.item()), float(u.item())
 
 
+def split_objects(costs, world):
+    """Cost-balanced split of a batch's objects over ranks: objects in order of decreasing cost
+    (ties by index), each to the rank whose total is smallest so far (ties to the lower rank).
+    Returns each rank's object indices, ascending."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def gather_objects(local, sizes, parts, world, rank, device):
+    """One collective at the end of a split batch job: every rank contributes the float32 results
+    of its own objects (local: object index -> 1-D array of sizes[index] values); rank 0 returns
+    {index: array} for every object, the other ranks None.  The objects of rank r are packed in
+    ascending order, padded to the longest rank's length, and all ranks' buffers exchanged by one
+    all_gather (any backend: nccl on GPUs, gloo on CPU)."""
+    import torch
+    import torch.distributed as dist
+    lengths = [sum(sizes[i] for i in p) for p in parts]
+    n = max(lengths) if lengths else 0
+    buf = torch.zeros(n, dtype=torch.float32, device=device)
+    off = 0
+    for i in parts[rank]:
+        buf[off:off + sizes[i]] = torch.as_tensor(np.asarray(local[i], np.float32).ravel(), device=device)
+        off += sizes[i]
+    if world > 1:
+        bufs = [torch.empty(n, dtype=torch.float32, device=device) for _ in range(world)]
+        dist.all_gather(bufs, buf)
+    else:
+        bufs = [buf]
+    if rank != 0:
+        return None
+    out = {}
+    for r, p in enumerate(parts):
+        b = bufs[r].cpu().numpy()
+        off = 0
+        for i in p:
+            out[i] = b[off:off + sizes[i]].copy()
+            off += sizes[i]
+    return out
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -278,7 +343,9 @@ def run_reference(args):
 
 
 def run_batch(args):
-    """The batched pattern: all objects in one batch against per-object contexts."""
+    """The batched pattern: the objects of the job in one batch per rank (a cost-balanced split of
+    the objects over the ranks; one gather of the results at the end), against per-object
+    contexts."""
     import torch
     import scenes
     from paper_1811_02357_gb300 import build
@@ -291,9 +358,12 @@ def run_batch(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    _, _, _, _, n_iter, rspp, rb = WORKLOADS[args.workload]
-    _, kw, _, _, _, _, _ = WORKLOADS[args.workload]
-    objs = scenes.batch_objects(seed=4 + 100 * rank, **kw)
+    _, kw, _, _, n_iter, rspp, rb = WORKLOADS[args.workload]
+    job = scenes.batch_objects(seed=4, **kw)  # the same job on every rank
+    costs = [float(sc.H * sc.W * sc.K * s_ * b_) for sc, s_, b_ in job]
+    parts = split_objects(costs, world)
+    mine = parts[rank]
+    objs = [job[i] for i in mine]
     stream = torch.cuda.Stream(device=dev)
     img_dtype = irtps.IRTPS_F16 if args.images == "f16" else irtps.IRTPS_F32
     ctxs, imgs = [], []
@@ -301,42 +371,66 @@ def run_batch(args):
     opt.sampling = 1 if args.sampling == "shared" else 0
     if args.early_escape is not None:
         opt.early_escape = args.early_escape
-    for i, (sc, _, _) in enumerate(objs):
+    for g, (sc, _, _) in zip(mine, objs):
         c = irtps.Context(sc.H, sc.W, sc.lights, sc.env, opt)
         c.set_stream(stream.cuda_stream)
         c.set_state(sc.depth, sc.normals, sc.albedo)
         A = torch.empty((sc.K, sc.C, sc.H, sc.W), dtype=torch.float32, device=dev)
-        c.render(rspp, rb, 1000 + i, 0.002, out=A)
+        c.render(rspp, rb, 1000 + g, 0.002, out=A)
         ctxs.append(c)
         imgs.append(A.half() if args.images == "f16" else A)
     torch.cuda.synchronize()
     spp = [o[1] for o in objs]
     bnc = [o[2] for o in objs]
-    seed = 1 + rank
+    seed = 1
+    # pinned host images and results of the end-to-end path (copied in and out every step)
+    host = []
+    for a in imgs:
+        h = torch.empty(a.shape, dtype=a.dtype, pin_memory=True)
+        h.copy_(a.cpu())
+        host.append(h)
+    outs = [torch.empty((sc.H, sc.W), pin_memory=True) for sc, _, _ in objs]
+
+    def make_batch(use_graph):
+        b = irtps.Batch(ctxs, use_graph=use_graph)
+        b.set_stream(stream.cuda_stream)
+        for c, g in zip(ctxs, mine):  # each object keeps its index in the whole job (its Philox key)
+            c.set_object(g)
+        return b
+
     # stage events need the enqueued form; the captured (graph) form is timed once after it
-    batch = irtps.Batch(ctxs, use_graph=False)
-    batch.set_stream(stream.cuda_stream)
+    batch = make_batch(False)
     P = sum(sc.H * sc.W for sc, _, _ in objs)
 
-    def set_all(host=None):
-        src = host if host is not None else imgs
+    def set_all(src, on_device):
         ptrs = (irtps.ctypes.c_void_p * len(src))(*[a.data_ptr() for a in src])
-        irtps._check_batch(batch.b, irtps._lib.irtps_batch_set_images(batch.b, ptrs, img_dtype,
-                                                                      0 if host is not None else 1))
+        irtps._check_batch(batch.b, irtps._lib.irtps_batch_set_images(batch.b, ptrs, img_dtype, on_device))
         return batch.stats()
 
-    def batched():
-        s0 = set_all()
+    def step(ev=None):
+        """One user step: images in from pinned host memory (iteration 0 of every object), the IRT
+        iteration, every object's depth back; ev = four events (start, iteration start / end, end)."""
+        if ev:
+            ev[0].record(stream)
+        s0 = set_all(host, 0)
+        if ev:
+            ev[1].record(stream)
         batch.iterate(n_iter, spp, bnc, seed)
+        if ev:
+            ev[2].record(stream)
         st = dict(batch.stats())
-        for k in ("ps_ms", "depth_ms"):
-            st[k] += s0[k]
+        for c, o in zip(ctxs, outs):
+            irtps._check(c.h, irtps._lib.irtps_get_depth(c.h, irtps._addr(o.data_ptr()), 0))
+        if ev:
+            ev[3].record(stream)
+        st["set_ps_ms"], st["set_depth_ms"] = s0["ps_ms"], s0["depth_ms"]
         return st
 
     def per_object():
         segs = 0
-        for c, s_, b_ in zip(ctxs, spp, bnc):
-            c.set_images(imgs[ctxs.index(c)], dtype=img_dtype, on_device=True)
+        for c, g, a, s_, b_ in zip(ctxs, mine, imgs, spp, bnc):
+            c.set_object(g)
+            c.set_images(a, dtype=img_dtype, on_device=True)
             c.iterate(n_iter, s_, b_, seed)
             segs += c.stats()["segments"]
         return segs
@@ -354,92 +448,96 @@ def run_batch(args):
 
     # the tuner picks the trace grid and pyramid depth (no result bit depends on them)
     if not args.no_autotune and not args.workload.endswith("_profile"):  # profile cases keep the defaults
-        set_all()
+        set_all(imgs, 1)
         batch.autotune([max(1, s_ // (4 if args.sampling == "shared" else 16)) for s_ in spp], bnc, seed)
     for _ in range(args.warmup):
-        batched()
+        step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     launches0 = batch.stats()["launches"] + sum(c.stats()["launches"] for c in ctxs)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    res = []
     with ClockSampler(local) as clk:
-        res = timed(batched, args.steps)
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            res.append(step(evs[i]))
+        torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
     launches = batch.stats()["launches"] + sum(c.stats()["launches"] for c in ctxs) - launches0
-    ms = sum(r[0] for r in res)
-    segs = sum(r[1]["segments"] for r in res)
-    draws = sum(r[1]["draws"] for r in res)
-    nodes = sum(r[1]["node_visits"] for r in res)
-    tris = sum(r[1]["tri_tests"] for r in res)
-    trace_ms = sum(r[1]["trace_ms"] for r in res)
-    primary = sum(r[1]["primary_segments"] for r in res)
+    ms = sum(e[1].elapsed_time(e[2]) for e in evs)
+    ms_e2e = sum(e[0].elapsed_time(e[3]) for e in evs)
+    segs = sum(r["segments"] for r in res)
+    draws = sum(r["draws"] for r in res)
+    nodes = sum(r["node_visits"] for r in res)
+    tris = sum(r["tri_tests"] for r in res)
+    trace_ms = sum(r["trace_ms"] for r in res)
+    primary = sum(r["primary_segments"] for r in res)
     ms_all, segs_all = combine_ranks(ms, segs, world, dev)
+    ms_e2e_all, _ = combine_ranks(ms_e2e, segs, world, dev)
+    P_all = sum(sc.H * sc.W for sc, _, _ in job)
     value = segs_all / (ms_all / 1e3) / 1e6
+    # the results of the job: one gather of every object's surface to rank 0 (outside the timed region)
+    sizes = [sc.H * sc.W for sc, _, _ in job]
+    local_depth = {g: o.numpy() for g, o in zip(mine, outs)}
+    gathered = gather_objects(local_depth, sizes, parts, world, rank, dev)
     # the same step with the iteration replayed as a CUDA graph
     tuning = batch.tuning()
     batch.close()
-    batch = irtps.Batch(ctxs, use_graph=True)
-    batch.set_stream(stream.cuda_stream)
+    batch = make_batch(True)
     batch.set_tuning(*tuning)
-    batched()
-    graph_ms = timed(batched, 1)[0][0]
+    set_all(imgs, 1)
+    batch.iterate(n_iter, spp, bnc, seed)
+    graph_ms = timed(lambda: (set_all(imgs, 1), batch.iterate(n_iter, spp, bnc, seed)), 1)[0][0]
     # the same job as per-object launches of the plain form (one context after another)
     per_object()
     po = timed(per_object, max(1, min(2, args.steps)))
     po_ms = sum(r[0] for r in po)
     po_value = sum(r[1] for r in po) / (po_ms / 1e3) / 1e6
-
-    e2e = None
-    if not args.no_e2e:
-        host = []
-        for a in imgs:
-            h = torch.empty(a.shape, dtype=a.dtype, pin_memory=True)
-            h.copy_(a.cpu())
-            host.append(h)
-        outs = [torch.empty((sc.H, sc.W), pin_memory=True) for sc, _, _ in objs]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        set_all(host)
-        batch.iterate(n_iter, spp, bnc, seed)
-        segs_e2e = batch.stats()["segments"]
-        for c, o in zip(ctxs, outs):
-            irtps._check(c.h, irtps._lib.irtps_get_depth(c.h, irtps._addr(o.data_ptr()), 0))
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        e2e = {"value": segs_e2e / dt / 1e6, "unit": "Mrays/s",
-               "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in host),
-               "d2h_bytes_per_step": sum(o.numel() * 4 for o in outs), "steps": 1}
+    e2e = {"value": segs_all / (ms_e2e_all / 1e3) / 1e6, "unit": "Mrays/s",
+           "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in host),
+           "d2h_bytes_per_step": sum(o.numel() * 4 for o in outs), "steps": args.steps,
+           "ms_per_step": ms_e2e_all / args.steps,
+           "how": "CUDA events around irtps_batch_set_images (pinned host images; iteration 0), "
+                  "irtps_batch_iterate and every object's depth read back, every timed step"}
     clocks = clk.summary()
     mhz = clocks["sm_max_mhz"] or sm_max_mhz()
     ops = OPS_PER_DRAW * draws + OPS_PER_NODE * nodes + OPS_PER_TRI * tris
     achieved = ops / (trace_ms / 1e3) / 1e12
-    peak = SM_COUNT * LANES_PER_SM * mhz * 1e6 / 1e12
+    peak = sm_count(dev) * LANES_PER_SM * mhz * 1e6 / 1e12
     bps, cut = tuning
     line = {"metric": "IRT-PS Mrays/s", "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "objects": len(objs), "pixels": P,
-                       "sides": [sc.H for sc, _, _ in objs], "K": [sc.K for sc, _, _ in objs], "spp": spp,
-                       "bounces": bnc, "images": args.images, "sampling": args.sampling,
-                       "irt_iterations_per_step": n_iter,
-                       "trace_blocks_per_sm": bps, "mip_cut": cut, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (images of all objects)"},
-            "pixel_iters_per_s": P * n_iter * world * args.steps / (ms_all / 1e3),
-            "primary_mrays_per_s": primary * world / (ms_all / 1e3) / 1e6,
-            "per_object_launches": {"value": po_value, "unit": "Mrays/s", "ms_per_step": po_ms / len(po)},
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "objects": len(job), "pixels": P_all,
+                       "sides": [sc.H for sc, _, _ in job], "K": [sc.K for sc, _, _ in job],
+                       "spp": [o[1] for o in job], "bounces": [o[2] for o in job], "images": args.images,
+                       "sampling": args.sampling, "irt_iterations_per_step": n_iter,
+                       "trace_blocks_per_sm": bps, "mip_cut": cut,
+                       "parallelism": f"objects split over {world} rank(s) by cost" if world > 1 else "one batch",
+                       "rank_objects": [len(p) for p in parts],
+                       "l2": "inputs larger than L2 (images of all objects, copied in every step)"},
+            "pixel_iters_per_s": P_all * n_iter * args.steps / (ms_all / 1e3),
+            "primary_mrays_per_s": combine_ranks(0.0, primary, world, dev)[1] / (ms_all / 1e3) / 1e6,
+            "per_object_launches": {"value": po_value, "unit": "Mrays/s", "ms_per_step": po_ms / len(po),
+                                    "rank": 0 if world > 1 else None},
             "graph_ms_per_step": graph_ms,
-            "speedup_vs_per_object": value / po_value,
+            "speedup_vs_per_object": (segs / (ms / 1e3) / 1e6) / po_value,
             "stage_ms_per_step": {"trace": trace_ms / args.steps,
-                                  "ps": sum(r[1]["ps_ms"] for r in res) / args.steps,
-                                  "depth": sum(r[1]["depth_ms"] for r in res) / args.steps},
+                                  "ps": sum(r["ps_ms"] for r in res) / args.steps,
+                                  "depth": sum(r["depth_ms"] for r in res) / args.steps,
+                                  "iteration0_ps": sum(r["set_ps_ms"] for r in res) / args.steps,
+                                  "iteration0_depth": sum(r["set_depth_ms"] for r in res) / args.steps},
             "gpu_launches": launches, "clocks": clocks,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_trace (batched)",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_trace_pool (batched)",
                          "launch_ms": trace_ms / (args.steps * n_iter)},
             "e2e": e2e}
+    if rank == 0:
+        line["gathered_objects"] = len(gathered)
     if rank == 0 and not args.no_cpu_baseline:
-        sc0, s0, b0 = objs[0]
+        sc0, s0, b0 = job[0]
         line["cpu_baseline"] = cpu_baseline(sc0, s0, b0, shared=args.sampling == "shared")
     batch.close()
     for c in ctxs:
@@ -451,17 +549,71 @@ def run_batch(args):
     return 0
 
 
+def sm_count(dev):
+    import torch
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
+def accuracy(oracle, ctx, sc, A_host, spp, bounces, seed, t, n_samples=256, rng_seed=11):
+    """Stage-wise errors of one IRT iteration against the FP64 oracle, given the GPU's own
+    iteration-t state (outside the timed region).  The GPU runs iteration t; on a sample of
+    pixels the oracle traces the same paths over the GPU's surface (Lbar), solves the normals
+    from the same (FP16) images with its own Lbar and with the GPU's, and integrates the GPU's
+    normals over the whole grid."""
+    import torch
+    K, C, H, W = sc.K, sc.C, sc.H, sc.W
+    d_t, n_t, a_t = ctx.depth(), ctx.normals(), ctx.albedo()
+    ctx.iterate(1, spp, bounces, seed)
+    n_1, d_1, a_1, v_1 = ctx.normals(), ctx.depth(), ctx.albedo(), ctx.valid()
+    rng = np.random.default_rng(rng_seed)
+    pix = np.sort(rng.choice(H * W, n_samples, replace=False)).astype(np.int32)
+    lb = torch.empty((K, C, H, W), dtype=torch.float32, device="cuda")
+    ctx.indirect(out=lb)
+    torch.cuda.synchronize()
+    lb_gpu = lb.reshape(K, C, -1)[:, :, torch.as_tensor(pix, device="cuda").long()].cpu().numpy()
+    del lb
+    t0 = time.perf_counter()
+    lb_or, _, _ = oracle.trace(d_t, n_t[..., :3], a_t, sc.lights, sc.env, spp, bounces, seed, t, pixels=pix)
+    trace_s = time.perf_counter() - t0
+    img = A_host.reshape(K, C, -1)[:, :, pix].float().numpy()[..., None]   # (K, C, n, 1)
+    rho_t = a_t.reshape(C, -1)[:, pix]
+    n_or, rho_or, ok_or = oracle.ps_step(img, rho_t, lb_or, sc.lights)
+    n_st, rho_st, ok_st = oracle.ps_step(img, rho_t, lb_gpu.astype(np.float64), sc.lights)
+    got_n = n_1.reshape(-1, 4)[pix, :3]
+    got_rho = a_1.reshape(C, -1)[:, pix]
+    err = oracle.angular_error_deg(got_n, n_or)
+    err_st = oracle.angular_error_deg(got_n, n_st)
+    want_d = oracle.poisson_solve(n_1[..., :3].astype(np.float64), 1.0 / W)
+    rel = np.abs(lb_gpu - lb_or) / np.maximum(np.abs(lb_or), 1e-30)
+    return {"iteration": t, "pixels": int(n_samples),
+            "normal_mean_deg": float(err.mean()), "normal_max_deg": float(err.max()),
+            "albedo_mean_abs": float(np.abs(got_rho - rho_or).mean()),
+            "albedo_max_abs": float(np.abs(got_rho - rho_or).max()),
+            "depth_max_rel_range": float(np.abs(d_1 - want_d).max() / np.ptp(want_d)),
+            "lbar_max_rel": float(rel[np.abs(lb_or) > 1e-6].max()),
+            "ps_stage_normal_max_deg": float(err_st.max()),
+            "ps_stage_masks_equal": bool(np.array_equal(ok_st, v_1.reshape(-1)[pix].astype(bool))),
+            "oracle_trace_s": trace_s,
+            "how": "the GPU's iteration-t state (depth, normals, albedo) in; the oracle traces the "
+                   "sampled pixels with the same Philox stream, subtracts and solves from the same "
+                   "images (normal_*: its own Lbar; ps_stage_*: the GPU's Lbar), and solves the depth "
+                   "of the GPU's normals exactly over the whole grid"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bumps_512", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="bumps_2048", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--images", default="f32", choices=["f32", "f16"],
-                    help="storage type of the input images (f16: the mixed-precision pattern)")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="batch workloads: leave out the end-to-end run (single objects time it in every step)")
+    ap.add_argument("--images", default=None, choices=["f32", "f16"],
+                    help="storage type of the input images (default: the workload's; f16 is the "
+                         "mixed-precision pattern)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default trace grid and pyramid depth (profiler captures)")
     ap.add_argument("--evaluate", action="store_true",
@@ -472,6 +624,8 @@ def main():
     ap.add_argument("--early-escape", type=int, choices=[0, 1], default=None,
                     help="horizon bounds before each trace (default: the library's option default)")
     args = ap.parse_args()
+    if args.images is None:
+        args.images = WORKLOAD_IMAGES.get(args.workload, "f32")
     if args.impl == "reference":
         return run_reference(args)
     if WORKLOADS[args.workload][0] == "batch_objects":
@@ -506,41 +660,63 @@ def main():
     ctx.set_state(sc.depth, sc.normals, sc.albedo)
     ctx.render(rspp, rb, 1000 + rank, 0.002, out=A0)
     torch.cuda.synchronize()
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
-
     img_dtype = irtps.IRTPS_F16 if args.images == "f16" else irtps.IRTPS_F32
     A0_in = A0.half() if args.images == "f16" else A0
-
-    def job():
-        ctx.set_images(A0_in, dtype=img_dtype, on_device=True)
-        ctx.iterate(n_iter, spp, bounces, seed)
-        return ctx.stats()
+    del A0
+    # the step's inputs and outputs in pinned host memory (the end-to-end path copies them every step)
+    A_host = torch.empty((K, C, H, W), dtype=A0_in.dtype, pin_memory=True)
+    A_host.copy_(A0_in.cpu())
+    outs = {"depth": torch.empty((H, W), pin_memory=True), "normals": torch.empty((H, W, 4), pin_memory=True),
+            "albedo": torch.empty((C, H, W), pin_memory=True)}
+    in_bytes = A_host.numel() * A_host.element_size()
+    big = in_bytes > 256 * 1024 * 1024
+    # below twice the L2 size a 512 MB write flushes L2 between timed steps
+    flush = None if big else torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    lib = irtps._lib
 
     # the tuner picks the trace grid and pyramid depth (no result bit depends on them)
     if not args.no_autotune and not args.workload.endswith("_profile"):  # profile cases keep the defaults
         ctx.set_images(A0_in, dtype=img_dtype, on_device=True)
-        # probes with a sixteenth of the samples (a quarter when light-shared, whose work items are
-        # sample chunks of at least 16: fewer samples would change the items the grid shares)
-        ctx.autotune(max(1, spp // (4 if args.sampling == "shared" else 16)), bounces, seed)
+        # probes with a fraction of the samples (at most a quarter when light-shared, whose work items
+        # are sample chunks of at least 16: fewer samples would change the items the grid shares)
+        div = 4 if args.sampling == "shared" else WORKLOAD_TUNE_DIV.get(args.workload, 16)
+        ctx.autotune(max(1, spp // div), bounces, seed)
     tuning = ctx.tuning()
 
+    def step(ev=None):
+        """One user step through the C ABI; ev = four events (start, iteration start / end, end)."""
+        if ev:
+            ev[0].record(stream)
+        irtps._check(ctx.h, lib.irtps_set_images(ctx.h, irtps._addr(A_host.data_ptr()), img_dtype, 0))
+        if ev:
+            ev[1].record(stream)
+        irtps._check(ctx.h, lib.irtps_iterate(ctx.h, n_iter, spp, bounces, seed, None))
+        if ev:
+            ev[2].record(stream)
+        st = ctx.stats()
+        irtps._check(ctx.h, lib.irtps_get_depth(ctx.h, irtps._addr(outs["depth"].data_ptr()), 0))
+        irtps._check(ctx.h, lib.irtps_get_normals(ctx.h, irtps._addr(outs["normals"].data_ptr()), 0))
+        irtps._check(ctx.h, lib.irtps_get_albedo(ctx.h, irtps._addr(outs["albedo"].data_ptr()), 0))
+        if ev:
+            ev[3].record(stream)
+        return st
+
     for _ in range(args.warmup):
-        job()
+        step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     launches0 = ctx.stats()["launches"]
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     tot = dict(segments=0, primary=0, draws=0, nodes=0, tris=0, trace_ms=0.0, ps_ms=0.0, depth_ms=0.0,
-               fill_ms=0.0, cg_iters=0)
+               fill_ms=0.0, cg_iters=0, launches=0)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         for i in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            ev[i][0].record(stream)
-            st = job()
-            ev[i][1].record(stream)
+            if flush is not None:
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+            st = step(evs[i])
             tot["segments"] += st["segments"]
             tot["primary"] += st["primary_segments"]
             tot["draws"] += st["draws"]
@@ -555,50 +731,32 @@ def main():
         if world > 1:
             torch.distributed.barrier()
     launches = ctx.stats()["launches"] - launches0
-    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms = sum(e[1].elapsed_time(e[2]) for e in evs)
+    ms_e2e = sum(e[0].elapsed_time(e[3]) for e in evs)
     ms_all, segs_all = combine_ranks(ms, tot["segments"], world, dev)
+    ms_e2e_all, _ = combine_ranks(ms_e2e, tot["segments"], world, dev)
     value = segs_all / (ms_all / 1e3) / 1e6
     P = H * W
-
-    # end to end through the C ABI: pinned host images in, results back to pinned host memory
-    e2e = None
-    if not args.no_e2e:
-        A0_host = torch.empty((K, C, H, W), dtype=A0_in.dtype, pin_memory=True)
-        A0_host.copy_(A0_in.cpu())
-        outs = {"depth": torch.empty((H, W), pin_memory=True), "normals": torch.empty((H, W, 4), pin_memory=True),
-                "albedo": torch.empty((C, H, W), pin_memory=True)}
-        lib = irtps._lib
-        steps_e2e = max(1, min(args.steps, 3))
-        segs_e2e = 0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(steps_e2e):
-            irtps._check(ctx.h, lib.irtps_set_images(ctx.h, irtps._addr(A0_host.data_ptr()), img_dtype, 0))
-            irtps._check(ctx.h, lib.irtps_iterate(ctx.h, n_iter, spp, bounces, seed, None))
-            segs_e2e += ctx.stats()["segments"]
-            irtps._check(ctx.h, lib.irtps_get_depth(ctx.h, irtps._addr(outs["depth"].data_ptr()), 0))
-            irtps._check(ctx.h, lib.irtps_get_normals(ctx.h, irtps._addr(outs["normals"].data_ptr()), 0))
-            irtps._check(ctx.h, lib.irtps_get_albedo(ctx.h, irtps._addr(outs["albedo"].data_ptr()), 0))
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        e2e = {"value": segs_e2e / dt / 1e6, "unit": "Mrays/s",
-               "h2d_bytes_per_step": A0_host.numel() * A0_host.element_size(),
-               "d2h_bytes_per_step": sum(t.numel() * 4 for t in outs.values()), "steps": steps_e2e}
+    e2e = {"value": segs_all / (ms_e2e_all / 1e3) / 1e6, "unit": "Mrays/s", "h2d_bytes_per_step": in_bytes,
+           "d2h_bytes_per_step": sum(t.numel() * 4 for t in outs.values()), "steps": args.steps,
+           "ms_per_step": ms_e2e_all / args.steps,
+           "how": "CUDA events around irtps_set_images (pinned host images; runs iteration 0), "
+                  "irtps_iterate and the depth / normals / albedo read-back, every timed step"}
 
     # roofline of the dominant kernel (the trace): algorithmic lane-ops / its event-timed duration
     clocks = clk.summary()
     mhz = clocks["sm_max_mhz"] or sm_max_mhz()
+    sms = sm_count(dev)
     ops = OPS_PER_DRAW * tot["draws"] + OPS_PER_NODE * tot["nodes"] + OPS_PER_TRI * tot["tris"]
     trace_launches = args.steps * n_iter
     achieved = ops / (tot["trace_ms"] / 1e3) / 1e12
-    peak = SM_COUNT * LANES_PER_SM * mhz * 1e6 / 1e12
+    peak = sms * LANES_PER_SM * mhz * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": (TRACE_DRAM_BYTES if args.sampling == "per_light" else
-                            TRACE_DRAM_BYTES_SHARED).get(args.workload),
+                "traffic": TRACE_DRAM_BYTES.get((args.workload, args.sampling)),
                 "kernel": "k_trace",
                 "launch_ms": tot["trace_ms"] / trace_launches,
-                "note": "lane-operation issue peak = 152 SMs x 128 lanes x max SM clock; ops counted per "
-                        "sampled direction, pyramid node visit and triangle test"}
+                "note": f"lane-operation issue peak = {sms} SMs x {LANES_PER_SM} lanes x max SM clock; ops "
+                        "counted per sampled direction, pyramid node visit and triangle test"}
 
     line = {"metric": "IRT-PS Mrays/s", "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
@@ -607,7 +765,8 @@ def main():
                        "sampling": args.sampling, "trace_blocks_per_sm": tuning[0], "mip_cut": tuning[1],
                        "options": dict(WORKLOAD_OPTIONS.get(args.workload, {}), early_escape=opt.early_escape),
                        "bounces": bounces, "irt_iterations_per_step": n_iter, "parallelism": f"replicas{world}",
-                       "l2": "512 MB buffer written between timed steps"},
+                       "l2": ("inputs larger than L2 (the step's images, copied in every step)" if big else
+                              "512 MB buffer written between timed steps")},
             "pixel_iters_per_s": P * n_iter * world * args.steps / (ms_all / 1e3),
             "primary_mrays_per_s": tot["primary"] * world / (ms_all / 1e3) / 1e6,
             "stage_ms_per_step": {"trace": tot["trace_ms"] / args.steps, "ps": tot["ps_ms"] / args.steps,
@@ -617,6 +776,9 @@ def main():
                                  "tri_tests": tot["tris"] / max(1, tot["segments"]),
                                  "draws": tot["draws"] / max(1, tot["segments"])},
             "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e}
+    if rank == 0 and not args.no_accuracy and opt.sampling == 0 and not opt.fill_holes:
+        import oracle
+        line["accuracy"] = accuracy(oracle, ctx, sc, A_host, spp, bounces, seed, n_iter)
     if args.evaluate:
         line["evaluation"] = evaluate(irtps, sc, spp, n_iter, seed, opt, stream, dev, render_spp=max(spp, rspp))
     if rank == 0 and not args.no_cpu_baseline:

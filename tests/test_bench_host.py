@@ -4,7 +4,8 @@
   paper's evaluation measures (height, albedo and normal error), on random estimates.
 * The batched workload follows its recipe: 64 objects, sides log-uniform in 96..1024,
   K in {4, 8, 16, 32}, spp in {64, 128, 256}, bounces in {1, 2}.
-* The workload table is self-consistent (scene factories, option names, traffic entries).
+* The workload table is self-consistent (scene factories, option names, traffic entries,
+  image types and tuner divisors).
 """
 import os
 import sys
@@ -59,5 +60,7 @@ def test_workload_table_is_consistent():
         assert spp is None or (spp >= 1 and bounces in (1, 2, 3)), name
     for name, opts in bench.WORKLOAD_OPTIONS.items():
         assert name in bench.WORKLOADS and set(opts) <= fields, name
-    for table in (bench.TRACE_DRAM_BYTES, bench.TRACE_DRAM_BYTES_SHARED):
+    for (name, sampling), traffic in bench.TRACE_DRAM_BYTES.items():
+        assert name in bench.WORKLOADS and sampling in ("per_light", "shared") and traffic > 0
+    for table in (bench.WORKLOAD_IMAGES, bench.WORKLOAD_TUNE_DIV):
         assert set(table) <= set(bench.WORKLOADS)

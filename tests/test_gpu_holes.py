@@ -19,6 +19,7 @@ import pytest
 
 import scenes
 from conftest import rel_close
+from stagewise import check_iteration, snapshot
 
 pytestmark = pytest.mark.gpu
 
@@ -164,9 +165,12 @@ def test_loop_with_holes_matches_oracle_loop(lib, oracle_mod):
     with lib.Context(sc.H, sc.W, sc.lights, sc.env, opt) as ctx:
         ctx.set_images(A0)
         for t in range(n_iter):
+            before = snapshot(ctx)
             ctx.iterate(1, spp, bounces, seed)
             st = ctx.stats()
             assert st["walk_overflows"] == 0 and st["cg_rel_residual"] <= 1e-9
+            check_iteration(oracle_mod, A0, sc.lights, sc.env, before, snapshot(ctx), ctx.indirect(), spp, bounces,
+                            seed, t, fill_holes=True)
             h = hist[t + 1]
             err = oracle_mod.angular_error_deg(ctx.normals()[..., :3].reshape(-1, 3), h["normals"].reshape(-1, 3))
             dabs = np.abs(ctx.depth() - h["depth"]) / np.ptp(h["depth"])

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import scenes
+from stagewise import check_iteration, snapshot
 
 pytestmark = pytest.mark.gpu
 
@@ -49,8 +50,11 @@ def test_irls_loop_matches_oracle(lib, oracle_mod):
     with lib.Context(sc.H, sc.W, sc.lights, sc.env, opt) as ctx:
         ctx.set_images(A0)
         out = [(ctx.normals(), ctx.depth())]
-        for _ in range(2):
+        for t in range(2):
+            before = snapshot(ctx)
             ctx.iterate(1, 16, 2, 5)
+            check_iteration(oracle_mod, A0, sc.lights, sc.env, before, snapshot(ctx), ctx.indirect(), 16, 2, 5, t,
+                            irls=(0.05, 3))
             out.append((ctx.normals(), ctx.depth()))
     for t, ((n, d), h) in enumerate(zip(out, hist)):
         err = oracle_mod.angular_error_deg(n[..., :3].reshape(-1, 3), h["normals"].reshape(-1, 3))

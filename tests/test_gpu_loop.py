@@ -1,16 +1,19 @@
 """End-to-end IRT-PS on the GPU against the oracle loop.
 
 The 64x64 bowl (K=8, 64 spp, 1 bounce, 3 iterations, seed 1) and a ragged RGB
-scene run fully on both sides from the same input images: mean angular normal
-error <= 0.05 degrees and depth within 1e-4 of the depth range, at every
-iteration.  Later iterations trace over slightly different (FP32 vs FP64)
-surfaces, so rare segments and row masks may decide differently: from iteration
-1 on the depth bar applies to the mean error (max within 1e-3 of the range).
+scene.  Every iteration is checked stage by stage from the GPU's own state before
+it (stagewise.check_iteration: trace, subtract + PS with bit-exact row masks,
+integration with the depth within 1e-4 of its range at every pixel, D_H).  As a
+secondary check both loops also run freely from the same input images: mean
+angular normal error <= 0.05 degrees at every iteration and depth within 1e-4 of
+the range (at iteration 0 at every pixel; later in the mean, since rare row masks
+near tau_lo take different sides under the FP32 and FP64 Lbar).
 """
 import numpy as np
 import pytest
 
 import scenes
+from stagewise import check_iteration, snapshot
 
 pytestmark = pytest.mark.gpu
 
@@ -23,8 +26,13 @@ def _run_both(lib, oracle_mod, sc, A0, n_iter, spp, bounces, seed):
         ctx.set_images(A0)
         out.append((ctx.normals(), ctx.depth(), ctx.albedo(), None))
         for t in range(n_iter):
-            dh = ctx.iterate(1, spp, bounces, seed)
-            out.append((ctx.normals(), ctx.depth(), ctx.albedo(), ctx.stats()))
+            before = snapshot(ctx)
+            ctx.iterate(1, spp, bounces, seed)
+            st = ctx.stats()
+            dh = check_iteration(oracle_mod, A0, sc.lights, sc.env, before, snapshot(ctx), ctx.indirect(), spp,
+                                 bounces, seed, t)
+            assert abs(st["dH_max"] - dh) <= 1e-9 + 1e-6 * dh, (t, st["dH_max"], dh)
+            out.append((ctx.normals(), ctx.depth(), ctx.albedo(), st))
     return hist, out
 
 

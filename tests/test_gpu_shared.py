@@ -10,6 +10,7 @@ import pytest
 
 import scenes
 from conftest import rel_close
+from stagewise import check_iteration, snapshot
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +56,10 @@ def test_shared_loop_matches_oracle(lib, oracle_mod):
     with _ctx(lib, sc) as ctx:
         ctx.set_images(A0)
         for t in range(2):
+            before = snapshot(ctx)
             ctx.iterate(1, 24, 2, 11)
+            check_iteration(oracle_mod, A0, sc.lights, sc.env, before, snapshot(ctx), ctx.indirect(), 24, 2, 11, t,
+                            shared=True)
             n, d = ctx.normals(), ctx.depth()
             h = hist[t + 1]
             err = oracle_mod.angular_error_deg(n[..., :3].reshape(-1, 3), h["normals"].reshape(-1, 3))
