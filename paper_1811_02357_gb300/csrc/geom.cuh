@@ -151,10 +151,9 @@ struct Field {
 };
 
 struct LevelTable {
-  int off[kMaxLevels];
-  int lw[kMaxLevels];
-  float zmax_margin;  // (max height) + 1e-4: above it a rising ray can hit nothing
-  float dz;           // node-skip margin on heights, 1e-5 (1 + |max height|)
+  int2 ol[kMaxLevels];  // per level: offset of its nodes in the pyramid arrays, row width
+  float zmax_margin;    // (max height) + 1e-4: above it a rising ray can hit nothing
+  float dz;             // node-skip margin on heights, 1e-5 (1 + |max height|)
 };
 
 // Height bounds of a surface from its top pyramid node.
@@ -167,10 +166,7 @@ __device__ __forceinline__ void set_height_bounds(const Field &f, LevelTable *t)
 // Copy the level table of f into shared memory and derive the height bounds from
 // the top pyramid node (whole block; ends with a barrier).
 __device__ __forceinline__ void load_levels(const Field &f, LevelTable *t) {
-  if (threadIdx.x < kMaxLevels) {
-    t->off[threadIdx.x] = f.off[threadIdx.x];
-    t->lw[threadIdx.x] = f.lw[threadIdx.x];
-  }
+  if (threadIdx.x < kMaxLevels) t->ol[threadIdx.x] = make_int2(f.off[threadIdx.x], f.lw[threadIdx.x]);
   if (threadIdx.x == 0) set_height_bounds(f, t);
   __syncthreads();
 }
@@ -275,10 +271,16 @@ struct Walker {
   float ix, iy;
   int cx, cy, lv;
   float t_entry;
+  float t_stop;  // the walk ends once a cell's entry lies beyond it: past the best hit (plus a margin),
+                 // or, rising, above every vertex (plus a margin)
   float bt;
   int btri;
-  int flags;  // bit 0: any-hit; bits 1, 2: a second walk in x, in y; bits 3-4: current walk index
+  int flags;  // bit 0: any-hit; bits 1, 2: a second walk in x, in y; bits 3-4: current walk index;
+              // bits 5-6, 7-8: sign of d.x, of d.y, plus one
 };
+
+__device__ __forceinline__ int walker_sx(const Walker &m) { return ((m.flags >> 5) & 3) - 1; }
+__device__ __forceinline__ int walker_sy(const Walker &m) { return ((m.flags >> 7) & 3) - 1; }
 
 // Start cell of walk `wi`: the cell holding the origin, on the side the ray moves
 // toward when the origin is on a grid line, shifted back by one column / row for
@@ -292,18 +294,25 @@ __device__ __forceinline__ void walker_begin_walk(Walker &m, int wi) {
   m.cy = cy - (wi / nx);
   m.lv = 0;
   m.t_entry = 0.0f;
-  m.flags = (m.flags & 7) | (wi << 3);
+  m.flags = (m.flags & ~(3 << 3)) | (wi << 3);
 }
 
-__device__ __forceinline__ void walker_init(Walker &m, F3 o, F3 d, bool any) {
+// zmax_margin: the surface's maximum height plus its margin (LevelTable::zmax_margin).
+__device__ __forceinline__ void walker_init(Walker &m, F3 o, F3 d, bool any, float zmax_margin) {
   m.o = o;
   m.d = d;
   m.ix = __frcp_rn(d.x);
   m.iy = __frcp_rn(d.y);
   const bool on_x = floorf(o.x) == o.x, on_y = floorf(o.y) == o.y;
-  m.flags = (any ? 1 : 0) | ((on_x && d.x == 0.0f) ? 2 : 0) | ((on_y && d.y == 0.0f) ? 4 : 0);
+  const int sx = d.x > 0.0f ? 1 : (d.x < 0.0f ? -1 : 0);
+  const int sy = d.y > 0.0f ? 1 : (d.y < 0.0f ? -1 : 0);
+  m.flags = (any ? 1 : 0) | ((on_x && d.x == 0.0f) ? 2 : 0) | ((on_y && d.y == 0.0f) ? 4 : 0) | ((sx + 1) << 5) |
+            ((sy + 1) << 7);
   m.bt = __int_as_float(0x7f800000);
   m.btri = -1;
+  // a rising ray is above every vertex (by the margin) beyond this parameter; any rounding of it
+  // only moves the end of the walk within the margin, where no triangle can be hit
+  m.t_stop = d.z > 0.0f ? (zmax_margin - o.z) / d.z : __int_as_float(0x7f800000);
   walker_begin_walk(m, 0);
 }
 
@@ -318,7 +327,7 @@ __device__ __forceinline__ void walker_init(Walker &m, F3 o, F3 d, bool any) {
 // or moves to the next walk of a grid-line ray).  Returns true when the march is over.
 __device__ __forceinline__ bool walker_finish_walk(Walker &m) {
   if ((m.flags & 1) && m.btri >= 0) return true;
-  const int wi = (m.flags >> 3) + 1;
+  const int wi = ((m.flags >> 3) & 3) + 1;
   const int walks = ((m.flags & 2) ? 2 : 1) * ((m.flags & 4) ? 2 : 1);
   if (wi < walks) {
     walker_begin_walk(m, wi);
@@ -327,10 +336,8 @@ __device__ __forceinline__ bool walker_finish_walk(Walker &m) {
   return true;
 }
 
-__device__ __forceinline__ bool walker_walk_over(const Walker &m, const Field &f, const LevelTable &lt) {
-  return (unsigned)m.cx >= (unsigned)f.Wc || (unsigned)m.cy >= (unsigned)f.Hc ||
-         (m.btri >= 0 && m.t_entry > radd(m.bt, kHitMargin)) ||
-         (m.d.z > 0.0f && radd(m.o.z, rmul(m.t_entry, m.d.z)) > lt.zmax_margin);
+__device__ __forceinline__ bool walker_walk_over(const Walker &m, const Field &f) {
+  return (unsigned)m.cx >= (unsigned)f.Wc || (unsigned)m.cy >= (unsigned)f.Hc || m.t_entry > m.t_stop;
 }
 
 // Node step.  Returns true when the march is over; sets at_leaf when the walker
@@ -338,14 +345,14 @@ __device__ __forceinline__ bool walker_walk_over(const Walker &m, const Field &f
 __device__ __forceinline__ bool walker_node_step(Walker &m, const Field &f, const LevelTable &lt, Work &w,
                                                  bool &at_leaf) {
   const float inf = __int_as_float(0x7f800000);
-  if (walker_walk_over(m, f, lt)) return walker_finish_walk(m);
-  const int sx = m.d.x > 0.0f ? 1 : (m.d.x < 0.0f ? -1 : 0);
-  const int sy = m.d.y > 0.0f ? 1 : (m.d.y < 0.0f ? -1 : 0);
+  if (walker_walk_over(m, f)) return walker_finish_walk(m);
+  const int sx = walker_sx(m), sy = walker_sy(m);
   const int lv = m.lv;
   const int nx = m.cx >> lv, ny = m.cy >> lv;
   const int X0 = nx << lv, Y0 = ny << lv;
   const int X1 = min(X0 + (1 << lv), f.Wc), Y1 = min(Y0 + (1 << lv), f.Hc);
-  const float nmax = __ldg(f.pmax + lt.off[lv] + ny * lt.lw[lv] + nx);
+  const int2 ol = lt.ol[lv];
+  const float nmax = __ldg(f.pmax + ol.x + ny * ol.y + nx);
   ++w.nodes;
   const float tX = sx != 0 ? rmul(rsub((float)(sx > 0 ? X1 : X0), m.o.x), m.ix) : inf;
   const float tY = sy != 0 ? rmul(rsub((float)(sy > 0 ? Y1 : Y0), m.o.y), m.iy) : inf;
@@ -381,8 +388,7 @@ __device__ __forceinline__ bool walker_node_step(Walker &m, const Field &f, cons
 // Returns true when the march is over.
 __device__ __forceinline__ bool walker_leaf_step(Walker &m, const Field &f, Work &w) {
   const float inf = __int_as_float(0x7f800000);
-  const int sx = m.d.x > 0.0f ? 1 : (m.d.x < 0.0f ? -1 : 0);
-  const int sy = m.d.y > 0.0f ? 1 : (m.d.y < 0.0f ? -1 : 0);
+  const int sx = walker_sx(m), sy = walker_sy(m);
   test_cell(f, m.cy, m.cx, m.o, m.d, m.bt, m.btri, w);
   const float tx =
       sx > 0 ? rmul(rsub((float)(m.cx + 1), m.o.x), m.ix) : (sx < 0 ? rmul(rsub((float)m.cx, m.o.x), m.ix) : inf);
@@ -392,7 +398,10 @@ __device__ __forceinline__ bool walker_leaf_step(Walker &m, const Field &f, Work
     if (m.cx + sx >= 0 && m.cx + sx < f.Wc) test_cell(f, m.cy, m.cx + sx, m.o, m.d, m.bt, m.btri, w);
     if (m.cy + sy >= 0 && m.cy + sy < f.Hc) test_cell(f, m.cy + sy, m.cx, m.o, m.d, m.bt, m.btri, w);
   }
-  if ((m.flags & 1) && m.btri >= 0) return true;
+  if (m.btri >= 0) {
+    if (m.flags & 1) return true;
+    m.t_stop = fminf(m.t_stop, radd(m.bt, kHitMargin));  // later cells may only hold closer hits
+  }
   if (tx == inf && ty == inf) return walker_finish_walk(m);
   if (tx < ty) {
     m.cx += sx;
@@ -419,7 +428,7 @@ __device__ __forceinline__ bool walker_step(Walker &m, const Field &f, const Lev
 __device__ __forceinline__ bool march(const Field &f, const LevelTable &lt, F3 o, F3 d, bool any, float &t, int &tri,
                                      int &budget, Work &w) {
   Walker m;
-  walker_init(m, o, d, any);
+  walker_init(m, o, d, any, lt.zmax_margin);
   while (!walker_step(m, f, lt, w)) {
     if (--budget < 0) break;
   }

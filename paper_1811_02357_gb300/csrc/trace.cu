@@ -368,8 +368,7 @@ __global__ void __launch_bounds__(kTraceThreads,
   if constexpr (BATCH) {
     for (int i = threadIdx.x; i < n_obj * kMaxLevels; i += blockDim.x) {
       const int o = i / kMaxLevels, l = i - o * kMaxLevels;
-      lts[o].off[l] = a.objs[o].f.off[l];
-      lts[o].lw[l] = a.objs[o].f.lw[l];
+      lts[o].ol[l] = make_int2(a.objs[o].f.off[l], a.objs[o].f.lw[l]);
     }
     for (int o = threadIdx.x; o < n_obj; o += blockDim.x) {
       set_height_bounds(a.objs[o].f, lts + o);
@@ -502,7 +501,7 @@ __global__ void __launch_bounds__(kTraceThreads,
       if (f3dot(nq, l) > 0.0f) {
         cosv = fmaxf(0.0f, nq.x * l.x + nq.y * l.y + nq.z * l.z);
         if (ob->shadow) {
-          walker_init(m, m.o, F3{rmul(l.x, ob->Wf), rmul(l.y, ob->Wf), l.z}, true);
+          walker_init(m, m.o, F3{rmul(l.x, ob->Wf), rmul(l.y, ob->Wf), l.z}, true, lt->zmax_margin);
           shadow = true;
           ++segs;
           budget = budget0();
@@ -574,7 +573,7 @@ __global__ void __launch_bounds__(kTraceThreads,
       const float4 n4 = __ldg(ob->nrm + (b == 1 ? p : qp));
       const F3 dw = cosine_dir(F3{n4.x, n4.y, n4.z}, x.x, x.y);
       const F3 dg = {rmul(dw.x, ob->Wf), rmul(dw.y, ob->Wf), dw.z};
-      walker_init(m, org, dg, false);
+      walker_init(m, org, dg, false, lt->zmax_margin);
       shadow = false;
       ++segs;
       ++w.draws;
@@ -673,7 +672,7 @@ __global__ void __launch_bounds__(kTraceThreads,
           if (f3dot(nq, l) > 0.0f) {
             cosv = fmaxf(0.0f, nq.x * l.x + nq.y * l.y + nq.z * l.z);
             if (ob->shadow) {
-              walker_init(m, o2, F3{rmul(l.x, ob->Wf), rmul(l.y, ob->Wf), l.z}, true);
+              walker_init(m, o2, F3{rmul(l.x, ob->Wf), rmul(l.y, ob->Wf), l.z}, true, lt->zmax_margin);
               shadow = true;
               ++segs;
               phase = PH_MARCH;
