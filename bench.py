@@ -490,11 +490,39 @@ def run_batch(args):
     set_all(imgs, 1)
     batch.iterate(n_iter, spp, bnc, seed)
     graph_ms = timed(lambda: (set_all(imgs, 1), batch.iterate(n_iter, spp, bnc, seed)), 1)[0][0]
-    # the same job as per-object launches of the plain form (one context after another)
+    # the same job as per-object launches with the batch's options (one context after another)
     per_object()
     po = timed(per_object, max(1, min(2, args.steps)))
     po_ms = sum(r[0] for r in po)
     po_value = sum(r[1] for r in po) / (po_ms / 1e3) / 1e6
+    # the plain form: per-object contexts, FP32 images, per-light sampling (the form the
+    # mixed-precision batch is compared with); timed when the batch's options differ from it
+    plain = None
+    if args.images != "f32" or args.sampling != "per_light":
+        popt = irtps.irtps_default_options()
+        if args.early_escape is not None:
+            popt.early_escape = args.early_escape
+        pctx = []
+        for g, (sc, _, _) in zip(mine, objs):
+            c = irtps.Context(sc.H, sc.W, sc.lights, sc.env, popt)
+            c.set_stream(stream.cuda_stream)
+            c.set_object(g)
+            pctx.append(c)
+        imgs32 = [a.float() if a.dtype != torch.float32 else a for a in imgs]
+
+        def plain_step():
+            for c, a, s_, b_ in zip(pctx, imgs32, spp, bnc):
+                c.set_images(a, dtype=irtps.IRTPS_F32, on_device=True)
+                c.iterate(n_iter, s_, b_, seed)
+            return 0
+        plain_step()
+        pl_ms = timed(plain_step, 1)[0][0]
+        plain = {"pixel_iters_per_s": P * n_iter / (pl_ms / 1e3), "ms_per_step": pl_ms,
+                 "what": "the same objects as per-object contexts of the plain form: FP32 images, per-light "
+                         "sampling, default options"}
+        for c in pctx:
+            c.close()
+        del imgs32
     e2e = {"value": segs_all / (ms_e2e_all / 1e3) / 1e6, "unit": "Mrays/s",
            "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in host),
            "d2h_bytes_per_step": sum(o.numel() * 4 for o in outs), "steps": args.steps,
@@ -522,6 +550,9 @@ def run_batch(args):
             "primary_mrays_per_s": combine_ranks(0.0, primary, world, dev)[1] / (ms_all / 1e3) / 1e6,
             "per_object_launches": {"value": po_value, "unit": "Mrays/s", "ms_per_step": po_ms / len(po),
                                     "rank": 0 if world > 1 else None},
+            "plain_fp32_per_object": plain,
+            "speedup_vs_plain_fp32_per_object": (None if plain is None else
+                                                 (P * n_iter * args.steps / (ms / 1e3)) / plain["pixel_iters_per_s"]),
             "graph_ms_per_step": graph_ms,
             "speedup_vs_per_object": (segs / (ms / 1e3) / 1e6) / po_value,
             "stage_ms_per_step": {"trace": trace_ms / args.steps,
@@ -531,11 +562,15 @@ def run_batch(args):
                                   "iteration0_depth": sum(r["set_depth_ms"] for r in res) / args.steps},
             "gpu_launches": launches, "clocks": clocks,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_trace_pool (batched)",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_trace (batched)",
                          "launch_ms": trace_ms / (args.steps * n_iter)},
             "e2e": e2e}
     if rank == 0:
         line["gathered_objects"] = len(gathered)
+    if rank == 0 and not args.no_accuracy:
+        # every context has run set_images and n_iter iterations (the per-object runs were last)
+        line["accuracy"] = batch_accuracy(irtps, batch, ctxs, mine, objs, host, spp, bnc, seed,
+                                          args.sampling == "shared", n_iter)
     if rank == 0 and not args.no_cpu_baseline:
         sc0, s0, b0 = job[0]
         line["cpu_baseline"] = cpu_baseline(sc0, s0, b0, shared=args.sampling == "shared")
@@ -547,6 +582,45 @@ def run_batch(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def batch_accuracy(irtps, batch, ctxs, mine, objs, host, spp, bnc, seed, shared, t, n_check=4, n_samples=64):
+    """Stage-wise errors of one batched iteration (iteration index t of every object) against the FP64
+    oracle for a few of the batch's objects (the largest, the smallest and two between), from each
+    object's own GPU state: the oracle
+    traces sampled pixels with the object's Philox key and iteration index, solves their normals from
+    the same images, and integrates the object's GPU normals exactly (outside the timed region)."""
+    import oracle
+    order = sorted(range(len(objs)), key=lambda i: objs[i][0].H * objs[i][0].W)
+    pick = sorted({order[0], order[-1], order[len(order) // 3], order[2 * len(order) // 3]})[:n_check]
+    before = {i: (ctxs[i].depth(), ctxs[i].normals(), ctxs[i].albedo()) for i in pick}
+    batch.iterate(1, spp, bnc, seed)
+    rng = np.random.default_rng(13)
+    errs, derr, lrel = [], [], []
+    for i in pick:
+        sc = objs[i][0]
+        c = ctxs[i]
+        K, C, H, W = sc.K, sc.C, sc.H, sc.W
+        d_t, n_t, a_t = before[i]
+        n_1, d_1 = c.normals(), c.depth()
+        lb = c.indirect().reshape(K, C, -1)
+        pix = np.sort(rng.choice(H * W, min(n_samples, H * W), replace=False)).astype(np.int32)
+        lb_or, _, _ = oracle.trace(d_t, n_t[..., :3], a_t, sc.lights, sc.env, spp[i], bnc[i], seed, t,
+                                   pixels=pix, obj=mine[i], shared=shared)
+        img = host[i].reshape(K, C, -1)[:, :, pix].float().numpy()[..., None]
+        n_or, _, _ = oracle.ps_step(img, a_t.reshape(C, -1)[:, pix], lb_or, sc.lights)
+        errs.append(oracle.angular_error_deg(n_1.reshape(-1, 4)[pix, :3], n_or))
+        want_d = oracle.poisson_solve(n_1[..., :3].astype(np.float64), 1.0 / W)
+        derr.append(float(np.abs(d_1 - want_d).max() / np.ptp(want_d)))
+        got = lb[:, :, pix]
+        lrel.append(float((np.abs(got - lb_or) / np.maximum(np.abs(lb_or), 1e-30))[np.abs(lb_or) > 1e-6].max()))
+    e = np.concatenate(errs)
+    return {"objects": [int(mine[i]) for i in pick], "pixels_per_object": n_samples,
+            "normal_mean_deg": float(e.mean()), "normal_max_deg": float(e.max()),
+            "depth_max_rel_range": max(derr), "lbar_max_rel": max(lrel),
+            "how": "per object: the GPU's state before one batched iteration in; the oracle traces sampled pixels "
+                   "(same Philox key and iteration, same sampling), solves their normals from the same images, "
+                   "and solves the depth of the GPU's normals exactly"}
 
 
 def sm_count(dev):

@@ -100,18 +100,54 @@ __device__ __forceinline__ void ps_store(const PSArgs &a, int p, const float (&G
 }
 
 // A pixel with masked rows: the normal equations (L_v^T L_v) G_c = L_v^T I_v,c over the
-// valid rows.  The matrix, its inverse (by the adjugate) and its 1-norm condition number
-// are computed in FP64 from the lights; fewer than 3 rows, a singular or ill-conditioned
-// system (condition above cond_max): ok = false.  The right-hand side R is the FP32 sum
-// of ps_row, except for systems whose condition number exceeds kRefineCond, where the
-// FP32 rounding of R would be amplified: their R is summed again in FP64 from the
-// pixel's valid rows (read again).
+// valid rows, R = L_v^T I the FP32 sum of ps_row.  A well-conditioned system (FP32
+// condition number at most kRefineCond, the common case) is solved in FP32.  Otherwise
+// the matrix, its inverse (by the adjugate) and its 1-norm condition number are computed
+// in FP64 from the lights; fewer than 3 rows, a singular or ill-conditioned system
+// (condition above cond_max): ok = false; and R, whose FP32 rounding the condition number
+// would amplify, is summed again in FP64 from the pixel's valid rows (read again).
 constexpr double kRefineCond = 16.0;
 
 template <int C, typename TI>
 __device__ __forceinline__ bool ps_masked_solve(const PSArgs &a, int p, const float (&R)[3][C], float (&G)[3][C],
                                                 unsigned long long valid) {
   if (__popcll(valid) < 3) return false;
+  {  // the common case in FP32: a system whose FP32 condition number is at most kRefineCond is
+     // certainly below cond_max in FP64 too (FP32 rounding moves it by far less than the gap),
+     // so its validity is decided as in FP64, and FP32 solves it within the normal tolerance
+    float m00 = 0, m01 = 0, m02 = 0, m11 = 0, m12 = 0, m22 = 0;
+    for (int k = 0; k < a.K; ++k) {
+      if (!((valid >> k) & 1ull)) continue;
+      const float lx = a.light[k][0], ly = a.light[k][1], lz = a.light[k][2];
+      m00 = fmaf(lx, lx, m00);
+      m01 = fmaf(lx, ly, m01);
+      m02 = fmaf(lx, lz, m02);
+      m11 = fmaf(ly, ly, m11);
+      m12 = fmaf(ly, lz, m12);
+      m22 = fmaf(lz, lz, m22);
+    }
+    const float a00 = m11 * m22 - m12 * m12, a01 = m02 * m12 - m01 * m22, a02 = m01 * m12 - m02 * m11;
+    const float a11 = m00 * m22 - m02 * m02, a12 = m01 * m02 - m00 * m12, a22 = m00 * m11 - m01 * m01;
+    const float det = m00 * a00 + m01 * a01 + m02 * a02;
+    const float nm = fmaxf(fabsf(m00) + fabsf(m01) + fabsf(m02),
+                           fmaxf(fabsf(m01) + fabsf(m11) + fabsf(m12), fabsf(m02) + fabsf(m12) + fabsf(m22)));
+    const float na = fmaxf(fabsf(a00) + fabsf(a01) + fabsf(a02),
+                           fmaxf(fabsf(a01) + fabsf(a11) + fabsf(a12), fabsf(a02) + fabsf(a12) + fabsf(a22)));
+    // cond = nm * |M^-1|_1 = nm * na / |det|; the test also keeps det away from zero; with a
+    // cond_max below kRefineCond only systems well inside it take this path
+    const float thr = (float)fmin(kRefineCond, 0.5 * a.cond_max);
+    if (det > 0.0f && isfinite(det) && nm * na <= thr * det) {
+      const float id = 1.0f / det;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const float r0 = R[0][c], r1 = R[1][c], r2 = R[2][c];
+        G[0][c] = (a00 * r0 + a01 * r1 + a02 * r2) * id;
+        G[1][c] = (a01 * r0 + a11 * r1 + a12 * r2) * id;
+        G[2][c] = (a02 * r0 + a12 * r1 + a22 * r2) * id;
+      }
+      return true;
+    }
+  }
   double M00 = 0, M01 = 0, M02 = 0, M11 = 0, M12 = 0, M22 = 0;
   for (int k = 0; k < a.K; ++k) {
     if (!((valid >> k) & 1ull)) continue;
