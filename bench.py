@@ -62,6 +62,9 @@ WORKLOADS = {
     "bowl_64": ("bowl_64", {}, 64, 1, 3, 256, 1),
     # a small case of the same kernels for profiler captures (one IRT iteration per job)
     "bumps_256_profile": ("bumps_512", {"H": 256, "W": 256}, 32, 2, 1, 32, 2),
+    # a small case of the 2048x2048, K = 32 kernels for profiler captures (2 spp: one trace launch
+    # of about a tenth of a second)
+    "bumps_2048_profile": ("bumps_2048", {}, 2, 2, 1, 4, 1),
     # the 2048x2048, K = 32 configuration at an eighth of its samples (64 spp)
     "bumps_2048_spp64": ("bumps_2048", {}, 64, 2, 1, 4, 1),
     # the 4096x4096, K = 64 configuration at a sixty-fourth of its samples (16 spp)
@@ -77,9 +80,9 @@ WORKLOADS = {
 # context options a workload sets beyond the defaults
 WORKLOAD_OPTIONS = {"bumps_512_single": {"fill_holes": 1}}
 # image storage of a workload when --images is not given (the precision configurations keep FP16)
-WORKLOAD_IMAGES = {"bumps_2048": "f16", "bumps_2048_spp64": "f16", "bumps_4096_spp16": "f16"}
+WORKLOAD_IMAGES = {"bumps_2048": "f16", "bumps_2048_spp64": "f16", "bumps_2048_profile": "f16", "bumps_4096_spp16": "f16"}
 # tuner probes take spp / this many samples (a few seconds of probes on the large grids)
-WORKLOAD_TUNE_DIV = {"bumps_2048": 64, "bumps_2048_spp64": 8, "bumps_4096_spp16": 4}
+WORKLOAD_TUNE_DIV = {"bumps_2048": 64, "bumps_2048_spp64": 8, "bumps_2048_profile": 2, "bumps_4096_spp16": 4}
 
 # Algorithmic lane operations per unit of trace work (counted from the formulas:
 # Philox4x32-10 = 10 rounds x (2 mul.hi + 2 mul.lo + 4 xor) + 9 x 2 key adds;

@@ -353,6 +353,22 @@ int irtps_create(irtps_ctx **out, int H, int W, int K, int C, const float *light
       for (int b = 0; b < 3; ++b) v += A[a][b] / det * lights[3 * k + b];
       c.h_pinv[a * K + k] = (float)v;
     }
+  {  // (L^T L)^-1 and its 1-norm condition number: a well-conditioned system lets PS sum
+     // R = L^T I alone and apply the inverse once per pixel (pinv(L) I = (L^T L)^-1 L^T I)
+    double nm = 0.0, ni = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      double rm = 0.0, ri = 0.0;
+      for (int b = 0; b < 3; ++b) {
+        rm += std::fabs(M[a][b]);
+        ri += std::fabs(A[a][b] / det);
+      }
+      nm = std::max(nm, rm);
+      ni = std::max(ni, ri);
+    }
+    const int idx[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int i = 0; i < 6; ++i) c.h_minv[i] = (float)(A[idx[i][0]][idx[i][1]] / det);
+    c.normal_eq = nm * ni <= 16.0 ? 1 : 0;
+  }
   // pyramid geometry
   int w = W - 1, h = H - 1, total = 0, l = 0;
   while (true) {

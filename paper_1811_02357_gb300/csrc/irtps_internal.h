@@ -95,6 +95,8 @@ struct Ctx {
   // host copies
   std::vector<float> h_lights;    // K*3
   std::vector<float> h_pinv;      // 3*K, (L^T L)^-1 L^T rounded to float
+  float h_minv[6] = {0};         // (L^T L)^-1 rounded to float: m00 m01 m02 m11 m12 m22
+  int normal_eq = 0;              // 1: PS of fully valid pixels as (L^T L)^-1 (L^T I) (cond(L^T L) <= 16)
   float *d_lights = nullptr;      // K*3 on the device (read at trace hits)
   float *horizon = nullptr;       // early escape: horizon bounds of every pixel, 8 x H x W (option)
   float *shared_part = nullptr;   // light-shared trace: partial sums of its sample chunks

@@ -3,14 +3,18 @@
 // Per pixel p: I(k, c) = A0(k, c, p) - rho_t(c, p) * Lbar(k, c, p); row k is valid
 // iff tau_lo < mean_c I(k, c) < tau_hi (decided in FP32, each operation rounded
 // on its own).  All rows valid: G_c = pinv(L) I_c with pinv(L) = (L^T L)^-1 L^T
-// (Eq. 4).  Otherwise the FP64 normal equations (L_v^T L_v) G_c = L_v^T I_v,c over
-// the valid rows; fewer than 3 rows or a 1-norm condition number above cond_max
-// marks the pixel invalid.  n = normalize(sum_c G_c), rho_c = |G_c|; invalid
-// pixels get n = (0, 0, 1), rho = 0.
+// (Eq. 4), summed as pinv(L) I, or - when L^T L is well conditioned (1-norm
+// condition number at most 16, decided on the host in FP64) - as (L^T L)^-1 (L^T I),
+// the same product associated the other way, which needs only the one running
+// sum L^T I that masked pixels need anyway.  Otherwise the normal equations
+// (L_v^T L_v) G_c = L_v^T I_v,c over the valid rows; fewer than 3 rows or a 1-norm
+// condition number above cond_max marks the pixel invalid.
+// n = normalize(sum_c G_c), rho_c = |G_c|; invalid pixels get n = (0, 0, 1), rho = 0.
 //
 // The contraction pinv(L) [3 x K] x I [K x C*P] streams K*C values per pixel for
 // 6*K*C flops: far below the tensor-core ridge, so it runs on the FP32 pipes
 // with coalesced [k][c][p] loads and the pixel's state written once.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <cuda_bf16.h>
@@ -32,6 +36,8 @@ struct PSArgs {
   int zero_indirect;    // 1: Lbar taken as 0 (iteration 0, classic PS)
   float pinv[3][kMaxLights];
   float light[kMaxLights][3];
+  float minv[6];        // (L^T L)^-1: m00 m01 m02 m11 m12 m22
+  int normal_eq;        // 1: fully valid pixels as (L^T L)^-1 (L^T I)
   int blk_begin;        // first block of the object in a batched launch
 };
 
@@ -43,10 +49,11 @@ template <>
 __device__ __forceinline__ float load_img<__half>(const __half *p) { return __half2float(__ldg(p)); }
 
 // Row k of pixel p: I(k, c) = A0 - rho_c Lbar (each operation rounded on its own)
-// and its validity (tau_lo < mean_c I < tau_hi), accumulated into G = pinv(L) I
-// over all rows and into R = L_v^T I over the valid rows (the right-hand side of
-// the masked normal equations), both in FP32.
-template <int C>
+// and its validity (tau_lo < mean_c I < tau_hi), accumulated into R = L_v^T I over
+// the valid rows (the right-hand side of the masked normal equations) and, unless
+// the normal-equation form (NE) serves fully valid pixels, into G = pinv(L) I over
+// all rows; both in FP32.
+template <int C, bool NE>
 __device__ __forceinline__ void ps_row(const PSArgs &a, int k, const float *rho, const float *a0, const float *lb,
                                        float (&G)[3][C], float (&R)[3][C], unsigned long long &valid) {
   float I[C];
@@ -61,9 +68,22 @@ __device__ __forceinline__ void ps_row(const PSArgs &a, int k, const float *rho,
     const float l = ok ? a.light[k][r] : 0.0f;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      G[r][c] = fmaf(a.pinv[r][k], I[c], G[r][c]);
+      if (!NE) G[r][c] = fmaf(a.pinv[r][k], I[c], G[r][c]);
       R[r][c] = fmaf(l, I[c], R[r][c]);
     }
+  }
+}
+
+// G = (L^T L)^-1 R for a fully valid pixel in the normal-equation form.
+template <int C>
+__device__ __forceinline__ void ps_apply_minv(const PSArgs &a, const float (&R)[3][C], float (&G)[3][C]) {
+  const float *m = a.minv;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const float r0 = R[0][c], r1 = R[1][c], r2 = R[2][c];
+    G[0][c] = fmaf(m[0], r0, fmaf(m[1], r1, m[2] * r2));
+    G[1][c] = fmaf(m[1], r0, fmaf(m[3], r1, m[4] * r2));
+    G[2][c] = fmaf(m[2], r0, fmaf(m[4], r1, m[5] * r2));
   }
 }
 
@@ -107,11 +127,14 @@ __device__ __forceinline__ void ps_store(const PSArgs &a, int p, const float (&G
 // (condition above cond_max): ok = false; and R, whose FP32 rounding the condition number
 // would amplify, is summed again in FP64 from the pixel's valid rows (read again).
 constexpr double kRefineCond = 16.0;
+enum : int { PS_SOLVED = 0, PS_INVALID = 1, PS_NEED_FP64 = 2 };
 
-template <int C, typename TI>
-__device__ __forceinline__ bool ps_masked_solve(const PSArgs &a, int p, const float (&R)[3][C], float (&G)[3][C],
-                                                unsigned long long valid) {
-  if (__popcll(valid) < 3) return false;
+// The FP32 part: fewer than 3 rows -> PS_INVALID; a system whose FP32 condition number
+// is at most kRefineCond -> solved (PS_SOLVED); anything else -> PS_NEED_FP64.
+template <int C>
+__device__ __forceinline__ int ps_masked_fp32(const PSArgs &a, const float (&R)[3][C], float (&G)[3][C],
+                                              unsigned long long valid) {
+  if (__popcll(valid) < 3) return PS_INVALID;
   {  // the common case in FP32: a system whose FP32 condition number is at most kRefineCond is
      // certainly below cond_max in FP64 too (FP32 rounding moves it by far less than the gap),
      // so its validity is decided as in FP64, and FP32 solves it within the normal tolerance
@@ -145,9 +168,19 @@ __device__ __forceinline__ bool ps_masked_solve(const PSArgs &a, int p, const fl
         G[1][c] = (a01 * r0 + a11 * r1 + a12 * r2) * id;
         G[2][c] = (a02 * r0 + a12 * r1 + a22 * r2) * id;
       }
-      return true;
+      return PS_SOLVED;
     }
   }
+  return PS_NEED_FP64;
+}
+
+// The FP64 part (a pixel that ps_masked_fp32 passed on): the matrix, its inverse (by the
+// adjugate) and its 1-norm condition number from the lights; singular or above cond_max:
+// false; above kRefineCond the right-hand side is summed again in FP64 from the pixel's
+// valid rows (read again).
+template <int C, typename TI>
+__device__ __forceinline__ bool ps_masked_fp64(const PSArgs &a, int p, const float (&R)[3][C], float (&G)[3][C],
+                                               unsigned long long valid) {
   double M00 = 0, M01 = 0, M02 = 0, M11 = 0, M12 = 0, M22 = 0;
   for (int k = 0; k < a.K; ++k) {
     if (!((valid >> k) & 1ull)) continue;
@@ -209,19 +242,29 @@ __device__ __forceinline__ bool ps_masked_solve(const PSArgs &a, int p, const fl
   return true;
 }
 
-// The rest of pixel p once every row is in: the FP64 solve when some row is masked, then
-// the stored normal, albedo and validity.
 template <int C, typename TI>
+__device__ __forceinline__ bool ps_masked_solve(const PSArgs &a, int p, const float (&R)[3][C], float (&G)[3][C],
+                                                unsigned long long valid) {
+  const int st = ps_masked_fp32<C>(a, R, G, valid);
+  if (st != PS_NEED_FP64) return st == PS_SOLVED;
+  return ps_masked_fp64<C, TI>(a, p, R, G, valid);
+}
+
+// The rest of pixel p once every row is in: the masked solve when some row is masked
+// (else G as summed, or from R in the normal-equation form), then the stored normal,
+// albedo and validity.
+template <int C, typename TI, bool NE>
 __device__ __forceinline__ void ps_finish(const PSArgs &a, int p, const float (&R)[3][C], float (&G)[3][C],
                                           unsigned long long valid) {
   const unsigned long long all = a.K == 64 ? ~0ull : ((1ull << a.K) - 1ull);
   bool ok = true;
   if (valid != all) ok = ps_masked_solve<C, TI>(a, p, R, G, valid);
+  else if (NE) ps_apply_minv<C>(a, R, G);
   ps_store<C>(a, p, G, ok);
 }
 
-template <int C, typename TI>
-__device__ __forceinline__ void ps_pixel(const PSArgs &a, int p) {
+template <int C, typename TI, bool NE>
+__device__ __forceinline__ void ps_pixel_t(const PSArgs &a, int p) {
   const TI *img = reinterpret_cast<const TI *>(a.images);
   const size_t P = (size_t)a.P;
   float rho[C];
@@ -241,19 +284,27 @@ __device__ __forceinline__ void ps_pixel(const PSArgs &a, int p) {
       a0[c] = load_img<TI>(img + o);
       lb[c] = a.zero_indirect ? 0.0f : __ldg(a.lbar + o);
     }
-    ps_row<C>(a, k, rho, a0, lb, G, R, valid);
+    ps_row<C, NE>(a, k, rho, a0, lb, G, R, valid);
   }
-  ps_finish<C, TI>(a, p, R, G, valid);
+  ps_finish<C, TI, NE>(a, p, R, G, valid);
+}
+
+template <int C, typename TI>
+__device__ __forceinline__ void ps_pixel(const PSArgs &a, int p) {
+  if (a.normal_eq)
+    ps_pixel_t<C, TI, true>(a, p);
+  else
+    ps_pixel_t<C, TI, false>(a, p);
 }
 
 // The single-object form in two kernels, so that the common path stays small (few
 // registers, many resident threads, several pixels' loads in flight per thread):
 //   k_ps_fast: V consecutive pixels per thread (P a multiple of V, so that every
 //     plane row is 4V-byte aligned; one vector load per plane row for all V), the
-//     FP32 contraction and row masks; a pixel with every row valid is stored, a
-//     masked one goes to a list with its row mask;
-//   k_ps_masked: the normal equations of the listed pixels (ps_masked_solve: FP64 3 x 3
-//     system from the lights, FP32 right-hand side from the first pass; no image re-read).
+//     FP32 contraction and row masks; a pixel with every row valid is stored, and so
+//     is a masked one whose system FP32 settles (ps_masked_fp32); the rest go to a
+//     list with their row masks and right-hand sides;
+//   k_ps_masked: the FP64 part of the listed pixels' solves (ps_masked_fp64).
 // Per pixel the arithmetic is that of ps_pixel, so both forms give the same bits.
 
 template <typename TI, int V>
@@ -312,8 +363,8 @@ struct PSList {
   unsigned *count;           // entries (zero before the launch)
 };
 
-template <int C, typename TI, int V>
-__global__ void __launch_bounds__(256) k_ps_fast(const PSArgs a, const PSList L) {
+template <int C, typename TI, int V, bool NE>
+__global__ void __launch_bounds__(256, (NE && V < 4) ? 4 : 2) k_ps_fast(const PSArgs a, const PSList L) {
   const int p = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   const bool in = p < a.P;
   const TI *img = reinterpret_cast<const TI *>(a.images);
@@ -361,16 +412,25 @@ __global__ void __launch_bounds__(256) k_ps_fast(const PSArgs a, const PSList L)
           x0[c] = a0[c][j];
           x1[c] = lb[c][j];
         }
-        ps_row<C>(a, k, rho[j], x0, x1, G[j], R[j], valid[j]);
+        ps_row<C, NE>(a, k, rho[j], x0, x1, G[j], R[j], valid[j]);
       }
     }
   }
   const unsigned long long all = a.K == 64 ? ~0ull : ((1ull << a.K) - 1ull);
 #pragma unroll
   for (int j = 0; j < V; ++j) {
-    const bool masked = in && valid[j] != all;
-    if (in && !masked) ps_store<C>(a, p + j, G[j], true);
-    // masked pixels of the warp appended with one atomic
+    bool masked = false;
+    if (in) {
+      if (valid[j] == all) {
+        if (NE) ps_apply_minv<C>(a, R[j], G[j]);
+        ps_store<C>(a, p + j, G[j], true);
+      } else {
+        const int st = ps_masked_fp32<C>(a, R[j], G[j], valid[j]);
+        if (st != PS_NEED_FP64) ps_store<C>(a, p + j, G[j], st == PS_SOLVED);
+        masked = st == PS_NEED_FP64;
+      }
+    }
+    // pixels left for the FP64 solve, appended with one atomic per warp
     const unsigned mm = __ballot_sync(0xffffffffu, masked);
     if (mm) {
       const int lane = threadIdx.x & 31, leader = __ffs(mm) - 1;
@@ -400,7 +460,7 @@ __global__ void __launch_bounds__(128) k_ps_masked(const PSArgs a, const PSList 
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int c = 0; c < C; ++c) R[r][c] = L.rhs[(size_t)i * 9 + r * C + c];
-    const bool ok = ps_masked_solve<C, TI>(a, p, R, G, L.mask[i]);
+    const bool ok = ps_masked_fp64<C, TI>(a, p, R, G, L.mask[i]);
     ps_store<C>(a, p, G, ok);
   }
 }
@@ -640,7 +700,7 @@ __global__ void __launch_bounds__(kTcRows) k_ps_tc(const PSArgs a, unsigned long
       for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < C; ++c) G[r][c] = __uint_as_float(d[r * C + c]);
-      ps_finish<C, TI>(a, p, R, G, valid);
+      ps_finish<C, TI, false>(a, p, R, G, valid);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -668,6 +728,8 @@ static void fill_ps_args(const Ctx &c, bool zero_indirect, PSArgs &a) {
       a.light[k][r] = c.h_lights[3 * k + r];
     }
   }
+  for (int i = 0; i < 6; ++i) a.minv[i] = c.h_minv[i];
+  a.normal_eq = c.normal_eq;
   a.blk_begin = 0;
 }
 
@@ -711,23 +773,32 @@ static cudaError_t launch_ps_tc_t(Ctx &c, const PSArgs &a) {
   return cudaGetLastError();
 }
 
+template <int C, typename TI, bool NE>
+static void launch_ps_fast(Ctx &c, const PSArgs &a, const PSList &L, int v, unsigned blocks) {
+  if (v == 4)
+    k_ps_fast<C, TI, 4, NE><<<blocks, 256, 0, c.stream>>>(a, L);
+  else if (v == 2)
+    k_ps_fast<C, TI, 2, NE><<<blocks, 256, 0, c.stream>>>(a, L);
+  else
+    k_ps_fast<C, TI, 1, NE><<<blocks, 256, 0, c.stream>>>(a, L);
+}
+
 template <int C, typename TI>
 static cudaError_t launch_ps_split(Ctx &c, const PSArgs &a) {
   const PSList L{c.ps_pix, c.ps_mask, c.ps_rhs, c.ps_count};
   cudaError_t e = cudaMemsetAsync(c.ps_count, 0, sizeof(unsigned), c.stream);
   if (e != cudaSuccess) return e;
-  const int threads = 256;
   const int v = ps_vec_for(c);
   const int n = (a.P + v - 1) / v;
-  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
-  if (v == 4)
-    k_ps_fast<C, TI, 4><<<blocks, threads, 0, c.stream>>>(a, L);
-  else if (v == 2)
-    k_ps_fast<C, TI, 2><<<blocks, threads, 0, c.stream>>>(a, L);
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (a.normal_eq)
+    launch_ps_fast<C, TI, true>(c, a, L, v, blocks);
   else
-    k_ps_fast<C, TI, 1><<<blocks, threads, 0, c.stream>>>(a, L);
-  // one listed pixel per thread (the list can hold every pixel; threads past its end return)
-  k_ps_masked<C, TI><<<(unsigned)((a.P + 127) / 128), 128, 0, c.stream>>>(a, L);
+    launch_ps_fast<C, TI, false>(c, a, L, v, blocks);
+  // the listed pixels (few: ill-conditioned masked systems), a grid-stride loop over the list
+  const int cap = 4 * (c.sms > 0 ? c.sms : 1);
+  const unsigned mblocks = (unsigned)std::min<long long>(cap, ((long long)a.P + 127) / 128);
+  k_ps_masked<C, TI><<<mblocks, 128, 0, c.stream>>>(a, L);
   return cudaGetLastError();
 }
 
