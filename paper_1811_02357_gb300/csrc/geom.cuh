@@ -341,46 +341,54 @@ __device__ __forceinline__ bool walker_walk_over(const Walker &m, const Field &f
 }
 
 // Node step.  Returns true when the march is over; sets at_leaf when the walker
-// waits for a leaf step.
+// waits for a leaf step.  A skip leaves the node across the axis whose exit comes
+// first (both on a tie); the cell on the other axis at that parameter comes from one
+// cell_at on the selected axis, so that lanes skipping across x and across y run the
+// same instructions.  The walk's end has one call site.
 __device__ __forceinline__ bool walker_node_step(Walker &m, const Field &f, const LevelTable &lt, Work &w,
                                                  bool &at_leaf) {
   const float inf = __int_as_float(0x7f800000);
-  if (walker_walk_over(m, f)) return walker_finish_walk(m);
-  const int sx = walker_sx(m), sy = walker_sy(m);
-  const int lv = m.lv;
-  const int nx = m.cx >> lv, ny = m.cy >> lv;
-  const int X0 = nx << lv, Y0 = ny << lv;
-  const int X1 = min(X0 + (1 << lv), f.Wc), Y1 = min(Y0 + (1 << lv), f.Hc);
-  const int2 ol = lt.ol[lv];
-  const float nmax = __ldg(f.pmax + ol.x + ny * ol.y + nx);
-  ++w.nodes;
-  const float tX = sx != 0 ? rmul(rsub((float)(sx > 0 ? X1 : X0), m.o.x), m.ix) : inf;
-  const float tY = sy != 0 ? rmul(rsub((float)(sy > 0 ? Y1 : Y0), m.o.y), m.iy) : inf;
-  const float t_exit = fminf(tX, tY);
-  // lowest height of the ray over the node: at entry when rising, else at exit
-  const float zlow = fmaf(m.d.z >= 0.0f ? m.t_entry : t_exit, m.d.z, m.o.z);
-  if (zlow > nmax + lt.dz) {
-    if (t_exit == inf) return walker_finish_walk(m);  // vertical ray above everything below it
-    if (tX < tY) {
-      m.cx = sx > 0 ? X1 : X0 - 1;
-      if (sy != 0) m.cy = cell_at(m.o.y, m.d.y, m.iy, sy, m.cy, Y0, Y1, tX);
-      m.t_entry = tX;
-    } else if (tY < tX) {
-      m.cy = sy > 0 ? Y1 : Y0 - 1;
-      if (sx != 0) m.cx = cell_at(m.o.x, m.d.x, m.ix, sx, m.cx, X0, X1, tY);
-      m.t_entry = tY;
+  bool over = walker_walk_over(m, f);
+  if (!over) {
+    const int sx = walker_sx(m), sy = walker_sy(m);
+    const int lv = m.lv;
+    const int nx = m.cx >> lv, ny = m.cy >> lv;
+    const int X0 = nx << lv, Y0 = ny << lv;
+    const int X1 = min(X0 + (1 << lv), f.Wc), Y1 = min(Y0 + (1 << lv), f.Hc);
+    const int2 ol = lt.ol[lv];
+    const float nmax = __ldg(f.pmax + ol.x + ny * ol.y + nx);
+    ++w.nodes;
+    const float tX = sx != 0 ? rmul(rsub((float)(sx > 0 ? X1 : X0), m.o.x), m.ix) : inf;
+    const float tY = sy != 0 ? rmul(rsub((float)(sy > 0 ? Y1 : Y0), m.o.y), m.iy) : inf;
+    const float t_exit = fminf(tX, tY);
+    // lowest height of the ray over the node: at entry when rising, else at exit
+    const float zlow = fmaf(m.d.z >= 0.0f ? m.t_entry : t_exit, m.d.z, m.o.z);
+    if (zlow > nmax + lt.dz) {
+      if (t_exit == inf) {
+        over = true;  // vertical ray above everything below it
+      } else {
+        // crossed axes: x alone (tX < tY), y alone (tY < tX), or both (a tie)
+        const bool cross_x = !(tY < tX), cross_y = !(tX < tY);
+        const float te = (cross_y && !cross_x) ? tY : tX;
+        const bool y_alone = cross_y && !cross_x;
+        const int s_o = y_alone ? sx : sy;  // the axis not crossed, when one is crossed alone
+        if (cross_x != cross_y && s_o != 0) {
+          const int c = cell_at(y_alone ? m.o.x : m.o.y, y_alone ? m.d.x : m.d.y, y_alone ? m.ix : m.iy, s_o,
+                                y_alone ? m.cx : m.cy, y_alone ? X0 : Y0, y_alone ? X1 : Y1, te);
+          if (y_alone) m.cx = c; else m.cy = c;
+        }
+        if (cross_x) m.cx = sx > 0 ? X1 : X0 - 1;
+        if (cross_y) m.cy = sy > 0 ? Y1 : Y0 - 1;
+        m.t_entry = te;
+        m.lv = min(lv + kClimb, f.levels - 1);
+      }
+    } else if (lv > 0) {
+      m.lv = lv - 1;
     } else {
-      m.cx = sx > 0 ? X1 : X0 - 1;
-      m.cy = sy > 0 ? Y1 : Y0 - 1;
-      m.t_entry = tX;
+      at_leaf = true;
     }
-    m.lv = min(lv + kClimb, f.levels - 1);
-  } else if (lv > 0) {
-    m.lv = lv - 1;
-  } else {
-    at_leaf = true;
   }
-  return false;
+  return over ? walker_finish_walk(m) : false;
 }
 
 // Leaf step: both triangles of the current cell (and, at a near-vertex

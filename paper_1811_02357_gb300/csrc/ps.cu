@@ -363,8 +363,19 @@ struct PSList {
   unsigned *count;           // entries (zero before the launch)
 };
 
+#ifndef IRTPS_PS_MINB
+#define IRTPS_PS_MINB 4
+#endif
+#ifndef IRTPS_PS_KUNROLL
+#define IRTPS_PS_KUNROLL 4
+#endif
+// resident blocks per SM asked of the normal-equation form (its state fits 64 registers at V <= 2)
+constexpr int kPsMinBlocks = IRTPS_PS_MINB;
+// lights per unrolled step of the streaming loop, over all V pixels of a thread
+constexpr int kPsKUnroll = IRTPS_PS_KUNROLL;
+
 template <int C, typename TI, int V, bool NE>
-__global__ void __launch_bounds__(256, (NE && V < 4) ? 4 : 2) k_ps_fast(const PSArgs a, const PSList L) {
+__global__ void __launch_bounds__(256, (NE && V < 4) ? kPsMinBlocks : 2) k_ps_fast(const PSArgs a, const PSList L) {
   const int p = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   const bool in = p < a.P;
   const TI *img = reinterpret_cast<const TI *>(a.images);
@@ -390,7 +401,7 @@ __global__ void __launch_bounds__(256, (NE && V < 4) ? 4 : 2) k_ps_fast(const PS
 #pragma unroll
       for (int j = 0; j < V; ++j) rho[j][c] = v[j];
     }
-#pragma unroll(4 / V)
+#pragma unroll(kPsKUnroll / V > 0 ? kPsKUnroll / V : 1)
     for (int k = 0; k < a.K; ++k) {
       float a0[C][V], lb[C][V];
 #pragma unroll
