@@ -174,70 +174,126 @@ __device__ __forceinline__ int ps_masked_fp32(const PSArgs &a, const float (&R)[
   return PS_NEED_FP64;
 }
 
-// The FP64 part (a pixel that ps_masked_fp32 passed on): the matrix, its inverse (by the
-// adjugate) and its 1-norm condition number from the lights; singular or above cond_max:
-// false; above kRefineCond the right-hand side is summed again in FP64 from the pixel's
-// valid rows (read again).
-template <int C, typename TI>
-__device__ __forceinline__ bool ps_masked_fp64(const PSArgs &a, int p, const float (&R)[3][C], float (&G)[3][C],
-                                               unsigned long long valid) {
-  double M00 = 0, M01 = 0, M02 = 0, M11 = 0, M12 = 0, M22 = 0;
-  for (int k = 0; k < a.K; ++k) {
-    if (!((valid >> k) & 1ull)) continue;
-    const double lx = a.light[k][0], ly = a.light[k][1], lz = a.light[k][2];
-    M00 += lx * lx;
-    M01 += lx * ly;
-    M02 += lx * lz;
-    M11 += ly * ly;
-    M12 += ly * lz;
-    M22 += lz * lz;
-  }
-  // inverse by the adjugate; 1-norm condition number
+// The part that FP32 passed on (ps_masked_fp32): the matrix L_v^T L_v and the right-hand side
+// in double-float arithmetic, the inverse (by the adjugate) and the 1-norm condition number in
+// FP64; singular or above cond_max: false.  Above kRefineCond the right-hand side is summed again
+// from the pixel's valid rows (read again), since the condition number would amplify the FP32
+// rounding of the streaming pass's sum.  GB300's FP64 pipe is narrow, so the sums, which are
+// most of the work, run on the FP32 pipes as double-float values (hi + lo, about 48 bits), built
+// from error-free transformations: Knuth's two-sum and the fused-multiply-add two-product.
+// Every operation is rounded on its own (the _rn intrinsics keep the compiler from fusing or
+// reordering them), so the per-thread uses of these helpers give the same bits everywhere.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return DF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // needs |a| >= |b| (or a = 0)
+  const float s = __fadd_rn(a, b);
+  return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  const DF s = df_two_sum(x.hi, y.hi);
+  const DF t = df_two_sum(x.lo, y.lo);
+  const DF u = df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return df_fast_two_sum(u.hi, __fadd_rn(u.lo, t.lo));
+}
+// x * b exactly as hi + lo (two-product)
+__device__ __forceinline__ DF df_prod(float x, float b) {
+  const float p = __fmul_rn(x, b);
+  return DF{p, __fmaf_rn(x, b, -p)};
+}
+__device__ __forceinline__ DF df_mul_f(DF x, float b) {
+  const DF p = df_prod(x.hi, b);
+  return df_fast_two_sum(p.hi, __fmaf_rn(x.lo, b, p.lo));
+}
+__device__ __forceinline__ double df_to_double(DF x) { return (double)x.hi + (double)x.lo; }
+
+// Entry (u, v) of L_v^T L_v, over the valid rows in light order (each product exact).
+__device__ __forceinline__ double ps_m_df(const PSArgs &a, unsigned long long valid, int u, int v) {
+  DF s = {0.0f, 0.0f};
+  for (int k = 0; k < a.K; ++k)
+    if ((valid >> k) & 1ull) s = df_add(s, df_prod(a.light[k][u], a.light[k][v]));
+  return df_to_double(s);
+}
+// the six entries m00 m01 m02 m11 m12 m22
+__device__ __constant__ const int kMu[6] = {0, 0, 0, 1, 1, 2};
+__device__ __constant__ const int kMv[6] = {0, 1, 2, 1, 2, 2};
+
+// Inverse (m00 m01 m02 m11 m12 m22 layout) and 1-norm condition number; false when the
+// system is singular or above cond_max.
+__device__ __forceinline__ bool ps_inv64(const PSArgs &a, const double (&M)[6], double (&I)[6], double &cond) {
+  const double M00 = M[0], M01 = M[1], M02 = M[2], M11 = M[3], M12 = M[4], M22 = M[5];
   const double A00 = M11 * M22 - M12 * M12, A01 = M02 * M12 - M01 * M22, A02 = M01 * M12 - M02 * M11;
   const double A11 = M00 * M22 - M02 * M02, A12 = M01 * M02 - M00 * M12, A22 = M00 * M11 - M01 * M01;
   const double det = M00 * A00 + M01 * A01 + M02 * A02;
   if (!(det != 0.0) || !isfinite(det)) return false;
   const double id = 1.0 / det;
-  const double i00 = A00 * id, i01 = A01 * id, i02 = A02 * id, i11 = A11 * id, i12 = A12 * id, i22 = A22 * id;
+  I[0] = A00 * id;
+  I[1] = A01 * id;
+  I[2] = A02 * id;
+  I[3] = A11 * id;
+  I[4] = A12 * id;
+  I[5] = A22 * id;
   const double nM = fmax(fabs(M00) + fabs(M01) + fabs(M02),
                          fmax(fabs(M01) + fabs(M11) + fabs(M12), fabs(M02) + fabs(M12) + fabs(M22)));
-  const double nI = fmax(fabs(i00) + fabs(i01) + fabs(i02),
-                         fmax(fabs(i01) + fabs(i11) + fabs(i12), fabs(i02) + fabs(i12) + fabs(i22)));
-  const double cond = nM * nI;
-  if (!(cond <= a.cond_max)) return false;
+  const double nI = fmax(fabs(I[0]) + fabs(I[1]) + fabs(I[2]),
+                         fmax(fabs(I[1]) + fabs(I[3]) + fabs(I[4]), fabs(I[2]) + fabs(I[4]) + fabs(I[5])));
+  cond = nM * nI;
+  return cond <= a.cond_max;
+}
+
+template <int C, typename TI>
+__device__ __forceinline__ bool ps_masked_fp64(const PSArgs &a, int p, const float (&R)[3][C], float (&G)[3][C],
+                                               unsigned long long valid) {
+  double M[6], I[6], cond;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) M[e] = ps_m_df(a, valid, kMu[e], kMv[e]);
+  if (!ps_inv64(a, M, I, cond)) return false;
   double Rd[3][C];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int c = 0; c < C; ++c) Rd[r][c] = R[r][c];
-  if (cond > kRefineCond) {  // ill-conditioned: the right-hand side in FP64
+  if (cond > kRefineCond) {  // ill-conditioned: the right-hand side again, in double-float
     const TI *img = reinterpret_cast<const TI *>(a.images);
     const size_t P = (size_t)a.P;
     float rho[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) rho[c] = a.zero_indirect ? 0.0f : a.albedo[c * P + p];
+    DF Rf[3][C];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int c = 0; c < C; ++c) Rd[r][c] = 0.0;
+      for (int c = 0; c < C; ++c) Rf[r][c] = DF{0.0f, 0.0f};
     for (int k = 0; k < a.K; ++k) {
       if (!((valid >> k) & 1ull)) continue;
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         const size_t o = ((size_t)k * C + c) * P + p;
-        const double lb = a.zero_indirect ? 0.0 : (double)__ldg(a.lbar + o);
-        const double Iv = (double)load_img<TI>(img + o) - (double)rho[c] * lb;
-        Rd[0][c] += (double)a.light[k][0] * Iv;
-        Rd[1][c] += (double)a.light[k][1] * Iv;
-        Rd[2][c] += (double)a.light[k][2] * Iv;
+        const float a0 = load_img<TI>(img + o);
+        const float lb = a.zero_indirect ? 0.0f : __ldg(a.lbar + o);
+        // I = a0 - rho lb: rho lb = q.hi + q.lo exactly, then two exact-error subtractions
+        const DF q = df_prod(rho[c], lb);
+        const DF d = df_two_sum(a0, -q.hi);
+        const DF iv = df_two_sum(d.hi, __fsub_rn(d.lo, q.lo));
+#pragma unroll
+        for (int r = 0; r < 3; ++r) Rf[r][c] = df_add(Rf[r][c], df_mul_f(iv, a.light[k][r]));
       }
     }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < C; ++c) Rd[r][c] = df_to_double(Rf[r][c]);
   }
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    G[0][c] = (float)(i00 * Rd[0][c] + i01 * Rd[1][c] + i02 * Rd[2][c]);
-    G[1][c] = (float)(i01 * Rd[0][c] + i11 * Rd[1][c] + i12 * Rd[2][c]);
-    G[2][c] = (float)(i02 * Rd[0][c] + i12 * Rd[1][c] + i22 * Rd[2][c]);
+    G[0][c] = (float)(I[0] * Rd[0][c] + I[1] * Rd[1][c] + I[2] * Rd[2][c]);
+    G[1][c] = (float)(I[1] * Rd[0][c] + I[3] * Rd[1][c] + I[4] * Rd[2][c]);
+    G[2][c] = (float)(I[2] * Rd[0][c] + I[4] * Rd[1][c] + I[5] * Rd[2][c]);
   }
   return true;
 }
@@ -461,6 +517,8 @@ __global__ void __launch_bounds__(256, (NE && V < 4) ? kPsMinBlocks : 2) k_ps_fa
   }
 }
 
+// The listed pixels, one per thread (the FP64 pipe is narrow: a pixel's FP64 work stays in
+// one lane), a grid-stride loop over the list.
 template <int C, typename TI>
 __global__ void __launch_bounds__(128) k_ps_masked(const PSArgs a, const PSList L) {
   const unsigned n = *L.count;
