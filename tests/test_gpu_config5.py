@@ -40,7 +40,7 @@ def test_config5_fp16_and_fp32_against_oracle(lib, oracle_mod, scene):
     rng = np.random.default_rng(5)
     ci, cj = np.meshgrid(np.arange(H)[CROP], np.arange(W)[CROP], indexing="ij")
     crop_pix = (ci * W + cj).ravel()
-    sample = np.sort(rng.choice(crop_pix, 24, replace=False)).astype(np.int32)
+    sample = np.sort(rng.choice(crop_pix, 64, replace=False)).astype(np.int32)
     normals_by = {}
     for name, dtype in (("f32", lib.IRTPS_F32), ("f16", lib.IRTPS_F16)):
         imgs = A if name == "f32" else A.half()

@@ -44,6 +44,58 @@ def test_ps_stage(lib, oracle_mod, case, f16):
     assert n1[..., 3].reshape(-1)[ok].min() > 0
 
 
+def _cond1(M):
+    return np.abs(M).sum(axis=1).max(axis=1) * np.abs(np.linalg.inv(M)).sum(axis=1).max(axis=1)
+
+
+@pytest.mark.parametrize("f16", [False, True])
+def test_ps_ill_conditioned_masked(lib, oracle_mod, f16):
+    """Pixels that keep only a narrow arc of 3-6 of 12 lights (the rest in shadow): their masked
+    systems are ill-conditioned (condition numbers far above 16), so the solve leaves the streaming
+    pass for the list kernel (double-float matrix and re-read right-hand side, FP64 inverse).
+    Masks and validity bit-exact, normals within 1e-3 deg and albedo within 1e-5 of the oracle, at
+    iteration 0 and with an indirect term subtracted."""
+    H, W, K, C = 37, 53, 12, 3
+    P = H * W
+    rng = np.random.default_rng(7)
+    lights = scenes.ring_lights(K, rng.uniform(35.0, 55.0, K), az0=0.3)
+    X, Y = scenes.grid(H, W)
+    n = scenes.normals_from_gradient(0.4 * np.sin(9 * X + 2 * Y), 0.4 * np.cos(7 * Y - X)).reshape(P, 3)
+    albedo = rng.uniform(0.4, 0.8, (C, P))
+    shade = np.clip(n @ lights.T, 0.0, None).T  # K x P
+    A0 = albedo[None] * shade[:, None, :] + rng.normal(0.0, 0.002, (K, C, P))
+    keep = rng.integers(3, 7, P)
+    start = rng.integers(0, K, P)
+    arc = ((np.arange(K)[:, None] - start[None, :]) % K) < keep[None, :]
+    arc[:, rng.uniform(size=P) < 0.2] = True  # some pixels keep every light
+    A0 = np.where(arc[:, None, :], A0, 0.005).astype(np.float32)
+    if f16:
+        A0 = A0.astype(np.float16).astype(np.float32)
+    lbar = rng.uniform(0.0, 0.02, (K, C, P)).astype(np.float32)
+    rho = (albedo * rng.uniform(0.95, 1.05, albedo.shape)).astype(np.float32)
+    env = np.zeros((C, 4, 8), np.float32)
+    imgs = A0.reshape(K, C, H, W)
+    with lib.Context(H, W, lights, env) as ctx:
+        ctx.set_images(imgs.astype(np.float16) if f16 else imgs, lib.IRTPS_F16 if f16 else lib.IRTPS_F32)
+        n0, a0, v0 = ctx.normals(), ctx.albedo(), ctx.valid()
+        ctx.set_state(albedo=rho.reshape(C, H, W))
+        ctx.set_indirect(lbar.reshape(K, C, H, W))
+        ctx.solve_normals()
+        n1, a1, v1 = ctx.normals(), ctx.albedo(), ctx.valid()
+    L = np.asarray(lights, np.float32).astype(np.float64)
+    for (nn, aa, vv, lb, r) in [(n0, a0, v0, np.zeros_like(lbar), np.zeros((C, P))),
+                                (n1, a1, v1, lbar, rho)]:
+        want_n, want_r, ok = oracle_mod.ps_step(imgs, r, lb, L)
+        rows = oracle_mod.valid_rows(A0, r, lb, oracle_mod.TAU_LO, oracle_mod.TAU_HI)  # K x P
+        masked = ok & ~rows.all(axis=0)
+        M = np.einsum("kp,ki,kj->pij", rows[:, masked].astype(np.float64), L, L)
+        assert (_cond1(M) > 16).sum() > 0.3 * P  # most pixels take the list kernel
+        assert np.array_equal(vv.ravel().astype(bool), ok)
+        err = oracle_mod.angular_error_deg(nn[..., :3].reshape(-1, 3)[ok], want_n[ok])
+        assert err.max() < 1e-3, err.max()
+        assert np.abs(aa.reshape(C, P)[:, ok] - want_r[:, ok]).max() < 1e-5 * max(1.0, want_r.max())
+
+
 @pytest.mark.parametrize("precond", [0, 1, 2])
 @pytest.mark.parametrize("H,W", [(64, 64), (37, 53), (256, 256), (2, 5), (3, 301), (2, 1030)])
 def test_integrate(lib, oracle_mod, H, W, precond):
