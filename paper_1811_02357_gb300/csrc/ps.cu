@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(256) k_ps_b(const PSArgs *__restrict__ objs, i
 // pinv are each a BF16 pair hi + lo (hi = bf16(x), lo = bf16(x - hi)); the chain
 // I_hi P_hi + I_lo P_hi + I_hi P_lo accumulates in FP32 in tensor memory (the
 // dropped I_lo P_lo is below 2^-16 of the product).  Row masks are decided in
-// FP32 from I exactly as in k_ps, and masked pixels take its FP64 path.
+// FP32 from I exactly as in k_ps_fast, and masked pixels take the same masked solve.
 //
 // Shared-memory operands use the canonical K-major layout without swizzle:
 // 8-row x 16-byte core matrices, the 16 core matrices of one 8-wide K column
