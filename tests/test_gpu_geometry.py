@@ -4,6 +4,8 @@ Integer decisions of the trace (hit or miss, hit triangle) are taken in FP32 on
 both sides with the same operation order, so they must agree exactly; the
 sampled directions they are built from must agree to the bit.
 """
+import zlib
+
 import numpy as np
 import pytest
 
@@ -53,9 +55,26 @@ def _rays(depth, rng, n):
     return np.array(out, np.float32)
 
 
+def _grazing_only(depth, rays, tri, t_b, tri_b):
+    """Rays where the walk's triangle differs from brute force over every triangle.  The walk reports
+    the first hit among the cells the ray passes through; brute force can also admit, by FP32
+    rounding in the triangle test, a hit on the far side of a cell edge that the ray runs along
+    within rounding of it.  Such a hit lies outside its own cell, by less than 1e-5 of a cell.
+    Returns the number of rays that differ; fails on any other difference."""
+    Wc = depth.shape[1] - 1
+    bad = np.nonzero(tri != tri_b)[0]
+    for r in bad:
+        assert tri_b[r] >= 0, (r, rays[r], tri[r], tri_b[r])
+        cy, cx = divmod(int(tri_b[r]) // 2, Wc)
+        q = rays[r, :3].astype(np.float64) + t_b[r] * rays[r, 3:].astype(np.float64)
+        outside = max(cx - q[0], q[0] - (cx + 1), cy - q[1], q[1] - (cy + 1))
+        assert 0.0 < outside < 1e-5, (r, rays[r], tri[r], tri_b[r], outside)
+    return bad.size
+
+
 @pytest.mark.parametrize("case", ["random16", "bowl64", "mixed_37x53", "bumps_200x137", "tiny_2x3"])
 def test_rays_match_oracle_walk(lib, oracle_mod, case):
-    rng = np.random.default_rng(hash(case) % 2 ** 32)
+    rng = np.random.default_rng(zlib.crc32(case.encode()))
     if case == "random16":
         depth = scenes.random_heightfield(3, 16, 16, 0.3 / 16)
     elif case == "bowl64":
@@ -81,5 +100,5 @@ def test_rays_match_oracle_walk(lib, oracle_mod, case):
     assert np.array_equal(t[hit], t_o[hit].astype(np.float32))
     assert hit.sum() > 100
     if H * W <= 16 * 16:
-        _, tri_b = oracle_mod.intersect(depth, rays.astype(np.float64), fp32=True, brute=True)
-        assert np.array_equal(tri, tri_b)
+        t_b, tri_b = oracle_mod.intersect(depth, rays.astype(np.float64), fp32=True, brute=True)
+        assert _grazing_only(depth, rays, tri, t_b, tri_b) <= 2  # a rounding corner, not a pattern

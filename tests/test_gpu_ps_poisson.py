@@ -96,6 +96,44 @@ def test_ps_ill_conditioned_masked(lib, oracle_mod, f16):
         assert np.abs(aa.reshape(C, P)[:, ok] - want_r[:, ok]).max() < 1e-5 * max(1.0, want_r.max())
 
 
+def test_ps_pinv_form_for_clustered_lights(lib, oracle_mod):
+    """Lights in a narrow cone (L^T L with 1-norm condition number far above 16): fully valid pixels
+    take the pinv(L) I form instead of the normal-equation form; parity as for the ring lights."""
+    H, W, K, C = 29, 41, 8, 3
+    P = H * W
+    rng = np.random.default_rng(11)
+    el = np.radians(rng.uniform(62.0, 72.0, K))
+    az = rng.uniform(0.0, 0.8, K)
+    lights = np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], axis=1)
+    L = np.asarray(lights, np.float32).astype(np.float64)
+    M = L.T @ L
+    assert np.abs(M).sum(axis=0).max() * np.abs(np.linalg.inv(M)).sum(axis=0).max() > 16
+    X, Y = scenes.grid(H, W)
+    n = scenes.normals_from_gradient(0.3 * np.sin(5 * X), 0.3 * np.cos(4 * Y)).reshape(P, 3)
+    albedo = rng.uniform(0.4, 0.8, (C, P))
+    A0 = (albedo[None] * np.clip(n @ L.T, 0.0, None).T[:, None, :] + rng.normal(0.0, 0.002, (K, C, P)))
+    A0 = A0.astype(np.float32)
+    lbar = rng.uniform(0.0, 0.02, (K, C, P)).astype(np.float32)
+    rho = (albedo * rng.uniform(0.95, 1.05, albedo.shape)).astype(np.float32)
+    imgs = A0.reshape(K, C, H, W)
+    with lib.Context(H, W, lights, np.zeros((C, 4, 8), np.float32)) as ctx:
+        ctx.set_images(imgs, lib.IRTPS_F32)
+        n0, a0, v0 = ctx.normals(), ctx.albedo(), ctx.valid()
+        ctx.set_state(albedo=rho.reshape(C, H, W))
+        ctx.set_indirect(lbar.reshape(K, C, H, W))
+        ctx.solve_normals()
+        n1, a1, v1 = ctx.normals(), ctx.albedo(), ctx.valid()
+    for (nn, aa, vv, lb, r) in [(n0, a0, v0, np.zeros_like(lbar), np.zeros((C, P))),
+                                (n1, a1, v1, lbar, rho)]:
+        want_n, want_r, ok = oracle_mod.ps_step(imgs, r, lb, L)
+        rows = oracle_mod.valid_rows(A0, r, lb, oracle_mod.TAU_LO, oracle_mod.TAU_HI)
+        assert (ok & rows.all(axis=0)).sum() > P // 2  # mostly fully valid pixels
+        assert np.array_equal(vv.ravel().astype(bool), ok)
+        err = oracle_mod.angular_error_deg(nn[..., :3].reshape(-1, 3)[ok], want_n[ok])
+        assert err.max() < 1e-3, err.max()
+        assert np.abs(aa.reshape(C, P)[:, ok] - want_r[:, ok]).max() < 1e-5 * max(1.0, want_r.max())
+
+
 @pytest.mark.parametrize("precond", [0, 1, 2])
 @pytest.mark.parametrize("H,W", [(64, 64), (37, 53), (256, 256), (2, 5), (3, 301), (2, 1030)])
 def test_integrate(lib, oracle_mod, H, W, precond):

@@ -116,3 +116,26 @@ def test_walk_equals_brute_force(oracle_mod, fp32):
         assert np.array_equal(t1[hit], t2[hit]), name
         total_hits += hit.sum()
     assert total_hits > 1000
+
+
+def test_grazing_ray_walk_keeps_its_row(oracle_mod):
+    """A ray from a vertex running within 1e-7 of a grid line: the cell walk tests the row the ray
+    travels through (its hit lies inside its cell); brute force over every triangle also admits, by
+    FP32 rounding in the triangle test, a hit in the neighbouring row 7.5e-8 of a cell outside that
+    triangle's cell.  The walk's answer is the geometric one; the GPU reproduces the walk."""
+    import scenes
+    depth = scenes.random_heightfield(3, 16, 16, 0.3 / 16)
+    ray = np.array([[11.0, 7.0, 0.011806140653789043, -1.0778954029083252, 0.0004152927431277931,
+                     -0.3501964509487152]], np.float32).astype(np.float64)
+    t_w, i_w = oracle_mod.intersect(depth, ray, fp32=True, brute=False)
+    t_b, i_b = oracle_mod.intersect(depth, ray, fp32=True, brute=True)
+    Wc = depth.shape[1] - 1
+
+    def outside(t, i):
+        cy, cx = divmod(int(i) // 2, Wc)
+        q = ray[0, :3] + t * ray[0, 3:]
+        return max(cx - q[0], q[0] - (cx + 1), cy - q[1], q[1] - (cy + 1))
+
+    assert i_w[0] >= 0 and i_b[0] >= 0 and i_w[0] != i_b[0]
+    assert outside(t_w[0], i_w[0]) <= 0.0          # the walk's hit: inside its own cell
+    assert 0.0 < outside(t_b[0], i_b[0]) < 1e-6    # brute force's: a rounding hit across the edge
