@@ -433,11 +433,16 @@ __global__ void __launch_bounds__(kTraceThreads,
   int b = 1, qp = 0, ks = 0, budget = alive ? budget0() : 0;
   bool shadow = false;
   float cosv = 0.0f;
-  float thr[C], acc[C], sum[C], comp[C];
+  float thr[C], acc[C];
+  // the item's Kahan sums over samples (touched once per sample) in shared memory, one column per
+  // lane: the registers they free keep the march's state out of local memory
+  __shared__ float s_kahan[2][3][kTraceThreads];
+  auto sum = [&](int c) -> float & { return s_kahan[0][c][threadIdx.x]; };
+  auto comp = [&](int c) -> float & { return s_kahan[1][c][threadIdx.x]; };
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     thr[c] = 1.0f;
-    acc[c] = sum[c] = comp[c] = 0.0f;
+    acc[c] = sum(c) = comp(c) = 0.0f;
   }
   Walker m;
   bool at_leaf = false;
@@ -467,10 +472,10 @@ __global__ void __launch_bounds__(kTraceThreads,
   auto end_sample = [&]() {
 #pragma unroll
     for (int c = 0; c < C; ++c) {  // Kahan summation over samples
-      const float y = acc[c] - comp[c];
-      const float t = sum[c] + y;
-      comp[c] = (t - sum[c]) - y;
-      sum[c] = t;
+      const float y = acc[c] - comp(c);
+      const float t = sum(c) + y;
+      comp(c) = (t - sum(c)) - y;
+      sum(c) = t;
       acc[c] = 0.0f;
       thr[c] = 1.0f;
     }
@@ -528,16 +533,16 @@ __global__ void __launch_bounds__(kTraceThreads,
           // (after all chunks' light sums); the reduction adds it to each light
           float *e = ob->part + ((size_t)ob->n_chunks * ob->n_pix * ob->K + (size_t)j * ob->n_pix + ip) * C;
 #pragma unroll
-          for (int c = 0; c < C; ++c) e[c] = sum[c];
+          for (int c = 0; c < C; ++c) e[c] = sum(c);
         } else {
           const float inv = 1.0f / (float)ob->spp;
 #pragma unroll
-          for (int c = 0; c < C; ++c) ob->out[((size_t)k * C + c) * ob->n_pix + ip] = sum[c] * inv;
+          for (int c = 0; c < C; ++c) ob->out[((size_t)k * C + c) * ob->n_pix + ip] = sum(c) * inv;
           if (ob->hole) ob->hole[(size_t)k * ob->n_pix + ip] = seen ? 0 : 1;
           seen = false;
         }
 #pragma unroll
-        for (int c = 0; c < C; ++c) sum[c] = comp[c] = 0.0f;
+        for (int c = 0; c < C; ++c) sum(c) = comp(c) = 0.0f;
       }
       const int lane = threadIdx.x & 31;
       const int leader = __ffs(need) - 1;
