@@ -433,16 +433,18 @@ __global__ void __launch_bounds__(kTraceThreads,
   int b = 1, qp = 0, ks = 0, budget = alive ? budget0() : 0;
   bool shadow = false;
   float cosv = 0.0f;
-  float thr[C], acc[C];
-  // the item's Kahan sums over samples (touched once per sample) in shared memory, one column per
-  // lane: the registers they free keep the march's state out of local memory
-  __shared__ float s_kahan[2][3][kTraceThreads];
-  auto sum = [&](int c) -> float & { return s_kahan[0][c][threadIdx.x]; };
-  auto comp = [&](int c) -> float & { return s_kahan[1][c][threadIdx.x]; };
+  // the path's throughput and radiance (touched once per segment) and the item's Kahan sums over
+  // samples (once per sample) in shared memory, one column per lane: the registers they free keep
+  // the march's state out of local memory
+  __shared__ float s_path[4][3][kTraceThreads];
+  auto thr = [&](int c) -> float & { return s_path[0][c][threadIdx.x]; };
+  auto acc = [&](int c) -> float & { return s_path[1][c][threadIdx.x]; };
+  auto sum = [&](int c) -> float & { return s_path[2][c][threadIdx.x]; };
+  auto comp = [&](int c) -> float & { return s_path[3][c][threadIdx.x]; };
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    thr[c] = 1.0f;
-    acc[c] = sum(c) = comp(c) = 0.0f;
+    thr(c) = 1.0f;
+    acc(c) = sum(c) = comp(c) = 0.0f;
   }
   Walker m;
   bool at_leaf = false;
@@ -467,17 +469,17 @@ __global__ void __launch_bounds__(kTraceThreads,
   auto add_direct = [&](int kk) {
     float *d = ob->part + ((size_t)j * ob->n_pix + ip) * ob->K * C + kk * C;
 #pragma unroll
-    for (int c = 0; c < C; ++c) d[c] += thr[c] * albedo_at(c, qp) * cosv;
+    for (int c = 0; c < C; ++c) d[c] += thr(c) * albedo_at(c, qp) * cosv;
   };
   auto end_sample = [&]() {
 #pragma unroll
     for (int c = 0; c < C; ++c) {  // Kahan summation over samples
-      const float y = acc[c] - comp(c);
+      const float y = acc(c) - comp(c);
       const float t = sum(c) + y;
       comp(c) = (t - sum(c)) - y;
       sum(c) = t;
-      acc[c] = 0.0f;
-      thr[c] = 1.0f;
+      acc(c) = 0.0f;
+      thr(c) = 1.0f;
     }
     ++s;
     b = 1;
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(kTraceThreads,
   // which the walker keeps as its origin m.o until the next set-up
   auto continue_path = [&](int q) {
 #pragma unroll
-    for (int c = 0; c < C; ++c) thr[c] *= albedo_at(c, q);
+    for (int c = 0; c < C; ++c) thr(c) *= albedo_at(c, q);
     if (b < ob->bounces) {
       ++b;
       phase = PH_SETUP;
@@ -636,7 +638,7 @@ __global__ void __launch_bounds__(kTraceThreads,
           if (a.rec) rec_slot(b)[1] = vis;
           if (vis) {
 #pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * albedo_at(c, qp), cosv, acc[c]);
+            for (int c = 0; c < C; ++c) acc(c) = fmaf(thr(c) * albedo_at(c, qp), cosv, acc(c));
           }
           continue_path(qp);
         }
@@ -646,7 +648,7 @@ __global__ void __launch_bounds__(kTraceThreads,
         float e[C];
         env_lookup<C>(ob->env, ob->EH, ob->EW, dw, e);
 #pragma unroll
-        for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c], e[c], acc[c]);
+        for (int c = 0; c < C; ++c) acc(c) = fmaf(thr(c), e[c], acc(c));
         if (a.rec) {
           int32_t *r = rec_slot(b);
           const int n = rec_width();
@@ -684,7 +686,7 @@ __global__ void __launch_bounds__(kTraceThreads,
             } else {
               if (a.rec) rec_slot(b)[1] = 1;
 #pragma unroll
-              for (int c = 0; c < C; ++c) acc[c] = fmaf(thr[c] * albedo_at(c, qp), cosv, acc[c]);
+              for (int c = 0; c < C; ++c) acc(c) = fmaf(thr(c) * albedo_at(c, qp), cosv, acc(c));
               m.o = o2;
               continue_path(qp);
             }
