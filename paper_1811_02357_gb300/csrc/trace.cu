@@ -333,7 +333,7 @@ struct TraceArgs {
 };
 
 #ifndef IRTPS_TRACE_MINB
-#define IRTPS_TRACE_MINB 8
+#define IRTPS_TRACE_MINB 9
 #endif
 #ifndef IRTPS_TRACE_MINB_BATCH
 #define IRTPS_TRACE_MINB_BATCH 6
@@ -389,7 +389,12 @@ __global__ void __launch_bounds__(kTraceThreads,
   unsigned item = blockIdx.x * blockDim.x + threadIdx.x;
   const ObjTrace *ob = &a.one;
   const LevelTable *lt = lts;
-  int k = 0, ip = 0, p = 0, j = 0, s_end = 0;
+  // the item's indices and the path's bounce state, used at set-up and resolve only, in shared-memory
+  // columns (one per lane) like the path's sums below: the registers go to the march
+  __shared__ int s_item[9][kTraceThreads];
+  int &k = s_item[0][threadIdx.x], &ip = s_item[1][threadIdx.x], &p = s_item[2][threadIdx.x];
+  int &j = s_item[3][threadIdx.x], &s_end = s_item[4][threadIdx.x];
+  k = ip = p = j = s_end = 0;
   auto take = [&](unsigned it) -> int {  // returns the item's first sample
     item = it;
     if constexpr (BATCH) {
@@ -415,7 +420,8 @@ __global__ void __launch_bounds__(kTraceThreads,
     }
   };
   const bool alive = item < n_items;
-  int s = alive ? take(item) : 0;
+  int &s = s_item[5][threadIdx.x];
+  s = alive ? take(item) : 0;
   // the pixel's own vertex, lifted: origin of every primary ray of this lane
   auto pixel_origin = [&]() -> F3 {
     const int W = ob->f.W;
@@ -430,7 +436,11 @@ __global__ void __launch_bounds__(kTraceThreads,
   const uint32_t iter_base = a.iter_dev ? *a.iter_dev : a.iter;
 
   int phase = alive ? PH_SETUP : PH_DONE;
-  int b = 1, qp = 0, ks = 0, budget = alive ? budget0() : 0;
+  int &b = s_item[6][threadIdx.x], &qp = s_item[7][threadIdx.x], &ks = s_item[8][threadIdx.x];
+  b = 1;
+  qp = 0;
+  ks = 0;
+  int budget = alive ? budget0() : 0;
   bool shadow = false;
   float cosv = 0.0f;
   // the path's throughput and radiance (touched once per segment) and the item's Kahan sums over
