@@ -336,10 +336,10 @@ struct TraceArgs {
 #define IRTPS_TRACE_MINB 9
 #endif
 #ifndef IRTPS_TRACE_MINB_BATCH
-#define IRTPS_TRACE_MINB_BATCH 6
+#define IRTPS_TRACE_MINB_BATCH 8
 #endif
 #ifndef IRTPS_TRACE_MINB_SHARED
-#define IRTPS_TRACE_MINB_SHARED 8
+#define IRTPS_TRACE_MINB_SHARED 9
 #endif
 #ifndef IRTPS_MARCH_KEEP
 #define IRTPS_MARCH_KEEP 2
