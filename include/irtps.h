@@ -97,12 +97,14 @@ typedef struct irtps_options {
                          confidence blends with the 2x linear upsampling of the coarser level back
                          down; known pixels keep their values, a light without known pixels keeps
                          its traced values) (0) */
-  int ps_tensor;      /* subtract + PS (Eq. 4) of a single context: 0 the contraction pinv(L) I on the
-                         FP32 pipes (four pixels a thread, vector loads); 1 on the tensor cores
-                         (tcgen05, 128 pixels a tile, BF16 hi + lo split of I and pinv(L), FP32
-                         accumulation: I_hi P_hi + I_lo P_hi + I_hi P_lo).  Row masks and masked pixels
-                         are decided and solved identically in both (FP32 masks, FP64 3x3 solves).
-                         Batches use the FP32 form (0) */
+  int ps_tensor;      /* subtract + PS (Eq. 4) of a single context: 0 the contraction on the FP32
+                         pipes (1, 2 or 4 pixels a thread, vector loads; pinv(L) I, or (L^T L)^-1 L^T I
+                         when L^T L is well conditioned); 1 on the tensor cores (tcgen05, 128 pixels a
+                         tile, BF16 hi + lo split of I and pinv(L), FP32 accumulation:
+                         I_hi P_hi + I_lo P_hi + I_hi P_lo).  Row masks and masked pixels are decided
+                         and solved identically in both (FP32 masks; masked 3x3 systems in FP32 when
+                         well conditioned, else double-float sums with an FP64 inverse and condition
+                         number).  Batches use the FP32 form (0) */
 } irtps_options;
 
 /* Counters of the last irtps_iterate / irtps_trace / irtps_integrate call. */
@@ -141,8 +143,8 @@ int irtps_set_stream(irtps_ctx *ctx, void *stream);
 
 /* Stage 0 / stage 1 (Sec. IV): take the K input images (dtype IRTPS_F32 or
  * IRTPS_F16; host pointer if on_device == 0, else a device pointer readable on
- * the context stream) and run iteration 0: classic PS (Eq. 4, masked rows
- * re-solved in FP64) and integration of the normals into the surface H_0.
+ * the context stream) and run iteration 0: classic PS (Eq. 4; pixels with masked
+ * rows solved from their valid rows) and integration of the normals into the surface H_0.
  * Resets the IRT iteration index to 0. */
 int irtps_set_images(irtps_ctx *ctx, const void *images, int dtype, int on_device);
 

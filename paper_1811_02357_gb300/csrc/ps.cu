@@ -122,10 +122,11 @@ __device__ __forceinline__ void ps_store(const PSArgs &a, int p, const float (&G
 // A pixel with masked rows: the normal equations (L_v^T L_v) G_c = L_v^T I_v,c over the
 // valid rows, R = L_v^T I the FP32 sum of ps_row.  A well-conditioned system (FP32
 // condition number at most kRefineCond, the common case) is solved in FP32.  Otherwise
-// the matrix, its inverse (by the adjugate) and its 1-norm condition number are computed
-// in FP64 from the lights; fewer than 3 rows, a singular or ill-conditioned system
-// (condition above cond_max): ok = false; and R, whose FP32 rounding the condition number
-// would amplify, is summed again in FP64 from the pixel's valid rows (read again).
+// the matrix is summed from the lights in double-float arithmetic and its inverse (by the
+// adjugate) and 1-norm condition number are formed in FP64; fewer than 3 rows, a singular
+// or ill-conditioned system (condition above cond_max): ok = false; and R, whose FP32
+// rounding the condition number would amplify, is summed again in double-float from the
+// pixel's valid rows (read again).
 constexpr double kRefineCond = 16.0;
 enum : int { PS_SOLVED = 0, PS_INVALID = 1, PS_NEED_FP64 = 2 };
 
@@ -360,7 +361,7 @@ __device__ __forceinline__ void ps_pixel(const PSArgs &a, int p) {
 //     FP32 contraction and row masks; a pixel with every row valid is stored, and so
 //     is a masked one whose system FP32 settles (ps_masked_fp32); the rest go to a
 //     list with their row masks and right-hand sides;
-//   k_ps_masked: the FP64 part of the listed pixels' solves (ps_masked_fp64).
+//   k_ps_masked: the rest of the listed pixels' solves (ps_masked_fp64).
 // Per pixel the arithmetic is that of ps_pixel, so both forms give the same bits.
 
 template <typename TI, int V>
@@ -497,7 +498,7 @@ __global__ void __launch_bounds__(256, (NE && V < 4) ? kPsMinBlocks : 2) k_ps_fa
         masked = st == PS_NEED_FP64;
       }
     }
-    // pixels left for the FP64 solve, appended with one atomic per warp
+    // pixels left for the list kernel, appended with one atomic per warp
     const unsigned mm = __ballot_sync(0xffffffffu, masked);
     if (mm) {
       const int lane = threadIdx.x & 31, leader = __ffs(mm) - 1;
