@@ -833,11 +833,19 @@ static cudaError_t launch_ps_tc_t(Ctx &c, const PSArgs &a) {
   const size_t smem = tc_smem_bytes(c.K, C);
   cudaError_t e = cudaFuncSetAttribute(k_ps_tc<C, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int per = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ps_tc<C, TI>, kTcRows, smem);
+  // CTAs per SM from the shared-memory fit (the operands are most of a CTA's footprint; the
+  // occupancy query answered one for this kernel).  The CTAs never wait on one another, and 4 of
+  // them hold 128 of an SM's 512 tensor-memory columns, so any grid size is safe.
+  e = cudaFuncSetAttribute(k_ps_tc<C, TI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
+  int dev = 0, smem_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+    return e;
+  const int fit = std::max(1, std::min(4, smem_sm / (int)(smem + 1024)));
   const int tiles = (a.P + kTcRows - 1) / kTcRows;
-  int blocks = (per > 0 ? per : 1) * (c.sms > 0 ? c.sms : 1);
+  int blocks = fit * (c.sms > 0 ? c.sms : 1);
   if (blocks > tiles) blocks = tiles;
   k_ps_tc<C, TI><<<blocks, kTcRows, smem, c.stream>>>(a, c.dstats->counts + 6);
   return cudaGetLastError();
