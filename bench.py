@@ -314,6 +314,21 @@ def cpu_baseline(sc, spp, bounces, target_s=12.0, seed=1, shared=False, single_t
     return out
 
 
+# the library's default early-escape option (irtps_default_options), for the reference arm's config
+DEFAULT_EARLY_ESCAPE = 2
+
+
+def single_config(args, H, W, K, C, spp, bounces, n_iter, early_escape, world):
+    """The workload part of a single-object line's config, the same in both arms."""
+    big = K * C * H * W * (2 if args.images == "f16" else 4) > 256 * 1024 * 1024
+    return {"workload": args.workload, "H": H, "W": W, "K": K, "C": C, "spp": spp, "images": args.images,
+            "sampling": args.sampling,
+            "options": dict(WORKLOAD_OPTIONS.get(args.workload, {}), early_escape=early_escape),
+            "bounces": bounces, "irt_iterations_per_step": n_iter, "parallelism": f"replicas{world}",
+            "l2": ("inputs larger than L2 (the step's images, copied in every step)" if big else
+                   "512 MB buffer written between timed steps")}
+
+
 def run_reference(args):
     """--impl reference: the oracle timed on the host cores, same workload and metric."""
     world, rank, _ = dist_setup()
@@ -335,10 +350,15 @@ def run_reference(args):
         last = cpu_baseline(sc, spp, bounces, target_s=per_step_s, shared=shared)
         vals.append(last["value"])
     v = float(np.mean(vals))
+    if name == "batch_objects":
+        config = {"workload": args.workload, "spp": spp, "bounces": bounces, "sampling": args.sampling}
+    else:
+        ee = args.early_escape if args.early_escape is not None else DEFAULT_EARLY_ESCAPE
+        config = single_config(args, sc.H, sc.W, sc.K, sc.C, spp, bounces, n_iter, ee, world)
     line = {"impl": "reference", "metric": "IRT-PS Mrays/s", "value": v, "unit": "Mrays/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "spp": spp, "bounces": bounces, "sampling": args.sampling},
+            "config": config,
             "cpu_baseline": dict(last, value=v),
             "e2e": {"value": v, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -838,12 +858,8 @@ def main():
     line = {"metric": "IRT-PS Mrays/s", "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "H": H, "W": W, "K": K, "C": C, "spp": spp, "images": args.images,
-                       "sampling": args.sampling, "trace_blocks_per_sm": tuning[0], "mip_cut": tuning[1],
-                       "options": dict(WORKLOAD_OPTIONS.get(args.workload, {}), early_escape=opt.early_escape),
-                       "bounces": bounces, "irt_iterations_per_step": n_iter, "parallelism": f"replicas{world}",
-                       "l2": ("inputs larger than L2 (the step's images, copied in every step)" if big else
-                              "512 MB buffer written between timed steps")},
+            "config": single_config(args, H, W, K, C, spp, bounces, n_iter, opt.early_escape, world),
+            "tuning": {"trace_blocks_per_sm": tuning[0], "mip_cut": tuning[1]},
             "pixel_iters_per_s": P * n_iter * world * args.steps / (ms_all / 1e3),
             "primary_mrays_per_s": tot["primary"] * world / (ms_all / 1e3) / 1e6,
             "stage_ms_per_step": {"trace": tot["trace_ms"] / args.steps, "ps": tot["ps_ms"] / args.steps,

@@ -7,6 +7,7 @@
 * The workload table is self-consistent (scene factories, option names, traffic entries,
   image types and tuner divisors).
 """
+import json
 import os
 import sys
 
@@ -64,3 +65,28 @@ def test_workload_table_is_consistent():
         assert name in bench.WORKLOADS and sampling in ("per_light", "shared") and traffic > 0
     for table in (bench.WORKLOAD_IMAGES, bench.WORKLOAD_TUNE_DIV):
         assert set(table) <= set(bench.WORKLOADS)
+
+
+def test_reference_arm_config_matches_ours(tmp_path):
+    """The reference arm prints the same config as ours for a single-object workload (built by the
+    same function from the workload), and its early-escape default is the library's."""
+    import argparse
+    import subprocess
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1811_02357_gb300 import irtps
+    assert bench.DEFAULT_EARLY_ESCAPE == irtps.irtps_default_options().early_escape
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "bowl_64", "--steps", "1", "--warmup", "0"], capture_output=True, text=True, env=env,
+                       cwd=ROOT, timeout=300)
+    assert r.returncode == 0
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    import scenes
+    sc = scenes.bowl_64()
+    _, _, spp, bounces, n_iter, _, _ = bench.WORKLOADS["bowl_64"]
+    args = argparse.Namespace(workload="bowl_64", images=bench.WORKLOAD_IMAGES.get("bowl_64", "f32"),
+                              sampling="per_light")
+    ours = bench.single_config(args, sc.H, sc.W, sc.K, sc.C, spp, bounces, n_iter,
+                               irtps.irtps_default_options().early_escape, 1)
+    assert line["config"] == json.loads(json.dumps(ours))
